@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched dense simplex (Gurung & Ray, arXiv 1802.08557).
+
+One step = one lp_batch_solve over the whole batch: every LP's tableau is
+built on the device from A, b, c and Steps 1-3 run until each LP halts.
+
+Default workload: 1e5 random dense LPs of 50 x 50 (A~U[-1,1], c~U[-1,1],
+80% with b~U[1,10], 20% with b~U[-5,10] needing phase I, ~5% infeasible or
+unbounded by construction), FP64.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+on the host cores instead (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LPs solved/s on 1 GB300 vs plain FP64 GPU simplex at <=1e-9 rel obj err; % roofline"
+DEFAULT_WORKLOAD = "dense50x50_phase1_100k"
+# FP64 roofline denominator: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
+# (the GB300's nominal 1.25 TFLOP/s FP64 at the maximum SM clock).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--num-lps", type=int, default=None, help="override the workload's batch size")
+    p.add_argument("--cpu-sample", type=int, default=20000, help="LPs timed for the CPU oracle baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_batch(name, num, rank):
+    """The named workload; rank r of a weak-scaling run solves LPs r*N .. (r+1)*N-1."""
+    import inspect
+    from paper_1802_08557_gb300 import workloads as W
+    fn = W.WORKLOADS[name]
+    count = num if num is not None else inspect.signature(fn).parameters["num"].default
+    return fn(num=count, start=rank * count)
+
+
+def algorithmic_fmas(batch, iters):
+    """Algorithmic FMA count: every pivot updates the (m+1) x (n+1) condensed
+    tableau (lower bound: phase I's wider tableau is not counted)."""
+    m = batch.m.astype(np.float64)
+    n = batch.n.astype(np.float64)
+    return float(np.sum(iters.astype(np.float64) * (m + 1.0) * (n + 1.0)))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+def cpu_oracle_rate(batch, sample: int, threads: int):
+    """The oracle as it stands, on `sample` LPs of the batch, on `threads`
+    host threads.  Returns LPs/s and the wall time."""
+    import oracle
+    k = min(sample, batch.num_lps)
+    idx = np.linspace(0, batch.num_lps - 1, k).astype(np.int64)
+    lps = [batch.lp(int(i)) for i in idx]
+    oracle.lib()
+    t0 = time.perf_counter()
+    oracle.solve_batch(lps, threads=threads)
+    dt = time.perf_counter() - t0
+    return k / dt, dt, k
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    batch = make_batch(args.workload, args.num_lps, 0)
+    threads = os.cpu_count() or 1
+    sample = max(100, min(args.cpu_sample, batch.num_lps))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(batch, max(10, sample // 20), threads)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt, k = cpu_oracle_rate(batch, sample, threads)
+        rates.append(r)
+        times.append(dt)
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "LPs/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "num_lps": batch.num_lps},
+        "cpu_baseline": {"value": value, "unit": "LPs/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{sample} of {batch.num_lps} LPs per step, evenly spaced indices"},
+        "e2e": {"value": value, "unit": "LPs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1802_08557_gb300 import build, lpbatch as lpb
+    build.build()
+    lpb.load()
+
+    batch = make_batch(args.workload, args.num_lps, rank)
+    N = batch.num_lps
+    A = torch.from_numpy(batch.A).to(dev)
+    b = torch.from_numpy(batch.b).to(dev)
+    c = torch.from_numpy(batch.c).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    h = lpb.lp_batch_create(batch.m, batch.n, batch.a_off, A, batch.b_off, b, batch.c_off, c,
+                            lpb.LPB_DEVICE, None, stream)
+    info = lpb.lp_batch_plan_info(h)
+    in_bytes = (A.numel() + b.numel() + c.numel()) * 8
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        lpb.lp_batch_solve(h, stream)
+    torch.cuda.synchronize()
+
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        time.sleep(0.25)
+        start.record(stream)
+        for s in range(args.steps):
+            ev[s][0].record(stream)
+            lpb.lp_batch_solve(h, stream)
+            ev[s][1].record(stream)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    elapsed_ms = start.elapsed_time(stop)
+    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    clocks = clk.summary()
+
+    res = dict(status=np.zeros(N, np.int32), iters=np.zeros(N, np.int32), obj=np.zeros(N))
+    lpb.lp_batch_results(h, res["status"], res["iters"], res["obj"], None, None, lpb.LPB_HOST)
+    fmas = algorithmic_fmas(batch, res["iters"])
+    kernel_ms = statistics.mean(step_ms)
+    achieved_gflops = 2.0 * fmas / (kernel_ms * 1e-3) / 1e9
+    total_lps = N * ws * args.steps
+    value = total_lps / (elapsed_ms * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers ----------------
+    e2e = None
+    if not args.no_e2e:
+        pinned = {k: torch.from_numpy(getattr(batch, k)).pin_memory() for k in ("A", "b", "c")}
+        out = dict(status=torch.empty(N, dtype=torch.int32).pin_memory(),
+                   iters=torch.empty(N, dtype=torch.int32).pin_memory(),
+                   obj=torch.empty(N, dtype=torch.float64).pin_memory(),
+                   x=torch.empty(int(batch.n.astype(np.int64).sum()), dtype=torch.float64).pin_memory())
+        meta_bytes = N * (4 + 4 + 8 + 8 + 8)
+        h2d = sum(v.numel() * 8 for v in pinned.values()) + meta_bytes
+        d2h = sum(v.numel() * v.element_size() for v in out.values())
+
+        def e2e_step():
+            hh = lpb.lp_batch_create(batch.m, batch.n, batch.a_off, pinned["A"], batch.b_off, pinned["b"],
+                                     batch.c_off, pinned["c"], lpb.LPB_HOST, None, stream)
+            lpb.lp_batch_solve(hh, stream)
+            lpb.lp_batch_results(hh, out["status"], out["iters"], out["obj"], out["x"], None, lpb.LPB_HOST)
+            lpb.lp_batch_destroy(hh)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        e2e_steps = max(1, min(args.steps, 3))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": N * ws * e2e_steps / dt, "unit": "LPs/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, dt, k = cpu_oracle_rate(batch, args.cpu_sample, threads)
+        cpu = {"value": rate, "unit": "LPs/s", "cores": threads, "kind": "oracle",
+               "sample": f"{k} of {N} LPs (evenly spaced indices), {dt:.1f} s wall"}
+
+    lpb.lp_batch_destroy(h)
+    if rank == 0:
+        counts = np.bincount(res["status"], minlength=5)
+        line = {
+            "metric": METRIC, "value": value, "unit": "LPs/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "num_lps_per_gpu": N, "precision": "fp64",
+                       "l2": f"inputs larger than L2 ({in_bytes / 1e9:.2f} GB of A,b,c per step vs 0.13 GB L2)",
+                       "launch_groups": info["num_groups"], "phase1_lps": info["num_phase1"],
+                       "status_counts": {"optimal": int(counts[0]), "infeasible": int(counts[1]),
+                                         "unbounded": int(counts[2]), "iter_limit": int(counts[3]),
+                                         "numerical": int(counts[4])},
+                       "mean_pivots": float(res["iters"].mean())},
+            "roofline": {"bound": "alu", "kernel": "fp64_resident_kernel", "achieved": achieved_gflops,
+                         "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved_gflops / FP64_PEAK_GFLOPS,
+                         "traffic": None,
+                         "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF)",
+                         "work": "sum over LPs of pivots x (m+1)(n+1) FMAs"},
+            "clocks": clocks,
+            "gpu_launches": args.steps * info["num_groups"],
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

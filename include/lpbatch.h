@@ -1,0 +1,159 @@
+/*
+ * lpbatch.h -- C ABI of the GB300 batched dense simplex solver.
+ *
+ * The solver runs the simplex method of Gurung & Ray, "Simultaneous Solving
+ * of Batched Linear Programs on a GPU" (arXiv 1802.08557), on many
+ * independent LPs at once.  Each LP is
+ *
+ *     maximize   c^T x                    (Section 3, Eq. 1)
+ *     subject to A x <= b                 (Eq. 2)
+ *                x >= 0                   (Eq. 3)
+ *
+ * with A of size m x n.  The solve starts from the slack basis (Eq. 4) and
+ * runs the two-phase method (Section 3) when some b_i < 0.  Each iteration is
+ * Step 1 (entering variable: most negative reduced cost), Step 2 (leaving
+ * variable: minimum ratio) and Step 3 (pivot: divide the pivot row by the
+ * pivot element, rank-1 update of every other row), Section 3.1.  LPs of
+ * different sizes may share a batch (the paper's Section 4 batches LPs of one
+ * size only).
+ *
+ * Conventions (identical in every entry point):
+ *  - All floating-point data is IEEE binary64.  A is row-major per LP.
+ *  - Ties: the entering variable is the LOWEST variable index whose reduced
+ *    cost lies within tau*max(1,|d*|) of the minimum d*; the leaving row is
+ *    the LOWEST row index whose ratio lies within tau*max(1,|r*|) of the
+ *    minimum r*.  Variables are numbered 0..n-1 (structural), n..n+m-1
+ *    (slack of row i = n+i), n+m.. (artificials of the rows with b_i < 0).
+ *  - A row takes part in the ratio test when its entry in the entering
+ *    column is > eps_piv.  An LP is optimal when no eligible reduced cost is
+ *    < -eps_opt, and infeasible when the phase-I optimum exceeds
+ *    eps_feas*max(1, max_i |b_i|).
+ *  - Error codes (lpb_err) report call failures; the outcome of each LP is
+ *    an lp_status value, not an error.  No entry point aborts or exits.
+ *  - Thread safety: distinct handles may be used from distinct threads; one
+ *    handle must not be used by two threads at once.
+ */
+#ifndef LPBATCH_H
+#define LPBATCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Outcome of one LP (Section 3.1 halt conditions; Section 3 two-phase test). */
+typedef enum {
+    LP_OPTIMAL = 0,     /* no entering variable: the basis is optimal          */
+    LP_INFEASIBLE = 1,  /* phase-I optimum > 0: Ax <= b, x >= 0 has no point    */
+    LP_UNBOUNDED = 2,   /* Step 2 found no admissible ratio in phase II         */
+    LP_ITER_LIMIT = 3,  /* max_iters pivots done without reaching a halt        */
+    LP_NUMERICAL = 4    /* breakdown (non-finite pivot, unbounded phase I)      */
+} lp_status;
+
+/* Result of a call. */
+typedef enum {
+    LPB_OK = 0,
+    LPB_EINVAL = 1,     /* bad argument (null pointer, size < 1, non-finite data, bad offset) */
+    LPB_ENOMEM = 2,     /* device or host allocation failed                     */
+    LPB_ECUDA = 3,      /* a CUDA runtime call failed (text in lpb_last_error)  */
+    LPB_ETOOBIG = 4,    /* an LP exceeds the supported size                     */
+    LPB_ENOTSOLVED = 5  /* results requested before any lp_batch_solve          */
+} lpb_err;
+
+/* Arithmetic of the tableau. */
+enum { LP_PREC_FP64 = 0 };
+
+/* Tolerances and limits.  Fill with lpb_default_opts() and then override. */
+typedef struct {
+    int32_t precision;   /* LP_PREC_FP64                                          */
+    int32_t max_iters;   /* pivots per LP, both phases; <= 0: 50*(m+n)             */
+    double eps_opt;      /* default 1e-9                                          */
+    double eps_piv;      /* default 1e-9                                          */
+    double eps_feas;     /* default 1e-9                                          */
+    double tau;          /* relative tie window, default 1e-12                    */
+    int32_t block_threads; /* threads per LP; 0 = chosen from the LP size        */
+    int32_t reserved;
+} lp_batch_opts;
+
+typedef struct lp_batch lp_batch;   /* opaque; owned by the library */
+
+/* Where a pointer argument lives. */
+enum { LPB_HOST = 0, LPB_DEVICE = 1 };
+
+/* Largest LP (m and n each) the library accepts. */
+#define LPB_MAX_DIM 16384
+
+void lpb_default_opts(lp_batch_opts *opts);
+
+/*
+ * Create a batch of `num_lps` LPs and upload / copy their data to the current
+ * CUDA device.  (Section 4.1 and Algorithm 1: the host gathers the LPs and
+ * copies them to device memory; here the library also plans the launches.)
+ *
+ *  m, n          [host, num_lps]  sizes of each LP, 1 <= m,n <= LPB_MAX_DIM.
+ *  a_off         [host, num_lps]  element offset of LP k's A (row-major m x n)
+ *                                 in `A`; NULL = packed back to back.
+ *                                 Offsets may repeat (LPs sharing A).
+ *  b_off, c_off  [host, num_lps]  same for b (m entries) and c (n entries).
+ *  A, b, c       [ptr_kind]       data; must hold every offset + size.
+ *  a_len, b_len, c_len            number of elements of A, b and c.
+ *  ptr_kind      LPB_HOST or LPB_DEVICE (A, b, c only; the size and offset
+ *                arrays are always host memory).
+ *  opts          NULL = defaults.
+ *  stream        cudaStream_t used for the copies (NULL = legacy default).
+ *
+ * Ownership: every argument is only read during the call; the library keeps
+ * its own copies and retains no caller pointer.  The call returns after the
+ * data has been copied and checked.  Non-finite entries give LPB_EINVAL.
+ * On error *out is set to NULL and nothing is leaked.
+ */
+lpb_err lp_batch_create(lp_batch **out, int32_t num_lps,
+                        const int32_t *m, const int32_t *n,
+                        const int64_t *a_off, const double *A, int64_t a_len,
+                        const int64_t *b_off, const double *b, int64_t b_len,
+                        const int64_t *c_off, const double *c, int64_t c_len,
+                        int32_t ptr_kind, const lp_batch_opts *opts, void *stream);
+
+/*
+ * Solve every LP of the batch on `stream` (cudaStream_t; NULL = legacy
+ * default stream).  Asynchronous: returns after the kernels are enqueued.
+ * Builds each tableau on the device from the uploaded A, b, c and runs
+ * Steps 1-3 until every LP halts (Section 3.1).  May be called again (each
+ * call solves from scratch).
+ */
+lpb_err lp_batch_solve(lp_batch *h, void *stream);
+
+/*
+ * Copy results of the last solve out (waits for that solve to finish).
+ *  status [num_lps] int32 lp_status, iters [num_lps] int32 pivots of both
+ *  phases, obj [num_lps] objective value of the final tableau,
+ *  x [sum n] final basic solution, LP k at offset sum_{j<k} n_j,
+ *  y [sum m] reduced costs of the slack variables (LP duals; for
+ *  LP_INFEASIBLE the Farkas multipliers of the phase-I optimum), LP k at
+ *  offset sum_{j<k} m_j.
+ * Any output pointer may be NULL (not copied).  ptr_kind says whether the
+ * outputs are host or device memory.  For LPs that are not LP_OPTIMAL, x, obj
+ * and y describe the last basis reached.
+ */
+lpb_err lp_batch_results(lp_batch *h, int32_t *status, int32_t *iters, double *obj,
+                         double *x, double *y, int32_t ptr_kind);
+
+/* Plan of the batch: number of launch groups, largest shared-memory
+ * footprint in bytes, and number of LPs with a phase I.  Any pointer may be NULL. */
+lpb_err lp_batch_plan_info(const lp_batch *h, int32_t *num_groups, int64_t *max_smem_bytes,
+                           int32_t *num_phase1);
+
+/* Free the batch (waits for its pending work).  NULL is accepted. */
+lpb_err lp_batch_destroy(lp_batch *h);
+
+/* Static text of an error code. */
+const char *lpb_strerror(lpb_err err);
+
+/* Detail of the last failing call on this thread ("" if none). */
+const char *lpb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPBATCH_H */

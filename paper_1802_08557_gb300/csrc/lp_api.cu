@@ -1,0 +1,345 @@
+// lp_api.cu -- host side of the C ABI declared in include/lpbatch.h.
+//
+// lp_batch_create uploads the LPs, checks them and plans the launches (the
+// role of the batching routine, Algorithm 1 of Section 4.1: it sizes the
+// work from each LP's tableau footprint, Eq. 5).  Instead of chunking by
+// free memory and launching one block per LP of a single size, LPs are
+// grouped by shared-memory footprint and each group is one launch of the
+// SMEM-resident kernel.  lp_batch_solve enqueues the groups on the caller's
+// stream; lp_batch_results copies the outputs.
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lp_internal.h"
+#include "lpbatch.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lpb_err fail(lpb_err e, const std::string& msg) {
+    g_last_error = msg;
+    return e;
+}
+
+lpb_err cuda_fail(cudaError_t err, const char* what) {
+    return fail(LPB_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
+}
+
+// One stream-ordered memory pool per device that keeps freed memory cached,
+// so that create/destroy cycles do not return memory to the driver.
+cudaError_t device_pool(int dev, cudaMemPool_t* out) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) { *out = it->second; return cudaSuccess; }
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    cudaError_t err = cudaMemPoolCreate(&pool, &props);
+    if (err != cudaSuccess) return err;
+    uint64_t keep = UINT64_MAX;
+    err = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (err != cudaSuccess) return err;
+    pools[dev] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+
+class DeviceGuard {
+public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev_);
+        if (prev_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != prev_) cudaSetDevice(prev_);
+    }
+private:
+    int prev_ = 0;
+};
+
+struct Group {
+    int64_t offset;  // into the order array
+    int32_t count;
+    int32_t threads;
+    size_t smem;
+};
+
+int pick_threads(int m, int n, int k, int requested) {
+    if (requested > 0) return std::min(std::max(32, (requested + 31) / 32 * 32), lpb::kMaxThreads);
+    const int64_t e = (int64_t)(m + 1 + (k > 0)) * (n + k + 1);
+    if (e <= 128) return 32;
+    if (e <= 1024) return 64;
+    if (e <= 8192) return 128;
+    if (e <= 32768) return 256;
+    return 512;
+}
+
+}  // namespace
+
+struct lp_batch {
+    int device = 0;
+    int32_t num_lps = 0;
+    cudaMemPool_t pool = nullptr;
+    std::vector<void*> allocs;
+    lpb::DeviceBatch d{};
+    int32_t* d_order = nullptr;
+    std::vector<Group> groups;
+    lpb::Tolerances tol{};
+    int64_t total_x = 0, total_y = 0;
+    cudaStream_t last_stream = nullptr;
+    bool solved = false;
+    int32_t num_phase1 = 0;
+    size_t max_smem = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t alloc(lp_batch* h, T** p, size_t count, cudaStream_t s) {
+    void* v = nullptr;
+    cudaError_t err = cudaMallocFromPoolAsync(&v, std::max<size_t>(count, 1) * sizeof(T), h->pool, s);
+    if (err != cudaSuccess) return err;
+    h->allocs.push_back(v);
+    *p = static_cast<T*>(v);
+    return cudaSuccess;
+}
+
+void release(lp_batch* h, cudaStream_t s) {
+    for (void* p : h->allocs) cudaFreeAsync(p, s);
+    h->allocs.clear();
+    cudaStreamSynchronize(s);
+}
+
+}  // namespace
+
+extern "C" {
+
+void lpb_default_opts(lp_batch_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = LP_PREC_FP64;
+    o->max_iters = 0;
+    o->eps_opt = 1e-9;
+    o->eps_piv = 1e-9;
+    o->eps_feas = 1e-9;
+    o->tau = 1e-12;
+    o->block_threads = 0;
+}
+
+const char* lpb_strerror(lpb_err e) {
+    switch (e) {
+        case LPB_OK: return "success";
+        case LPB_EINVAL: return "invalid argument";
+        case LPB_ENOMEM: return "out of memory";
+        case LPB_ECUDA: return "CUDA runtime error";
+        case LPB_ETOOBIG: return "LP too large";
+        case LPB_ENOTSOLVED: return "no solve has been run on this batch";
+    }
+    return "unknown error";
+}
+
+const char* lpb_last_error(void) { return g_last_error.c_str(); }
+
+lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const int32_t* n,
+                        const int64_t* a_off, const double* A, int64_t a_len,
+                        const int64_t* b_off, const double* b, int64_t b_len,
+                        const int64_t* c_off, const double* c, int64_t c_len,
+                        int32_t ptr_kind, const lp_batch_opts* opts, void* stream) {
+    g_last_error.clear();
+    if (!out) return fail(LPB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (num_lps < 1) return fail(LPB_EINVAL, "num_lps < 1");
+    if (!m || !n || !A || !b || !c) return fail(LPB_EINVAL, "m, n, A, b and c must be non-NULL");
+    if (ptr_kind != LPB_HOST && ptr_kind != LPB_DEVICE) return fail(LPB_EINVAL, "ptr_kind must be LPB_HOST or LPB_DEVICE");
+    lp_batch_opts o;
+    lpb_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != LP_PREC_FP64) return fail(LPB_EINVAL, "unsupported precision");
+    if (!(o.eps_opt >= 0) || !(o.eps_piv >= 0) || !(o.eps_feas >= 0) || !(o.tau >= 0))
+        return fail(LPB_EINVAL, "tolerances must be >= 0");
+
+    // sizes and offsets (host)
+    std::vector<int32_t> hm(m, m + num_lps), hn(n, n + num_lps);
+    std::vector<int64_t> ha(num_lps), hb(num_lps), hc(num_lps), hx(num_lps), hy(num_lps);
+    int64_t pa = 0, pb = 0, pc = 0, px = 0, py = 0;
+    for (int32_t k = 0; k < num_lps; ++k) {
+        const int64_t mk = hm[k], nk = hn[k];
+        if (mk < 1 || nk < 1) return fail(LPB_EINVAL, "LP " + std::to_string(k) + ": m and n must be >= 1");
+        if (mk > LPB_MAX_DIM || nk > LPB_MAX_DIM)
+            return fail(LPB_ETOOBIG, "LP " + std::to_string(k) + ": m or n above LPB_MAX_DIM");
+        ha[k] = a_off ? a_off[k] : pa;
+        hb[k] = b_off ? b_off[k] : pb;
+        hc[k] = c_off ? c_off[k] : pc;
+        pa += mk * nk; pb += mk; pc += nk;
+        if (ha[k] < 0 || ha[k] + mk * nk > a_len) return fail(LPB_EINVAL, "LP " + std::to_string(k) + ": A offset out of range");
+        if (hb[k] < 0 || hb[k] + mk > b_len) return fail(LPB_EINVAL, "LP " + std::to_string(k) + ": b offset out of range");
+        if (hc[k] < 0 || hc[k] + nk > c_len) return fail(LPB_EINVAL, "LP " + std::to_string(k) + ": c offset out of range");
+        hx[k] = px; px += nk;
+        hy[k] = py; py += mk;
+    }
+
+    lp_batch* h = new (std::nothrow) lp_batch();
+    if (!h) return fail(LPB_ENOMEM, "host allocation failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t err = cudaGetDevice(&h->device);
+    if (err != cudaSuccess) { delete h; return cuda_fail(err, "cudaGetDevice"); }
+    err = device_pool(h->device, &h->pool);
+    if (err != cudaSuccess) { delete h; return cuda_fail(err, "memory pool"); }
+    h->num_lps = num_lps;
+    h->total_x = px;
+    h->total_y = py;
+    h->tol = {o.eps_opt, o.eps_piv, o.eps_feas, o.tau, o.max_iters};
+    h->last_stream = s;
+
+    auto bail = [&](lpb_err e, const std::string& msg) {
+        release(h, s);
+        delete h;
+        return fail(e, msg);
+    };
+    auto bail_cuda = [&](cudaError_t e, const char* what) {
+        std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+        release(h, s);
+        delete h;
+        return fail(e == cudaErrorMemoryAllocation ? LPB_ENOMEM : LPB_ECUDA, msg);
+    };
+
+    int32_t *dm, *dn, *dk, *dorder, *dstatus, *diters;
+    int64_t *da, *db, *dc, *dx_off, *dy_off;
+    double *dA, *dbv, *dcv, *dobj, *dx, *dy;
+    unsigned long long* dbad;
+    if ((err = alloc(h, &dm, num_lps, s)) || (err = alloc(h, &dn, num_lps, s)) ||
+        (err = alloc(h, &dk, num_lps, s)) || (err = alloc(h, &dorder, num_lps, s)) ||
+        (err = alloc(h, &dstatus, num_lps, s)) || (err = alloc(h, &diters, num_lps, s)) ||
+        (err = alloc(h, &da, num_lps, s)) || (err = alloc(h, &db, num_lps, s)) ||
+        (err = alloc(h, &dc, num_lps, s)) || (err = alloc(h, &dx_off, num_lps, s)) ||
+        (err = alloc(h, &dy_off, num_lps, s)) || (err = alloc(h, &dA, (size_t)a_len, s)) ||
+        (err = alloc(h, &dbv, (size_t)b_len, s)) || (err = alloc(h, &dcv, (size_t)c_len, s)) ||
+        (err = alloc(h, &dobj, num_lps, s)) || (err = alloc(h, &dx, (size_t)px, s)) ||
+        (err = alloc(h, &dy, (size_t)py, s)) || (err = alloc(h, &dbad, 1, s)))
+        return bail_cuda(err, "device allocation");
+
+    const cudaMemcpyKind kind = ptr_kind == LPB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const size_t nl = (size_t)num_lps;
+    if ((err = cudaMemcpyAsync(dm, hm.data(), nl * 4, cudaMemcpyHostToDevice, s)) ||
+        (err = cudaMemcpyAsync(dn, hn.data(), nl * 4, cudaMemcpyHostToDevice, s)) ||
+        (err = cudaMemcpyAsync(da, ha.data(), nl * 8, cudaMemcpyHostToDevice, s)) ||
+        (err = cudaMemcpyAsync(db, hb.data(), nl * 8, cudaMemcpyHostToDevice, s)) ||
+        (err = cudaMemcpyAsync(dc, hc.data(), nl * 8, cudaMemcpyHostToDevice, s)) ||
+        (err = cudaMemcpyAsync(dx_off, hx.data(), nl * 8, cudaMemcpyHostToDevice, s)) ||
+        (err = cudaMemcpyAsync(dy_off, hy.data(), nl * 8, cudaMemcpyHostToDevice, s)) ||
+        (err = cudaMemcpyAsync(dA, A, (size_t)a_len * 8, kind, s)) ||
+        (err = cudaMemcpyAsync(dbv, b, (size_t)b_len * 8, kind, s)) ||
+        (err = cudaMemcpyAsync(dcv, c, (size_t)c_len * 8, kind, s)))
+        return bail_cuda(err, "copy of the LP data");
+
+    h->d = lpb::DeviceBatch{dm, dn, da, db, dc, dx_off, dy_off, dA, dbv, dcv, dstatus, diters, dobj, dx, dy};
+    h->d_order = dorder;
+    if ((err = lpb::launch_prepare(h->d, num_lps, a_len, b_len, c_len, dk, dbad, s)))
+        return bail_cuda(err, "input check kernel");
+    std::vector<int32_t> hk(num_lps);
+    unsigned long long bad = 0;
+    if ((err = cudaMemcpyAsync(hk.data(), dk, nl * 4, cudaMemcpyDeviceToHost, s)) ||
+        (err = cudaMemcpyAsync(&bad, dbad, sizeof bad, cudaMemcpyDeviceToHost, s)) ||
+        (err = cudaStreamSynchronize(s)))
+        return bail_cuda(err, "input check");
+    if (bad) return bail(LPB_EINVAL, std::to_string(bad) + " non-finite entries in A, b or c");
+
+    // Plan: group LPs by (threads per CTA, shared-memory footprint rounded
+    // up to 4 KiB); one launch per group.
+    std::map<std::pair<int, size_t>, std::vector<int32_t>> buckets;
+    for (int32_t k = 0; k < num_lps; ++k) {
+        const lpb::ResidentLayout L = lpb::resident_layout(hm[k], hn[k], hk[k]);
+        if (L.total > lpb::kMaxSmemPerBlock)
+            return bail(LPB_ETOOBIG, "LP " + std::to_string(k) + ": tableau of " + std::to_string(L.total) +
+                                         " bytes exceeds the shared-memory budget");
+        const size_t smem = std::min(lpb::kMaxSmemPerBlock, (L.total + 4095) / 4096 * 4096);
+        const int threads = pick_threads(hm[k], hn[k], hk[k], o.block_threads);
+        buckets[{threads, smem}].push_back(k);
+        h->num_phase1 += hk[k] > 0;
+        h->max_smem = std::max(h->max_smem, smem);
+    }
+    std::vector<int32_t> order;
+    order.reserve(num_lps);
+    for (auto& kv : buckets) {
+        Group g;
+        g.offset = (int64_t)order.size();
+        g.count = (int32_t)kv.second.size();
+        g.threads = kv.first.first;
+        g.smem = kv.first.second;
+        order.insert(order.end(), kv.second.begin(), kv.second.end());
+        h->groups.push_back(g);
+    }
+    if ((err = cudaMemcpyAsync(dorder, order.data(), nl * 4, cudaMemcpyHostToDevice, s)) ||
+        (err = lpb::fp64_resident_prepare()) || (err = cudaStreamSynchronize(s)))
+        return bail_cuda(err, "plan upload");
+    *out = h;
+    return LPB_OK;
+}
+
+lpb_err lp_batch_solve(lp_batch* h, void* stream) {
+    g_last_error.clear();
+    if (!h) return fail(LPB_EINVAL, "handle is NULL");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (const Group& g : h->groups) {
+        cudaError_t err = lpb::launch_fp64_resident(h->d, h->tol, h->d_order + g.offset, g.count, g.threads,
+                                                    g.smem, s);
+        if (err != cudaSuccess) return cuda_fail(err, "solver launch");
+    }
+    h->last_stream = s;
+    h->solved = true;
+    return LPB_OK;
+}
+
+lpb_err lp_batch_results(lp_batch* h, int32_t* status, int32_t* iters, double* obj, double* x, double* y,
+                         int32_t ptr_kind) {
+    g_last_error.clear();
+    if (!h) return fail(LPB_EINVAL, "handle is NULL");
+    if (ptr_kind != LPB_HOST && ptr_kind != LPB_DEVICE) return fail(LPB_EINVAL, "ptr_kind must be LPB_HOST or LPB_DEVICE");
+    if (!h->solved) return fail(LPB_ENOTSOLVED, "lp_batch_solve has not been called");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = h->last_stream;
+    const cudaMemcpyKind kind = ptr_kind == LPB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const size_t nl = (size_t)h->num_lps;
+    cudaError_t err = cudaSuccess;
+    if (status && (err = cudaMemcpyAsync(status, h->d.status, nl * 4, kind, s))) return cuda_fail(err, "copy status");
+    if (iters && (err = cudaMemcpyAsync(iters, h->d.iters, nl * 4, kind, s))) return cuda_fail(err, "copy iters");
+    if (obj && (err = cudaMemcpyAsync(obj, h->d.obj, nl * 8, kind, s))) return cuda_fail(err, "copy obj");
+    if (x && (err = cudaMemcpyAsync(x, h->d.x, (size_t)h->total_x * 8, kind, s))) return cuda_fail(err, "copy x");
+    if (y && (err = cudaMemcpyAsync(y, h->d.y, (size_t)h->total_y * 8, kind, s))) return cuda_fail(err, "copy y");
+    if ((err = cudaStreamSynchronize(s))) return cuda_fail(err, "solve");
+    return LPB_OK;
+}
+
+lpb_err lp_batch_plan_info(const lp_batch* h, int32_t* num_groups, int64_t* max_smem_bytes, int32_t* num_phase1) {
+    if (!h) return fail(LPB_EINVAL, "handle is NULL");
+    if (num_groups) *num_groups = (int32_t)h->groups.size();
+    if (max_smem_bytes) *max_smem_bytes = (int64_t)h->max_smem;
+    if (num_phase1) *num_phase1 = h->num_phase1;
+    return LPB_OK;
+}
+
+lpb_err lp_batch_destroy(lp_batch* h) {
+    if (!h) return LPB_OK;
+    DeviceGuard guard(h->device);
+    cudaStreamSynchronize(h->last_stream);
+    release(h, h->last_stream);
+    delete h;
+    return LPB_OK;
+}
+
+}  // extern "C"

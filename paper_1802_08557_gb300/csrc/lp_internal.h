@@ -1,0 +1,88 @@
+// lp_internal.h -- declarations shared by the host API (lp_api.cu) and the
+// solver kernels.  Not part of the public ABI (see include/lpbatch.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace lpb {
+
+// Device-side view of a batch: per-LP sizes and element offsets, the data,
+// and the result arrays (Section 4.1: tableau data in global memory).
+struct DeviceBatch {
+    const int32_t* m;
+    const int32_t* n;
+    const int64_t* a_off;
+    const int64_t* b_off;
+    const int64_t* c_off;
+    const int64_t* x_off;  // prefix sums of n
+    const int64_t* y_off;  // prefix sums of m
+    const double* A;
+    const double* b;
+    const double* c;
+    int32_t* status;
+    int32_t* iters;
+    double* obj;
+    double* x;
+    double* y;  // may be null
+};
+
+struct Tolerances {
+    double eps_opt;
+    double eps_piv;
+    double eps_feas;
+    double tau;
+    int32_t max_iters;  // <= 0: 50*(m+n)
+};
+
+// Per-LP outcome codes (same values as lp_status in include/lpbatch.h).
+enum : int32_t { kOptimal = 0, kInfeasible = 1, kUnbounded = 2, kIterLimit = 3, kNumerical = 4 };
+
+constexpr int kMaxThreads = 512;
+constexpr int kMaxWarps = kMaxThreads / 32;
+constexpr size_t kMaxSmemPerBlock = 227 * 1024;  // opt-in dynamic shared memory per CTA on sm_103
+
+// Shared-memory layout of the SMEM-resident FP64 kernel for an LP with m
+// rows, n structural columns and k rows with b_i < 0 (k artificials).  The
+// k-independent arrays come first so the kernel can place them before it
+// has counted k.  Condensed tableau: R = m+1 (+1 phase-I row) rows, LD >=
+// n+k+1 columns (column 0 = right-hand side, then the non-basic variables).
+struct ResidentLayout {
+    int R, LD;
+    size_t red64, rkey, red32, row_var, neg;   // k-independent
+    size_t T, colE, col_var;                   // k-dependent
+    size_t total;
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+__host__ __device__ inline ResidentLayout resident_layout(int m, int n, int k) {
+    ResidentLayout L;
+    L.R = m + 1 + (k > 0 ? 1 : 0);
+    L.LD = (n + k + 1) | 1;  // odd stride: column reads hit distinct banks
+    size_t o = 0;
+    L.red64 = o;   o += 2 * kMaxWarps * sizeof(long long);
+    L.rkey = o;    o += align16((size_t)m * sizeof(long long));
+    L.red32 = o;   o += 2 * kMaxWarps * sizeof(unsigned);
+    L.row_var = o; o += align16((size_t)m * sizeof(int));
+    L.neg = o;     o += align16((size_t)m * sizeof(int));
+    L.T = o;       o += align16((size_t)L.R * (size_t)L.LD * sizeof(double));
+    L.colE = o;    o += align16((size_t)L.R * sizeof(double));
+    L.col_var = o; o += align16((size_t)L.LD * sizeof(int));
+    L.total = o;
+    return L;
+}
+
+// Launchers (lp_fp64_resident.cu).
+cudaError_t fp64_resident_prepare();
+cudaError_t launch_fp64_resident(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
+                                 int32_t count, int threads, size_t smem, cudaStream_t stream);
+
+// Checks (lp_api.cu helpers in lp_prepare.cu): counts non-finite values of
+// A, b, c into *bad and the rows with b_i < 0 of every LP into k[].
+cudaError_t launch_prepare(const DeviceBatch& B, int32_t num_lps, int64_t a_len, int64_t b_len,
+                           int64_t c_len, int32_t* k, unsigned long long* bad, cudaStream_t stream);
+
+}  // namespace lpb

@@ -1,0 +1,219 @@
+"""Thin ctypes binding of the C ABI in ``include/lpbatch.h``.
+
+Names follow the C functions.  The binding only marshals arguments: every
+step of the solve runs in the CUDA library.  Device buffers and streams come
+from PyTorch (``tensor.data_ptr()``, ``torch.cuda.current_stream().cuda_stream``);
+host buffers are numpy arrays.  If the compiled library is missing this module
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LP_OPTIMAL, LP_INFEASIBLE, LP_UNBOUNDED, LP_ITER_LIMIT, LP_NUMERICAL = 0, 1, 2, 3, 4
+LPB_OK, LPB_EINVAL, LPB_ENOMEM, LPB_ECUDA, LPB_ETOOBIG, LPB_ENOTSOLVED = 0, 1, 2, 3, 4, 5
+LPB_HOST, LPB_DEVICE = 0, 1
+LP_PREC_FP64 = 0
+LPB_MAX_DIM = 16384
+
+# Every symbol include/lpbatch.h declares.
+EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_results",
+            "lp_batch_plan_info", "lp_batch_destroy", "lpb_strerror", "lpb_last_error")
+
+
+class LPBatchOpts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("max_iters", ctypes.c_int32),
+        ("eps_opt", ctypes.c_double),
+        ("eps_piv", ctypes.c_double),
+        ("eps_feas", ctypes.c_double),
+        ("tau", ctypes.c_double),
+        ("block_threads", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class LPBError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        self.code = code
+        super().__init__(f"{where} failed: {strerror(code)} ({detail})")
+
+
+_lib = None
+_lock = threading.Lock()
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or _build.LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"CUDA solver library not built: {p} is missing "
+                              "(run __graft_entry__.build() or python -m paper_1802_08557_gb300.build)")
+        L = ctypes.CDLL(p)
+        L.lpb_default_opts.argtypes = [ctypes.POINTER(LPBatchOpts)]
+        L.lpb_default_opts.restype = None
+        L.lp_batch_create.argtypes = [ctypes.POINTER(_vp), _i32, _vp, _vp,
+                                      _vp, _vp, _i64, _vp, _vp, _i64, _vp, _vp, _i64,
+                                      _i32, ctypes.POINTER(LPBatchOpts), _vp]
+        L.lp_batch_create.restype = ctypes.c_int
+        L.lp_batch_solve.argtypes = [_vp, _vp]
+        L.lp_batch_solve.restype = ctypes.c_int
+        L.lp_batch_results.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i32]
+        L.lp_batch_results.restype = ctypes.c_int
+        L.lp_batch_plan_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i32)]
+        L.lp_batch_plan_info.restype = ctypes.c_int
+        L.lp_batch_destroy.argtypes = [_vp]
+        L.lp_batch_destroy.restype = ctypes.c_int
+        L.lpb_strerror.argtypes = [ctypes.c_int]
+        L.lpb_strerror.restype = ctypes.c_char_p
+        L.lpb_last_error.argtypes = []
+        L.lpb_last_error.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().lpb_strerror(code).decode()
+    except ImportError:
+        return f"error {code}"
+
+
+def _check(code: int, where: str):
+    if code != LPB_OK:
+        raise LPBError(code, where, load().lpb_last_error().decode())
+
+
+def lpb_default_opts(**overrides) -> LPBatchOpts:
+    o = LPBatchOpts()
+    load().lpb_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def _addr(a) -> int | None:
+    """Address of a numpy array or torch tensor (None for None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensors must be contiguous"
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def lp_batch_create(m, n, a_off, A, b_off, b, c_off, c, ptr_kind: int, opts: LPBatchOpts | None = None,
+                    stream=None):
+    """Returns an opaque handle (c_void_p).  ``m, n, *_off`` are numpy arrays
+    (host); A, b, c are numpy arrays (LPB_HOST) or CUDA tensors (LPB_DEVICE)."""
+    L = load()
+    m = np.ascontiguousarray(m, np.int32)
+    n = np.ascontiguousarray(n, np.int32)
+    a_off = None if a_off is None else np.ascontiguousarray(a_off, np.int64)
+    b_off = None if b_off is None else np.ascontiguousarray(b_off, np.int64)
+    c_off = None if c_off is None else np.ascontiguousarray(c_off, np.int64)
+    h = _vp()
+    lens = [int(np.prod(np.shape(v))) if isinstance(v, np.ndarray) else int(v.numel()) for v in (A, b, c)]
+    code = L.lp_batch_create(ctypes.byref(h), int(m.shape[0]), _addr(m), _addr(n),
+                             _addr(a_off), _addr(A), lens[0], _addr(b_off), _addr(b), lens[1],
+                             _addr(c_off), _addr(c), lens[2], ptr_kind,
+                             ctypes.byref(opts) if opts is not None else None, _stream_handle(stream))
+    _check(code, "lp_batch_create")
+    return h
+
+
+def lp_batch_solve(h, stream=None):
+    _check(load().lp_batch_solve(h, _stream_handle(stream)), "lp_batch_solve")
+
+
+def lp_batch_results(h, status=None, iters=None, obj=None, x=None, y=None, ptr_kind: int = LPB_HOST):
+    _check(load().lp_batch_results(h, _addr(status), _addr(iters), _addr(obj), _addr(x), _addr(y), ptr_kind),
+           "lp_batch_results")
+
+
+def lp_batch_plan_info(h):
+    g, s, p = _i32(), _i64(), _i32()
+    _check(load().lp_batch_plan_info(h, ctypes.byref(g), ctypes.byref(s), ctypes.byref(p)), "lp_batch_plan_info")
+    return dict(num_groups=g.value, max_smem_bytes=s.value, num_phase1=p.value)
+
+
+def lp_batch_destroy(h):
+    _check(load().lp_batch_destroy(h), "lp_batch_destroy")
+
+
+class BatchSolver:
+    """Convenience owner of one batch handle (``workloads.LPBatch`` input)."""
+
+    def __init__(self, batch, device_data: bool = True, opts: LPBatchOpts | None = None, stream=None):
+        self.batch = batch
+        self.num_lps = batch.num_lps
+        self.total_x = int(batch.n.astype(np.int64).sum())
+        self.total_y = int(batch.m.astype(np.int64).sum())
+        if device_data:
+            import torch
+            A = torch.from_numpy(batch.A).cuda()
+            b = torch.from_numpy(batch.b).cuda()
+            c = torch.from_numpy(batch.c).cuda()
+            torch.cuda.synchronize()
+            self.h = lp_batch_create(batch.m, batch.n, batch.a_off, A, batch.b_off, b, batch.c_off, c,
+                                     LPB_DEVICE, opts, stream)
+            del A, b, c
+        else:
+            self.h = lp_batch_create(batch.m, batch.n, batch.a_off, batch.A, batch.b_off, batch.b,
+                                     batch.c_off, batch.c, LPB_HOST, opts, stream)
+
+    def solve(self, stream=None):
+        lp_batch_solve(self.h, stream)
+
+    def results(self):
+        status = np.zeros(self.num_lps, np.int32)
+        iters = np.zeros(self.num_lps, np.int32)
+        obj = np.zeros(self.num_lps)
+        x = np.zeros(self.total_x)
+        y = np.zeros(self.total_y)
+        lp_batch_results(self.h, status, iters, obj, x, y, LPB_HOST)
+        return dict(status=status, iters=iters, obj=obj, x=x, y=y)
+
+    def plan_info(self):
+        return lp_batch_plan_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

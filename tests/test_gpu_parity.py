@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA solver (through the C ABI) against the CPU oracle,
+element by element, on seeded inputs shaped like the benchmark workloads,
+plus edge cases.  Status and pivot counts must match exactly; objective, x
+and y within 1e-10 relative (both sides run the same FP64 operations in the
+same order, so they are expected to be bitwise equal)."""
+import json
+import glob
+import os
+
+import numpy as np
+import pytest
+
+from paper_1802_08557_gb300 import lpbatch as lpb
+from paper_1802_08557_gb300 import workloads as W
+import oracle
+from parity_util import compare, gpu_solve, oracle_solve
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1802_08557_gb300 import build
+    build.build()
+    lpb.load()
+
+
+def _check(batch, **kw):
+    g = gpu_solve(batch, **{k: v for k, v in kw.items() if k in ("device_data", "opts")})
+    r = oracle_solve(batch, opts=kw.get("opts"))
+    n, bitwise = compare(batch, g, r)
+    return g, r, n, bitwise
+
+
+def test_golden_examples_through_abi():
+    cases = [json.load(open(p)) for p in sorted(glob.glob(os.path.join(GOLDEN, "worked_*.json")))]
+    batch = W.pack("golden", [(np.array(g["A"], float), np.array(g["b"], float), np.array(g["c"], float))
+                              for g in cases])
+    g = gpu_solve(batch)
+    xo, yo = batch.x_offsets(), batch.y_offsets()
+    for k, case in enumerate(cases):
+        m, n = len(case["b"]), len(case["c"])
+        assert g["status"][k] == case["status"], case["name"]
+        assert g["iters"][k] == case["iters"], case["name"]
+        assert g["obj"][k] == case["obj"], case["name"]
+        np.testing.assert_array_equal(g["x"][xo[k]:xo[k] + n], case["x"])
+        np.testing.assert_array_equal(g["y"][yo[k]:yo[k] + m], case["y"])
+
+
+def test_tiny_ragged_batch_matches_oracle():
+    from test_oracle_pins import tiny_lps
+    batch = W.pack("tiny", tiny_lps(2024, 900))
+    g, r, n, bitwise = _check(batch)
+    assert set(np.unique(g["status"])) >= {0, 1, 2}
+    assert g["plan"]["num_groups"] >= 1
+    assert bitwise == n
+
+
+def test_dense5x5_full_workload():
+    batch = W.WORKLOADS["dense5x5_1k"]()
+    g, r, n, bitwise = _check(batch)
+    assert np.all(g["status"] == lpb.LP_OPTIMAL)
+    assert bitwise == n
+
+
+def test_dense50x50_phase1_several_tiles():
+    batch = W.mixed_sign_dense(3000, 50, 50, start=500)
+    g, r, n, bitwise = _check(batch)
+    assert set(np.unique(g["status"])) == {0, 1, 2}
+    assert np.all(g["status"][batch.kind == W.KIND_INFEASIBLE] == lpb.LP_INFEASIBLE)
+    assert np.all(g["status"][batch.kind == W.KIND_UNBOUNDED] == lpb.LP_UNBOUNDED)
+    assert g["plan"]["num_phase1"] > 0
+    assert bitwise == n
+
+
+def test_support_function_subset():
+    batch = W.support_function(2000, start=7)
+    g, r, n, bitwise = _check(batch)
+    assert bitwise == n
+
+
+def test_shared_matrix_200x100_and_phase1_at_size():
+    batch = W.shared_matrix_family(24, m=200, n=100)
+    # force a phase I on some of them at the full 200 x 100 size
+    B = batch.b.reshape(24, 200)
+    B[::3, ::17] *= -0.05
+    g, r, n, bitwise = _check(batch)
+    assert g["plan"]["num_phase1"] >= 8
+    assert bitwise == n
+
+
+def test_uneven_sizes_resident_range():
+    batch = W.uneven_dense(150, lo=10, hi=500, max_elems=20000)
+    g, r, n, bitwise = _check(batch)
+    assert g["plan"]["num_groups"] > 3
+    assert bitwise == n
+
+
+def test_edge_shapes():
+    rng = np.random.default_rng(5)
+    lps = []
+    lps.append((np.array([[2.0]]), np.array([3.0]), np.array([1.0])))          # 1 x 1
+    lps.append((np.array([[-1.0]]), np.array([-2.0]), np.array([-1.0])))       # 1 x 1, phase I
+    lps.append((np.zeros((3, 2)), np.array([1.0, 0.0, 2.0]), np.array([-1.0, -2.0])))  # zero A
+    lps.append((np.zeros((2, 2)), np.array([1.0, 1.0]), np.array([1.0, 0.0])))  # zero A, unbounded
+    # every b_i < 0 (k = m): -A x <= -b with A, b > 0, c < 0 (bounded)
+    lps.append((-rng.uniform(0.5, 1, (6, 6)), -rng.uniform(0.5, 1, 6), -rng.uniform(0.1, 1, 6)))
+    lps.append((rng.uniform(-1, 1, (1, 40)), np.array([-0.5]), rng.uniform(-1, 1, 40)))   # m = 1 wide
+    lps.append((rng.uniform(-1, 1, (60, 1)), rng.uniform(-1, 2, 60), np.array([0.7])))    # n = 1 tall
+    lps.append((np.ones((4, 4)), np.zeros(4), np.ones(4)))                                # fully degenerate
+    batch = W.pack("edges", lps)
+    g, r, n, bitwise = _check(batch)
+    assert bitwise == n
+
+
+def test_iteration_limit_parity():
+    batch = W.mixed_sign_dense(300, 30, 30, start=11)
+    opts = lpb.lpb_default_opts(max_iters=7)
+    g, r, n, bitwise = _check(batch, opts=opts)
+    assert np.sum(g["status"] == lpb.LP_ITER_LIMIT) > 100
+    assert bitwise == n
+
+
+def test_thread_count_does_not_change_results():
+    batch = W.mixed_sign_dense(400, 40, 40, start=99)
+    base = gpu_solve(batch)
+    for t in (32, 64, 256, 512):
+        g = gpu_solve(batch, opts=lpb.lpb_default_opts(block_threads=t))
+        for key in ("status", "iters", "obj", "x", "y"):
+            np.testing.assert_array_equal(g[key], base[key], err_msg=f"threads={t} {key}")
+
+
+def test_host_and_device_inputs_agree_and_resolve_is_deterministic():
+    batch = W.mixed_sign_dense(500, 25, 35, start=3)
+    a = gpu_solve(batch, device_data=True)
+    b = gpu_solve(batch, device_data=False)
+    s = lpb.BatchSolver(batch)
+    s.solve(); c1 = s.results()
+    s.solve(); c2 = s.results()
+    s.close()
+    for key in ("status", "iters", "obj", "x", "y"):
+        np.testing.assert_array_equal(a[key], b[key])
+        np.testing.assert_array_equal(c1[key], c2[key])
+        np.testing.assert_array_equal(a[key], c1[key])
+
+
+def test_errors_are_codes():
+    bad = W.pack("nan", [(np.array([[np.nan]]), np.array([1.0]), np.array([1.0]))])
+    with pytest.raises(lpb.LPBError) as ei:
+        lpb.BatchSolver(bad)
+    assert ei.value.code == lpb.LPB_EINVAL
+    s = lpb.BatchSolver(W.positive_dense(2, 3, 3))
+    with pytest.raises(lpb.LPBError) as ei:
+        lpb.lp_batch_results(s.h, np.zeros(2, np.int32))
+    assert ei.value.code == lpb.LPB_ENOTSOLVED
+    s.close()
+
+
+@pytest.mark.slow
+def test_full_size_dense50x50_100k_sampled():
+    """The benchmark workload at full size in the benchmark's launch
+    configuration: 1e5 LPs of 50 x 50.  A seeded sample is compared with the
+    oracle element by element; every LP is checked for properties that hold at
+    any size."""
+    batch = W.WORKLOADS["dense50x50_phase1_100k"]()
+    g = gpu_solve(batch)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(batch.num_lps, 600, replace=False))
+    idx = np.concatenate([idx, [0, batch.num_lps - 1]])
+    r = oracle_solve(batch, idx)
+    n, bitwise = compare(batch, g, r, idx)
+    assert bitwise == n
+    st = g["status"]
+    assert np.all(np.isin(st, [0, 1, 2]))
+    assert np.all(st[batch.kind == W.KIND_INFEASIBLE] == lpb.LP_INFEASIBLE)
+    assert np.all(st[batch.kind == W.KIND_UNBOUNDED] == lpb.LP_UNBOUNDED)
+    # primal feasibility of every optimal LP
+    A = batch.A.reshape(-1, 50, 50)
+    b = batch.b.reshape(-1, 50)
+    c = batch.c.reshape(-1, 50)
+    x = g["x"].reshape(-1, 50)
+    opt = st == lpb.LP_OPTIMAL
+    viol = np.einsum("kij,kj->ki", A[opt], x[opt]) - b[opt]
+    assert viol.max() <= 1e-8
+    assert x[opt].min() >= -1e-9
+    # objective equals c^T x
+    np.testing.assert_allclose(np.einsum("kj,kj->k", c[opt], x[opt]), g["obj"][opt], rtol=1e-9, atol=1e-9)
