@@ -9,6 +9,7 @@
 // stream; lp_batch_results copies the outputs.
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -77,6 +78,14 @@ struct Group {
     int32_t threads;
     size_t smem;
 };
+
+// Bound of Step 1's tie window in key units: ceil(tau * 2^54 * (1 + 2^-30)) + 4
+// (covers tau*2^54*(1+2^-53) + 1.5, see step1_window in the kernel); -1 when
+// tau is too large for the single-binade argument (tau > 2^-33).
+long long step1_key_window(double tau) {
+    if (!(tau <= std::ldexp(1.0, -33))) return -1;
+    return (long long)std::ceil(tau * std::ldexp(1.0, 54) * (1.0 + std::ldexp(1.0, -30))) + 4;
+}
 
 int pick_threads(int m, int n, int k, int requested) {
     if (requested > 0) return std::min(std::max(32, (requested + 31) / 32 * 32), lpb::kMaxThreads);
@@ -202,7 +211,12 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     h->num_lps = num_lps;
     h->total_x = px;
     h->total_y = py;
-    h->tol = {o.eps_opt, o.eps_piv, o.eps_feas, o.tau, o.max_iters};
+    // FP32 ratio screen of Step 2: a window far wider than the float rounding
+    // error of the screened ratios (< 8 * 2^-24 relative) and than the tie
+    // window (tau relative, or tau absolute below 1).
+    const float ratio_rel = (float)std::max(std::ldexp(1.0, -12), 8.0 * o.tau);
+    const float ratio_abs = (float)std::max(std::ldexp(1.0, -20), 8.0 * o.tau);
+    h->tol = {o.eps_opt, o.eps_piv, o.eps_feas, o.tau, o.max_iters, step1_key_window(o.tau), ratio_rel, ratio_abs};
     h->last_stream = s;
 
     auto bail = [&](lpb_err e, const std::string& msg) {

@@ -15,7 +15,15 @@
 //    touched only to read A, b, c and write the results;
 //  - reductions are warp `redux` instructions on 64-bit order-preserving
 //    integer keys of the FP64 values (exact, no FP64-pipe compares);
-//  - phase I runs in the same kernel (the paper launches twice, Section 5).
+//  - phase I runs in the same kernel (the paper launches twice, Section 5);
+//  - Steps 1 and 2 screen their candidates without FP64 arithmetic (the FP64
+//    pipe of GB300 is ~60x slower than FP32 and a warp FP64 instruction costs
+//    the whole warp's pipe time whatever its active mask): Step 1 bounds the tie
+//    window of the minimum reduced cost in units of the integer key, Step 2
+//    bounds the ratios in FP32 with a window wider than every FP32 rounding
+//    error.  When the screen leaves exactly one candidate it is the exact
+//    answer; otherwise the exact FP64 rule runs on the candidates.  The result
+//    is the same as the plain rule's in every case.
 //
 // Arithmetic is the oracle's, operation for operation, so that both reach the
 // same pivot sequence: ratio = rhs / t (IEEE divide), pivot row = row / PE
@@ -60,13 +68,41 @@ __device__ __forceinline__ long long warp_min_i64(long long v) {
     return (long long)(((unsigned long long)(unsigned)mhi << 32) | (unsigned long long)mlo);
 }
 
-// Block-wide minima.  `scratch` alternates between two halves so that a
-// buffer is never rewritten before every thread has read it.
+// Float order key (int32): a < b <=> fkey(a) < fkey(b); -0 and +0 map alike.
+__device__ __forceinline__ int fkey(float f) {
+    int b = __float_as_int(f);
+    b = (b == INT_MIN) ? 0 : b;
+    return b ^ ((b >> 31) & INT_MAX);
+}
+__device__ __forceinline__ float fval(int k) { return __int_as_float(k ^ ((k >> 31) & INT_MAX)); }
+
+// Unbiased binary exponent of a double from its bits (-1023 for 0 and subnormals).
+__device__ __forceinline__ int dexp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF) - 1023; }
+
+// Upper bound, in units of okey, of okey(thr) - okey(v) where thr is the tie
+// threshold v + tau*max(1,|v|) of a negative v (Step 1).  `wb` >=
+// tau*2^54*(1+2^-53) + 1.5 is precomputed on the host (< 0: no bound).  The
+// interval (v, thr] lies in v's binade or the one below (tau|v| < |v|/2), where
+// doubles are spaced at least 2^(E-53) apart, E = exponent of v:
+//   E >= 0: thr - v <= tau*2^(E+1)*(1+2^-53) + half an ulp  -> <= wb keys;
+//   E <  0: thr - v <= tau*(1+2^-53) + half an ulp          -> <= wb << (-E-1).
+__device__ __forceinline__ unsigned long long step1_window(long long kmin, long long wb) {
+    if (wb < 0) return ~0ull;
+    const int E = dexp(kval(kmin));
+    if (E >= 0) return (unsigned long long)wb;
+    const int sh = -E - 1;
+    if (sh > 30) return ~0ull;
+    return (unsigned long long)wb << sh;
+}
+
+// Block-wide reductions.  Each kind of buffer alternates between two halves
+// so that a buffer is never rewritten before every thread has read it (two
+// uses of the same half are always separated by another barrier).
 struct Reducer {
-    long long* s64;
-    unsigned* s32;
+    long long* s64;   // 2 x kMaxWarps
+    unsigned* s32;    // 6 x kMaxWarps: 2 min buffers, 2 pair-min buffers, 2 pair-count buffers
     int nw, warp, lane;
-    int b64 = 0, b32 = 0;
+    int b64 = 0, b32 = 0, bp = 0;
 
     __device__ long long min_i64(long long v) {
         v = warp_min_i64(v);
@@ -87,6 +123,23 @@ struct Reducer {
         unsigned r = s[0];
         for (int w = 1; w < nw; ++w) r = min(r, s[w]);
         return r;
+    }
+    __device__ int min_i32(int v) {
+        return (int)(min_u32((unsigned)v ^ 0x80000000u) ^ 0x80000000u);
+    }
+    // Block-wide (sum of cnt, min of v) behind a single barrier.
+    __device__ void count_min(unsigned cnt, unsigned v, unsigned& cnt_out, unsigned& v_out) {
+        cnt = __reduce_add_sync(kFull, cnt);
+        v = __reduce_min_sync(kFull, v);
+        unsigned* sv = s32 + (2 + bp) * kMaxWarps;
+        unsigned* sc = s32 + (4 + bp) * kMaxWarps;
+        bp ^= 1;
+        if (lane == 0) { sv[warp] = v; sc[warp] = cnt; }
+        __syncthreads();
+        unsigned c = 0, r = 0xffffffffu;
+        for (int w = 0; w < nw; ++w) { c += sc[w]; r = min(r, sv[w]); }
+        cnt_out = c;
+        v_out = r;
     }
 };
 
@@ -297,41 +350,91 @@ fp64_resident_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* _
             phase = 2;
             continue;
         }
-        long long kthr = 0;
-        if (lane == 0) kthr = okey(tie_threshold(kval(dmin), tol.tau));
-        kthr = __shfl_sync(kFull, kthr, 0);
-        unsigned esel = 0xffffffffu;
+        // screen: columns whose key lies within the tie-window bound of dmin
+        const unsigned long long win = step1_window(dmin, tol.key_window);
+        unsigned ecnt = 0, esel = 0xffffffffu;
         for (int j = 1 + tid; j <= Cvar; j += nt) {
             const int v = tb.col_var[j];
-            if (v < nm && okey(Trow[j]) <= kthr) esel = min(esel, ((unsigned)v << 16) | (unsigned)j);
+            if (v < nm && (unsigned long long)okey(Trow[j]) - (unsigned long long)dmin <= win) {
+                ++ecnt;
+                esel = min(esel, ((unsigned)v << 16) | (unsigned)j);
+            }
         }
-        esel = red.min_u32(esel);
+        red.count_min(ecnt, esel, ecnt, esel);
+        if (ecnt > 1) {
+            // several candidates: the exact rule (lowest label within the window)
+            const long long kthr = okey(tie_threshold(kval(dmin), tol.tau));
+            unsigned sel = 0xffffffffu;
+            for (int j = 1 + tid; j <= Cvar; j += nt) {
+                const int v = tb.col_var[j];
+                if (v < nm && okey(Trow[j]) <= kthr) sel = min(sel, ((unsigned)v << 16) | (unsigned)j);
+            }
+            esel = red.min_u32(sel);
+        }
         const int e = (int)(esel & 0xffffu);
 
         // ---- Step 2: leaving row (minimum ratio rhs_i / t_ie, t_ie > eps) --
-        long long rloc = LLONG_MAX;
+        // FP32 screen: rows with both operands in [2^-100, 2^100] (or rhs 0)
+        // get a float ratio; the others are always candidates.
+        int floc = INT_MAX;
         for (int i = tid; i < Ract; i += nt) {
             const double t = T[(size_t)i * LD + e];
             tb.colE[i] = t;
             if (i < m) {
-                long long rk = LLONG_MAX;
-                if (okey(t) > key_eps_piv) rk = okey(__ddiv_rn(T[(size_t)i * LD], t));
-                rkey[i] = rk;
-                rloc = min(rloc, rk);
+                long long code = LLONG_MAX;  // not eligible
+                if (okey(t) > key_eps_piv) {
+                    const double beta = T[(size_t)i * LD];
+                    const int et = dexp(t), eb = dexp(beta);
+                    const bool safe = et >= -100 && et <= 100 && (abskey(beta) == 0 || (eb >= -100 && eb <= 100));
+                    if (safe) {
+                        const int fk = fkey(__fdividef(__double2float_rn(beta), __double2float_rn(t)));
+                        code = fk;
+                        floc = min(floc, fk);
+                    } else {
+                        code = LLONG_MIN;  // unscreened: always a candidate
+                    }
+                }
+                rkey[i] = code;
             }
         }
-        const long long rmin = red.min_i64(rloc);
-        if (rmin == LLONG_MAX) {
+        const int fmin = red.min_i32(floc);
+        long long fwin = LLONG_MIN;
+        if (fmin != INT_MAX) {
+            const float fm = fval(fmin);
+            fwin = fkey(fm + __fmaf_rn(tol.ratio_rel, fabsf(fm), tol.ratio_abs));
+        }
+        unsigned lcnt = 0, lsel = 0xffffffffu;
+        for (int i = tid; i < m; i += nt) {
+            const long long code = rkey[i];
+            if (code == LLONG_MIN || (code != LLONG_MAX && code <= fwin)) {
+                ++lcnt;
+                lsel = min(lsel, (unsigned)i);
+            }
+        }
+        red.count_min(lcnt, lsel, lcnt, lsel);
+        if (lcnt == 0) {
             status = (phase == 2) ? kUnbounded : kNumerical;
             break;
         }
-        long long rthr = 0;
-        if (lane == 0) rthr = okey(tie_threshold(kval(rmin), tol.tau));
-        rthr = __shfl_sync(kFull, rthr, 0);
-        unsigned lsel = 0xffffffffu;
-        for (int i = tid; i < m; i += nt)
-            if (rkey[i] <= rthr) lsel = min(lsel, (unsigned)i);
-        const int l = (int)red.min_u32(lsel);
+        if (lcnt > 1) {
+            // several candidates: exact ratios of the candidates, exact rule
+            long long rloc = LLONG_MAX;
+            for (int i = tid; i < m; i += nt) {
+                const long long code = rkey[i];
+                long long rk = LLONG_MAX;
+                if (code == LLONG_MIN || (code != LLONG_MAX && code <= fwin))
+                    rk = okey(__ddiv_rn(T[(size_t)i * LD], tb.colE[i]));
+                rkey[i] = rk;
+                rloc = min(rloc, rk);
+            }
+            const long long rmin = red.min_i64(rloc);
+            const long long rthr = okey(tie_threshold(kval(rmin), tol.tau));
+            unsigned sel = 0xffffffffu;
+            for (int i = tid; i < m; i += nt)
+                if (rkey[i] <= rthr) sel = min(sel, (unsigned)i);
+            lsel = red.min_u32(sel);
+        }
+        const int l = (int)lsel;
         if (abskey(tb.colE[l]) >= 0x7FF0000000000000LL) { status = kNumerical; break; }
         if (iters >= max_iters) { status = kIterLimit; break; }
 

@@ -35,6 +35,13 @@ struct Tolerances {
     double eps_feas;
     double tau;
     int32_t max_iters;  // <= 0: 50*(m+n)
+    // Screening windows derived from tau on the host (see tie_screen_* in
+    // lp_api.cu): an upper bound on the tie window of Step 1 in units of the
+    // FP64 key (< 0: always take the exact FP64 path), and the relative /
+    // absolute FP32 windows of the Step 2 ratio screen.
+    long long key_window;
+    float ratio_rel;
+    float ratio_abs;
 };
 
 // Per-LP outcome codes (same values as lp_status in include/lpbatch.h).
@@ -65,7 +72,7 @@ __host__ __device__ inline ResidentLayout resident_layout(int m, int n, int k) {
     size_t o = 0;
     L.red64 = o;   o += 2 * kMaxWarps * sizeof(long long);
     L.rkey = o;    o += align16((size_t)m * sizeof(long long));
-    L.red32 = o;   o += 2 * kMaxWarps * sizeof(unsigned);
+    L.red32 = o;   o += 6 * kMaxWarps * sizeof(unsigned);  // 2 min buffers + 2 (count, min) buffers
     L.row_var = o; o += align16((size_t)m * sizeof(int));
     L.neg = o;     o += align16((size_t)m * sizeof(int));
     L.T = o;       o += align16((size_t)L.R * (size_t)L.LD * sizeof(double));

@@ -187,3 +187,38 @@ def test_full_size_dense50x50_100k_sampled():
     assert x[opt].min() >= -1e-9
     # objective equals c^T x
     np.testing.assert_allclose(np.einsum("kj,kj->k", c[opt], x[opt]), g["obj"][opt], rtol=1e-9, atol=1e-9)
+
+
+def test_screen_rare_paths_extreme_magnitudes():
+    """Rows whose right-hand side or pivot-column entry lies outside
+    [2^-100, 2^100] skip the FP32 ratio screen; LPs with exactly equal
+    reduced costs / ratios take the exact FP64 tie path."""
+    rng = np.random.default_rng(77)
+    lps = []
+    for t in range(120):
+        m, n = int(rng.integers(2, 20)), int(rng.integers(2, 20))
+        A = rng.uniform(-1, 1, (m, n))
+        b = rng.uniform(-0.5, 2, m)
+        c = rng.uniform(-1, 1, n)
+        s = [1e35, 1e-35, 1e200, 1e-200][t % 4]
+        if t % 3 == 0:
+            b = b * s
+        elif t % 3 == 1:
+            A = A * s
+        else:
+            A = np.round(A * 3)
+            b = np.round(b * 3)
+            c = np.round(c * 3)
+        lps.append((A, b, c))
+    batch = W.pack("extreme", lps)
+    g, r, n, bitwise = _check(batch)
+    assert bitwise == n
+
+
+@pytest.mark.parametrize("tau", [0.0, 1e-9, 1e-3])
+def test_tie_window_settings(tau):
+    from test_oracle_pins import tiny_lps
+    lps = tiny_lps(31, 300) + [W.mixed_sign_dense(200, 20, 20, start=5).lp(k) for k in range(200)]
+    batch = W.pack("tau", lps)
+    g, r, n, bitwise = _check(batch, opts=lpb.lpb_default_opts(tau=tau))
+    assert bitwise == n
