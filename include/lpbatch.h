@@ -72,9 +72,13 @@ typedef struct {
     double eps_piv;      /* default 1e-9                                          */
     double eps_feas;     /* default 1e-9                                          */
     double tau;          /* relative tie window, default 1e-12                    */
-    int32_t block_threads; /* threads per LP; 0 = chosen from the LP size        */
-    int32_t reserved;
+    int32_t block_threads; /* threads per LP of the resident kernel; 0 = from the LP size */
+    int32_t schedule;    /* LPB_SCHED_AUTO or LPB_SCHED_STREAMED                   */
 } lp_batch_opts;
+
+/* Kernel choice.  AUTO: shared-memory-resident tableau when it fits in one
+ * CTA, global workspace otherwise.  STREAMED: global workspace for every LP. */
+enum { LPB_SCHED_AUTO = 0, LPB_SCHED_STREAMED = 1 };
 
 typedef struct lp_batch lp_batch;   /* opaque; owned by the library */
 
@@ -119,8 +123,11 @@ lpb_err lp_batch_create(lp_batch **out, int32_t num_lps,
  * Solve every LP of the batch on `stream` (cudaStream_t; NULL = legacy
  * default stream).  Asynchronous: returns after the kernels are enqueued.
  * Builds each tableau on the device from the uploaded A, b, c and runs
- * Steps 1-3 until every LP halts (Section 3.1).  May be called again (each
- * call solves from scratch).
+ * Steps 1-3 until every LP halts (Section 3.1).  Tableaux that fit in one
+ * CTA's shared memory stay there for the whole solve; larger ones are kept
+ * in a library-owned global workspace (allocated by lp_batch_create).  May be
+ * called again (each call solves from scratch); calls on one handle must not
+ * overlap on the GPU (they share the workspace).
  */
 lpb_err lp_batch_solve(lp_batch *h, void *stream);
 
@@ -139,10 +146,18 @@ lpb_err lp_batch_solve(lp_batch *h, void *stream);
 lpb_err lp_batch_results(lp_batch *h, int32_t *status, int32_t *iters, double *obj,
                          double *x, double *y, int32_t ptr_kind);
 
-/* Plan of the batch: number of launch groups, largest shared-memory
- * footprint in bytes, and number of LPs with a phase I.  Any pointer may be NULL. */
-lpb_err lp_batch_plan_info(const lp_batch *h, int32_t *num_groups, int64_t *max_smem_bytes,
-                           int32_t *num_phase1);
+/* Launch plan of a batch (filled by lp_batch_plan_info). */
+typedef struct {
+    int32_t num_groups;        /* kernel launches per solve                         */
+    int32_t num_resident;      /* LPs whose tableau stays in one CTA's shared memory */
+    int32_t num_streamed;      /* LPs whose tableau lives in a global workspace      */
+    int32_t num_phase1;        /* LPs with some b_i < 0                              */
+    int64_t max_smem_bytes;    /* largest shared-memory footprint of a launch        */
+    int64_t workspace_bytes;   /* global workspace of the streamed LPs               */
+} lp_batch_plan;
+
+/* Report the launch plan made by lp_batch_create. */
+lpb_err lp_batch_plan_info(const lp_batch *h, lp_batch_plan *plan);
 
 /* Free the batch (waits for its pending work).  NULL is accepted. */
 lpb_err lp_batch_destroy(lp_batch *h);

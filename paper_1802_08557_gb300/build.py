@@ -26,7 +26,7 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcom
                  "-I", INCLUDE, "-I", CSRC]
 # FP64 kernels must not contract a*b+c: their arithmetic mirrors the oracle op by op.
 PER_FILE = {
-    "lp_fp64_resident.cu": ["--fmad=false"],
+    "lp_fp64_simplex.cu": ["--fmad=false"],
 }
 
 

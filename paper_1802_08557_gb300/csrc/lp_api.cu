@@ -87,6 +87,9 @@ long long step1_key_window(double tau) {
     return (long long)std::ceil(tau * std::ldexp(1.0, 54) * (1.0 + std::ldexp(1.0, -30))) + 4;
 }
 
+// Cap of the streamed kernel's global workspace (slots x largest tableau).
+constexpr int64_t kMaxWorkspaceBytes = int64_t(16) << 30;
+
 int pick_threads(int m, int n, int k, int requested) {
     if (requested > 0) return std::min(std::max(32, (requested + 31) / 32 * 32), lpb::kMaxThreads);
     const int64_t e = (int64_t)(m + 1 + (k > 0)) * (n + k + 1);
@@ -113,6 +116,13 @@ struct lp_batch {
     bool solved = false;
     int32_t num_phase1 = 0;
     size_t max_smem = 0;
+    // streamed LPs: order[streamed_offset ...), persistent CTAs over slots
+    int64_t streamed_offset = 0;
+    int32_t num_streamed = 0;
+    int32_t streamed_slots = 0;
+    size_t slot_bytes = 0;
+    unsigned char* workspace = nullptr;
+    int32_t* counter = nullptr;
 };
 
 namespace {
@@ -178,6 +188,7 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     lpb_default_opts(&o);
     if (opts) o = *opts;
     if (o.precision != LP_PREC_FP64) return fail(LPB_EINVAL, "unsupported precision");
+    if (o.schedule != LPB_SCHED_AUTO && o.schedule != LPB_SCHED_STREAMED) return fail(LPB_EINVAL, "unknown schedule");
     if (!(o.eps_opt >= 0) || !(o.eps_piv >= 0) || !(o.eps_feas >= 0) || !(o.tau >= 0))
         return fail(LPB_EINVAL, "tolerances must be >= 0");
 
@@ -272,18 +283,22 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         return bail_cuda(err, "input check");
     if (bad) return bail(LPB_EINVAL, std::to_string(bad) + " non-finite entries in A, b or c");
 
-    // Plan: group LPs by (threads per CTA, shared-memory footprint rounded
-    // up to 4 KiB); one launch per group.
+    // Plan: LPs whose tableau fits in one CTA's shared memory are grouped by
+    // (threads per CTA, footprint rounded up to 4 KiB), one launch per group;
+    // the others go to the streamed kernel (global workspace slots).
     std::map<std::pair<int, size_t>, std::vector<int32_t>> buckets;
+    std::vector<int32_t> streamed;
     for (int32_t k = 0; k < num_lps; ++k) {
-        const lpb::ResidentLayout L = lpb::resident_layout(hm[k], hn[k], hk[k]);
-        if (L.total > lpb::kMaxSmemPerBlock)
-            return bail(LPB_ETOOBIG, "LP " + std::to_string(k) + ": tableau of " + std::to_string(L.total) +
-                                         " bytes exceeds the shared-memory budget");
-        const size_t smem = std::min(lpb::kMaxSmemPerBlock, (L.total + 4095) / 4096 * 4096);
+        const size_t need = lpb::resident_smem_bytes(hm[k], hn[k], hk[k]);
+        h->num_phase1 += hk[k] > 0;
+        if (need > lpb::kMaxSmemPerBlock || o.schedule == LPB_SCHED_STREAMED) {
+            streamed.push_back(k);
+            h->slot_bytes = std::max(h->slot_bytes, lpb::streamed_slot_bytes(hm[k], hn[k], hk[k]));
+            continue;
+        }
+        const size_t smem = std::min(lpb::kMaxSmemPerBlock, (need + 4095) / 4096 * 4096);
         const int threads = pick_threads(hm[k], hn[k], hk[k], o.block_threads);
         buckets[{threads, smem}].push_back(k);
-        h->num_phase1 += hk[k] > 0;
         h->max_smem = std::max(h->max_smem, smem);
     }
     std::vector<int32_t> order;
@@ -297,8 +312,22 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         order.insert(order.end(), kv.second.begin(), kv.second.end());
         h->groups.push_back(g);
     }
+    h->streamed_offset = (int64_t)order.size();
+    h->num_streamed = (int32_t)streamed.size();
+    order.insert(order.end(), streamed.begin(), streamed.end());
+    if (h->num_streamed > 0) {
+        int sms = 0;
+        if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device)))
+            return bail_cuda(err, "device query");
+        int64_t slots = (int64_t)sms * lpb::fp64_streamed_ctas_per_sm();
+        const int64_t cap = std::max<int64_t>(1, kMaxWorkspaceBytes / (int64_t)h->slot_bytes);
+        slots = std::min<int64_t>({slots, (int64_t)h->num_streamed, cap});
+        h->streamed_slots = (int32_t)slots;
+        if ((err = alloc(h, &h->workspace, (size_t)slots * h->slot_bytes, s)) || (err = alloc(h, &h->counter, 1, s)))
+            return bail_cuda(err, "streamed workspace allocation");
+    }
     if ((err = cudaMemcpyAsync(dorder, order.data(), nl * 4, cudaMemcpyHostToDevice, s)) ||
-        (err = lpb::fp64_resident_prepare()) || (err = cudaStreamSynchronize(s)))
+        (err = lpb::fp64_kernels_prepare()) || (err = cudaStreamSynchronize(s)))
         return bail_cuda(err, "plan upload");
     *out = h;
     return LPB_OK;
@@ -313,6 +342,11 @@ lpb_err lp_batch_solve(lp_batch* h, void* stream) {
         cudaError_t err = lpb::launch_fp64_resident(h->d, h->tol, h->d_order + g.offset, g.count, g.threads,
                                                     g.smem, s);
         if (err != cudaSuccess) return cuda_fail(err, "solver launch");
+    }
+    if (h->num_streamed > 0) {
+        cudaError_t err = lpb::launch_fp64_streamed(h->d, h->tol, h->d_order + h->streamed_offset, h->num_streamed,
+                                                    h->streamed_slots, h->workspace, h->slot_bytes, h->counter, s);
+        if (err != cudaSuccess) return cuda_fail(err, "streamed solver launch");
     }
     h->last_stream = s;
     h->solved = true;
@@ -339,11 +373,14 @@ lpb_err lp_batch_results(lp_batch* h, int32_t* status, int32_t* iters, double* o
     return LPB_OK;
 }
 
-lpb_err lp_batch_plan_info(const lp_batch* h, int32_t* num_groups, int64_t* max_smem_bytes, int32_t* num_phase1) {
-    if (!h) return fail(LPB_EINVAL, "handle is NULL");
-    if (num_groups) *num_groups = (int32_t)h->groups.size();
-    if (max_smem_bytes) *max_smem_bytes = (int64_t)h->max_smem;
-    if (num_phase1) *num_phase1 = h->num_phase1;
+lpb_err lp_batch_plan_info(const lp_batch* h, lp_batch_plan* plan) {
+    if (!h || !plan) return fail(LPB_EINVAL, "handle or plan is NULL");
+    plan->num_groups = (int32_t)h->groups.size() + (h->num_streamed > 0 ? 1 : 0);
+    plan->num_resident = h->num_lps - h->num_streamed;
+    plan->num_streamed = h->num_streamed;
+    plan->num_phase1 = h->num_phase1;
+    plan->max_smem_bytes = (int64_t)h->max_smem;
+    plan->workspace_bytes = (int64_t)h->streamed_slots * (int64_t)h->slot_bytes;
     return LPB_OK;
 }
 

@@ -1,5 +1,8 @@
-// lp_fp64_resident.cu -- FP64 dense simplex with the tableau resident in
-// shared memory, one CTA per LP.
+// lp_fp64_simplex.cu -- FP64 dense simplex, one CTA per LP: the tableau is
+// resident in shared memory when it fits (fp64_resident_kernel) and streamed
+// through a global-memory workspace slot otherwise (fp64_streamed_kernel,
+// persistent CTAs taking LPs from an atomic counter).  Both run the same
+// per-LP code (solve_one).
 //
 // Method: Gurung & Ray, "Simultaneous Solving of Batched Linear Programs on a
 // GPU" (arXiv 1802.08557).  Section 4.1 assigns one CUDA block per LP; Section
@@ -206,11 +209,13 @@ __device__ __forceinline__ void retire_column(Tab& tb, int Ract, int e, int& Cva
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kMaxThreads)
-fp64_resident_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order)
+// One LP, Steps 1-3 until it halts.  `small` is shared memory
+// (SmallLayout); `big` is shared memory (resident) or a global workspace slot
+// (streamed), laid out by big_layout.
+template <bool kStreamed>
+__device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances& tol, const int lp,
+                                          unsigned char* small, unsigned char* big)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lp = order[blockIdx.x];
     const int m = B.m[lp];
     const int n = B.n[lp];
     const int nm = n + m;
@@ -221,12 +226,12 @@ fp64_resident_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* _
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
 
     // k-independent part of the layout (k = 0 gives the same offsets)
-    const ResidentLayout L0 = resident_layout(m, n, 0);
-    Reducer red{reinterpret_cast<long long*>(smem + L0.red64), reinterpret_cast<unsigned*>(smem + L0.red32),
-                nw, warp, lane};
-    long long* rkey = reinterpret_cast<long long*>(smem + L0.rkey);
-    int* row_var = reinterpret_cast<int*>(smem + L0.row_var);
-    int* neg = reinterpret_cast<int*>(smem + L0.neg);
+    const BigLayout L0 = big_layout(m, n, 0, kStreamed);
+    Reducer red{reinterpret_cast<long long*>(small + SmallLayout::red64),
+                reinterpret_cast<unsigned*>(small + SmallLayout::red32), nw, warp, lane};
+    long long* rkey = reinterpret_cast<long long*>(big + L0.rkey);
+    int* row_var = reinterpret_cast<int*>(big + L0.row_var);
+    int* neg = reinterpret_cast<int*>(big + L0.neg);
 
     // ---- Tableau build (the host-side fill of Section 4.1, done here) -----
     // Rows with b_i < 0 are negated and get an artificial (two-phase method,
@@ -257,11 +262,11 @@ fp64_resident_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* _
         __syncthreads();
     }
 
-    const ResidentLayout L = resident_layout(m, n, k);
+    const BigLayout L = big_layout(m, n, k, kStreamed);
     Tab tb;
-    tb.T = reinterpret_cast<double*>(smem + L.T);
-    tb.colE = reinterpret_cast<double*>(smem + L.colE);
-    tb.col_var = reinterpret_cast<int*>(smem + L.col_var);
+    tb.T = reinterpret_cast<double*>(big + L.T);
+    tb.colE = reinterpret_cast<double*>(big + L.colE);
+    tb.col_var = reinterpret_cast<int*>(big + L.col_var);
     tb.row_var = row_var;
     tb.LD = L.LD;
     const int LD = L.LD;
@@ -466,11 +471,55 @@ fp64_resident_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* _
     }
 }
 
+__global__ void __launch_bounds__(kMaxThreads)
+fp64_resident_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    solve_one<false>(B, tol, order[blockIdx.x], smem, smem + SmallLayout::total);
+}
+
+__global__ void __launch_bounds__(kStreamedThreads, 2)
+fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order,
+                     const int32_t count, unsigned char* __restrict__ workspace, const size_t slot_bytes,
+                     int32_t* __restrict__ counter)
+{
+    __shared__ __align__(16) unsigned char small[SmallLayout::total];
+    __shared__ int next;
+    unsigned char* big = workspace + (size_t)blockIdx.x * slot_bytes;
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int idx = next;
+        __syncthreads();
+        if (idx >= count) break;
+        solve_one<true>(B, tol, order[idx], small, big);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
-cudaError_t fp64_resident_prepare() {
+cudaError_t fp64_kernels_prepare() {
     return cudaFuncSetAttribute(fp64_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kMaxSmemPerBlock);
+}
+
+int fp64_streamed_ctas_per_sm() {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fp64_streamed_kernel, kStreamedThreads, 0) != cudaSuccess)
+        return 1;
+    return blocks > 0 ? blocks : 1;
+}
+
+cudaError_t launch_fp64_streamed(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
+                                 int32_t count, int slots, unsigned char* workspace, size_t slot_bytes,
+                                 int32_t* counter, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
+    if (err != cudaSuccess) return err;
+    fp64_streamed_kernel<<<slots, kStreamedThreads, 0, stream>>>(B, tol, order, count, workspace, slot_bytes,
+                                                                  counter);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fp64_resident(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,

@@ -51,28 +51,37 @@ constexpr int kMaxThreads = 512;
 constexpr int kMaxWarps = kMaxThreads / 32;
 constexpr size_t kMaxSmemPerBlock = 227 * 1024;  // opt-in dynamic shared memory per CTA on sm_103
 
-// Shared-memory layout of the SMEM-resident FP64 kernel for an LP with m
-// rows, n structural columns and k rows with b_i < 0 (k artificials).  The
-// k-independent arrays come first so the kernel can place them before it
-// has counted k.  Condensed tableau: R = m+1 (+1 phase-I row) rows, LD >=
-// n+k+1 columns (column 0 = right-hand side, then the non-basic variables).
-struct ResidentLayout {
+// Per-LP working storage of the FP64 simplex kernels.  The small part
+// (reduction scratch) is always in shared memory.  The big part holds the
+// condensed (Tucker) tableau -- R = m+1 (+1 phase-I row) rows x LD >= n+k+1
+// columns, column 0 = right-hand side, then the non-basic variables -- plus
+// per-row / per-column arrays.  It lives in shared memory for the resident
+// kernel and in a global-memory workspace slot for the streamed kernel.  The
+// k-independent arrays come first, so the kernel can place them before it has
+// counted the k rows with b_i < 0.
+struct SmallLayout {
+    static constexpr size_t red64 = 0;                                   // 2 x kMaxWarps int64
+    static constexpr size_t red32 = red64 + 2 * kMaxWarps * 8;           // 6 x kMaxWarps uint32
+    static constexpr size_t total = red32 + 6 * kMaxWarps * 4;
+};
+
+struct BigLayout {
     int R, LD;
-    size_t red64, rkey, red32, row_var, neg;   // k-independent
-    size_t T, colE, col_var;                   // k-dependent
+    size_t rkey, row_var, neg;   // k-independent
+    size_t T, colE, col_var;     // k-dependent
     size_t total;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-__host__ __device__ inline ResidentLayout resident_layout(int m, int n, int k) {
-    ResidentLayout L;
+// streamed = false: odd row stride (column reads hit distinct shared-memory
+// banks); streamed = true: rows padded to 32 bytes (aligned global sectors).
+__host__ __device__ inline BigLayout big_layout(int m, int n, int k, bool streamed) {
+    BigLayout L;
     L.R = m + 1 + (k > 0 ? 1 : 0);
-    L.LD = (n + k + 1) | 1;  // odd stride: column reads hit distinct banks
+    L.LD = streamed ? ((n + k + 1 + 3) & ~3) : ((n + k + 1) | 1);
     size_t o = 0;
-    L.red64 = o;   o += 2 * kMaxWarps * sizeof(long long);
     L.rkey = o;    o += align16((size_t)m * sizeof(long long));
-    L.red32 = o;   o += 6 * kMaxWarps * sizeof(unsigned);  // 2 min buffers + 2 (count, min) buffers
     L.row_var = o; o += align16((size_t)m * sizeof(int));
     L.neg = o;     o += align16((size_t)m * sizeof(int));
     L.T = o;       o += align16((size_t)L.R * (size_t)L.LD * sizeof(double));
@@ -82,10 +91,29 @@ __host__ __device__ inline ResidentLayout resident_layout(int m, int n, int k) {
     return L;
 }
 
-// Launchers (lp_fp64_resident.cu).
-cudaError_t fp64_resident_prepare();
+// Dynamic shared memory of the resident kernel for one LP.
+__host__ __device__ inline size_t resident_smem_bytes(int m, int n, int k) {
+    return SmallLayout::total + big_layout(m, n, k, false).total;
+}
+
+// Global workspace bytes of one streamed slot (256-byte aligned).
+__host__ __device__ inline size_t streamed_slot_bytes(int m, int n, int k) {
+    return (big_layout(m, n, k, true).total + 255) & ~size_t(255);
+}
+
+// Launchers (lp_fp64_simplex.cu).
+constexpr int kStreamedThreads = 512;
+cudaError_t fp64_kernels_prepare();
 cudaError_t launch_fp64_resident(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
                                  int32_t count, int threads, size_t smem, cudaStream_t stream);
+// Persistent CTAs (grid = slots) take LPs of `order` from the atomic `counter`
+// (must be 0 at launch); each CTA keeps its tableau in workspace slot
+// blockIdx.x of `slot_bytes` bytes.
+cudaError_t launch_fp64_streamed(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
+                                 int32_t count, int slots, unsigned char* workspace, size_t slot_bytes,
+                                 int32_t* counter, cudaStream_t stream);
+// CTAs of the streamed kernel that fit on one SM.
+int fp64_streamed_ctas_per_sm();
 
 // Checks (lp_api.cu helpers in lp_prepare.cu): counts non-finite values of
 // A, b, c into *bad and the rows with b_i < 0 of every LP into k[].

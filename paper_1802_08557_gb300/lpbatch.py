@@ -20,6 +20,7 @@ LP_OPTIMAL, LP_INFEASIBLE, LP_UNBOUNDED, LP_ITER_LIMIT, LP_NUMERICAL = 0, 1, 2, 
 LPB_OK, LPB_EINVAL, LPB_ENOMEM, LPB_ECUDA, LPB_ETOOBIG, LPB_ENOTSOLVED = 0, 1, 2, 3, 4, 5
 LPB_HOST, LPB_DEVICE = 0, 1
 LP_PREC_FP64 = 0
+LPB_SCHED_AUTO, LPB_SCHED_STREAMED = 0, 1
 LPB_MAX_DIM = 16384
 
 # Every symbol include/lpbatch.h declares.
@@ -36,7 +37,18 @@ class LPBatchOpts(ctypes.Structure):
         ("eps_feas", ctypes.c_double),
         ("tau", ctypes.c_double),
         ("block_threads", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("schedule", ctypes.c_int32),
+    ]
+
+
+class LPBatchPlan(ctypes.Structure):
+    _fields_ = [
+        ("num_groups", ctypes.c_int32),
+        ("num_resident", ctypes.c_int32),
+        ("num_streamed", ctypes.c_int32),
+        ("num_phase1", ctypes.c_int32),
+        ("max_smem_bytes", ctypes.c_int64),
+        ("workspace_bytes", ctypes.c_int64),
     ]
 
 
@@ -79,7 +91,7 @@ def load(path: str | None = None):
         L.lp_batch_solve.restype = ctypes.c_int
         L.lp_batch_results.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i32]
         L.lp_batch_results.restype = ctypes.c_int
-        L.lp_batch_plan_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i32)]
+        L.lp_batch_plan_info.argtypes = [_vp, ctypes.POINTER(LPBatchPlan)]
         L.lp_batch_plan_info.restype = ctypes.c_int
         L.lp_batch_destroy.argtypes = [_vp]
         L.lp_batch_destroy.restype = ctypes.c_int
@@ -161,10 +173,10 @@ def lp_batch_results(h, status=None, iters=None, obj=None, x=None, y=None, ptr_k
            "lp_batch_results")
 
 
-def lp_batch_plan_info(h):
-    g, s, p = _i32(), _i64(), _i32()
-    _check(load().lp_batch_plan_info(h, ctypes.byref(g), ctypes.byref(s), ctypes.byref(p)), "lp_batch_plan_info")
-    return dict(num_groups=g.value, max_smem_bytes=s.value, num_phase1=p.value)
+def lp_batch_plan_info(h) -> dict:
+    p = LPBatchPlan()
+    _check(load().lp_batch_plan_info(h, ctypes.byref(p)), "lp_batch_plan_info")
+    return {name: getattr(p, name) for name, _ in LPBatchPlan._fields_}
 
 
 def lp_batch_destroy(h):

@@ -222,3 +222,36 @@ def test_tie_window_settings(tau):
     batch = W.pack("tau", lps)
     g, r, n, bitwise = _check(batch, opts=lpb.lpb_default_opts(tau=tau))
     assert bitwise == n
+
+
+def test_streamed_kernel_matches_resident_bitwise():
+    """The same LPs through the global-workspace kernel and the shared-memory
+    kernel give identical results (same per-LP code, different storage)."""
+    batch = W.mixed_sign_dense(600, 50, 50, start=1234)
+    a = gpu_solve(batch)
+    b = gpu_solve(batch, opts=lpb.lpb_default_opts(schedule=lpb.LPB_SCHED_STREAMED))
+    assert b["plan"]["num_streamed"] == batch.num_lps and b["plan"]["workspace_bytes"] > 0
+    assert a["plan"]["num_streamed"] == 0
+    for key in ("status", "iters", "obj", "x", "y"):
+        np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+
+
+def test_large_lps_take_the_streamed_path():
+    """Tableaux above one CTA's shared memory (e.g. 500 x 500) are solved in a
+    global workspace; compared with the oracle, phase I included."""
+    rng = np.random.default_rng(8)
+    lps = []
+    for m, n in [(500, 500), (320, 260), (180, 420), (260, 200), (400, 90)]:
+        A = rng.uniform(0, 1, (m, n))
+        b = rng.uniform(1, 100, m)
+        c = rng.uniform(0, 1, n)
+        lps.append((A, b, c))
+    A = rng.uniform(0, 1, (250, 150)); b = rng.uniform(1, 100, 250); b[::25] *= -0.01
+    lps.append((A, b, rng.uniform(0, 1, 150)))                         # phase I, streamed
+    lps.append((rng.uniform(-1, 1, (300, 300)), rng.uniform(-5, 10, 300), rng.uniform(-1, 1, 300)))
+    lps += [W.mixed_sign_dense(30, 40, 40, start=9).lp(k) for k in range(30)]  # resident ones alongside
+    batch = W.pack("large", lps)
+    g, r, n, bitwise = _check(batch)
+    assert g["plan"]["num_streamed"] == 7
+    assert g["plan"]["num_resident"] == 30
+    assert bitwise == n
