@@ -159,6 +159,43 @@ typedef struct {
 /* Report the launch plan made by lp_batch_create. */
 lpb_err lp_batch_plan_info(const lp_batch *h, lp_batch_plan *plan);
 
+/*
+ * Solve a batch of LPs that all have the same size m x n without allocating
+ * any memory.  There is no counterpart in the paper: it is for callers that
+ * must not allocate while they run -- code that hands all device memory to its
+ * own pool, loops that cannot afford cudaMalloc/cudaFree (both can stall the
+ * whole device), or hosts where no allocator is reachable.  Such a caller
+ * allocates the inputs and outputs once and then calls this as often as it
+ * wants; every call gives the same results as lp_batch_create + lp_batch_solve
+ * + lp_batch_results on the same data.
+ *
+ *  num_lps, m, n  batch size and the common LP size (host values).
+ *  A, b, c        [device] packed: LP k's A (row-major m x n) at k*m*n, its b
+ *                 at k*m, its c at k*n.  Finite values (not checked here).
+ *  status, iters, obj [device, num_lps]; x [device, num_lps*n]; y [device,
+ *                 num_lps*m] or NULL: the outputs of lp_batch_results, packed
+ *                 the same way.
+ *  opts           NULL = defaults (opts->schedule and block_threads are ignored).
+ *  stream         cudaStream_t (NULL = legacy default); the call is
+ *                 asynchronous and returns once the work is enqueued.
+ *
+ * Scratch: a fixed 64 MiB array inside the library, present on every GPU that
+ * loads the library until the process exits.  It holds ~52 bytes per LP plus
+ * at least one tableau workspace of about 8*(m+2)*(n+m+4) bytes; a batch that
+ * does not fit returns LPB_ETOOBIG before any GPU work (e.g. up to ~1.2
+ * million 50 x 50 LPs per call).  The first call on a device looks up the
+ * array's device address (a one-time set-up with that device current); make
+ * that first call before capturing any stream.  All calls share the array, so
+ * calls that overlap on the GPU race and give wrong results: serialise them
+ * (one stream, or wait for the previous call).  Errors are reported by the
+ * return code only (LPB_EINVAL, LPB_ETOOBIG, LPB_ECUDA); lpb_last_error is not
+ * updated, since recording a message would allocate.
+ */
+lpb_err lp_solve_uniform_noalloc(int32_t num_lps, int32_t m, int32_t n,
+                                 const double *A, const double *b, const double *c,
+                                 int32_t *status, int32_t *iters, double *obj, double *x, double *y,
+                                 const lp_batch_opts *opts, void *stream);
+
 /* Free the batch (waits for its pending work).  NULL is accepted. */
 lpb_err lp_batch_destroy(lp_batch *h);
 

@@ -25,7 +25,8 @@ LPB_MAX_DIM = 16384
 
 # Every symbol include/lpbatch.h declares.
 EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_results",
-            "lp_batch_plan_info", "lp_batch_destroy", "lpb_strerror", "lpb_last_error")
+            "lp_batch_plan_info", "lp_batch_destroy", "lpb_strerror", "lpb_last_error",
+            "lp_solve_uniform_noalloc")
 
 
 class LPBatchOpts(ctypes.Structure):
@@ -97,6 +98,9 @@ def load(path: str | None = None):
         L.lp_batch_destroy.restype = ctypes.c_int
         L.lpb_strerror.argtypes = [ctypes.c_int]
         L.lpb_strerror.restype = ctypes.c_char_p
+        L.lp_solve_uniform_noalloc.argtypes = [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                               ctypes.POINTER(LPBatchOpts), _vp]
+        L.lp_solve_uniform_noalloc.restype = ctypes.c_int
         L.lpb_last_error.argtypes = []
         L.lpb_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -177,6 +181,17 @@ def lp_batch_plan_info(h) -> dict:
     p = LPBatchPlan()
     _check(load().lp_batch_plan_info(h, ctypes.byref(p)), "lp_batch_plan_info")
     return {name: getattr(p, name) for name, _ in LPBatchPlan._fields_}
+
+
+def lp_solve_uniform_noalloc(num_lps, m, n, A, b, c, status, iters, obj, x, y=None,
+                             opts: LPBatchOpts | None = None, stream=None) -> int:
+    """Solve equal-size LPs with caller-owned device buffers and no allocation
+    (see include/lpbatch.h).  Returns the lpb_err code (no message is
+    recorded by this entry point)."""
+    return load().lp_solve_uniform_noalloc(int(num_lps), int(m), int(n), _addr(A), _addr(b), _addr(c),
+                                           _addr(status), _addr(iters), _addr(obj), _addr(x), _addr(y),
+                                           ctypes.byref(opts) if opts is not None else None,
+                                           _stream_handle(stream))
 
 
 def lp_batch_destroy(h):
