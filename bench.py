@@ -33,6 +33,8 @@ DEFAULT_WORKLOAD = "dense50x50_phase1_100k"
 # FP64 roofline denominator: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
 # (the GB300's nominal 1.25 TFLOP/s FP64 at the maximum SM clock).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+# FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz.
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -47,6 +49,8 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=20000, help="LPs timed for the CPU oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--precision", default="fp32r", choices=["fp32r", "fp64"],
+                   help="headline path: FP32 tableau + FP64 certificate (default) or plain FP64")
     return p.parse_args()
 
 
@@ -192,51 +196,107 @@ def run_ours(args):
     b = torch.from_numpy(batch.b).to(dev)
     c = torch.from_numpy(batch.c).to(dev)
     stream = torch.cuda.current_stream(dev)
-    h = lpb.lp_batch_create(batch.m, batch.n, batch.a_off, A, batch.b_off, b, batch.c_off, c,
-                            lpb.LPB_DEVICE, None, stream)
-    info = lpb.lp_batch_plan_info(h)
     in_bytes = (A.numel() + b.numel() + c.numel()) * 8
+    head_prec = lpb.LP_PREC_FP32_REFINE if args.precision == "fp32r" else lpb.LP_PREC_FP64
+
+    def create(prec, host=None):
+        opts = lpb.lpb_default_opts(precision=prec)
+        if host is None:
+            return lpb.lp_batch_create(batch.m, batch.n, batch.a_off, A, batch.b_off, b, batch.c_off, c,
+                                       lpb.LPB_DEVICE, opts, stream)
+        return lpb.lp_batch_create(batch.m, batch.n, batch.a_off, host["A"], batch.b_off, host["b"],
+                                   batch.c_off, host["c"], lpb.LPB_HOST, opts, stream)
 
     def barrier():
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    for _ in range(max(3, args.warmup)):
-        lpb.lp_batch_solve(h, stream)
-    torch.cuda.synchronize()
+    def max_over_ranks(v):
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([v], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return v
 
-    start = torch.cuda.Event(enable_timing=True)
-    stop = torch.cuda.Event(enable_timing=True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(dev.index) as clk:
-        time.sleep(0.25)
+    def timed(h, steps, warmup, clocks=False):
+        for _ in range(max(3, warmup)):
+            lpb.lp_batch_solve(h, stream)
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(dev.index) if clocks else None
+        if sampler:
+            sampler.__enter__()
+            time.sleep(0.25)
         start.record(stream)
-        for s in range(args.steps):
+        for s in range(steps):
             ev[s][0].record(stream)
             lpb.lp_batch_solve(h, stream)
             ev[s][1].record(stream)
         stop.record(stream)
         torch.cuda.synchronize()
-    barrier()
-    elapsed_ms = start.elapsed_time(stop)
-    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    clocks = clk.summary()
+        if sampler:
+            sampler.__exit__()
+        barrier()
+        elapsed = max_over_ranks(start.elapsed_time(stop))
+        return elapsed, [e[0].elapsed_time(e[1]) for e in ev], (sampler.summary() if sampler else None)
 
-    res = dict(status=np.zeros(N, np.int32), iters=np.zeros(N, np.int32), obj=np.zeros(N))
-    lpb.lp_batch_results(h, res["status"], res["iters"], res["obj"], None, None, lpb.LPB_HOST)
-    fmas = algorithmic_fmas(batch, res["iters"])
+    def results(h):
+        r = dict(status=np.zeros(N, np.int32), iters=np.zeros(N, np.int32), obj=np.zeros(N))
+        lpb.lp_batch_results(h, r["status"], r["iters"], r["obj"], None, None, lpb.LPB_HOST)
+        return r
+
+    # ---- headline path ----------------------------------------------------
+    h = create(head_prec)
+    info = lpb.lp_batch_plan_info(h)
+    elapsed_ms, step_ms, clocks = timed(h, args.steps, args.warmup, clocks=True)
+    res = results(h)
+    info = lpb.lp_batch_plan_info(h)  # fallback count of the last solve
+    value = N * ws * args.steps / (elapsed_ms * 1e-3)
+
+    # ---- plain FP64 GPU simplex on the same data (the comparison) ----------
+    fp64 = None
+    if head_prec != lpb.LP_PREC_FP64:
+        h64 = create(lpb.LP_PREC_FP64)
+        e64, s64, _ = timed(h64, args.steps, args.warmup)
+        r64 = results(h64)
+        lpb.lp_batch_destroy(h64)
+        opt = r64["status"] == 0
+        rel = np.abs(res["obj"][opt] - r64["obj"][opt]) / np.maximum(1.0, np.abs(r64["obj"][opt]))
+        fp64 = {"value": N * ws * args.steps / (e64 * 1e-3), "unit": "LPs/s", "ms_per_step": e64 / args.steps,
+                "speedup_of_headline": value / (N * ws * args.steps / (e64 * 1e-3)),
+                "status_mismatches": int(np.sum(res["status"] != r64["status"])),
+                "max_rel_obj_err_on_optimal": float(rel.max()) if rel.size else 0.0}
+        fp64_fmas = algorithmic_fmas(batch, r64["iters"])
+        fp64_kernel_ms = statistics.mean(s64)
+        fp64["roofline"] = {"bound": "alu", "kernel": "fp64_resident_kernel",
+                            "achieved": 2.0 * fp64_fmas / (fp64_kernel_ms * 1e-3) / 1e9, "peak": FP64_PEAK_GFLOPS,
+                            "unit": "GFLOP/s",
+                            "frac": 2.0 * fp64_fmas / (fp64_kernel_ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS}
+
     kernel_ms = statistics.mean(step_ms)
-    achieved_gflops = 2.0 * fmas / (kernel_ms * 1e-3) / 1e9
-    total_lps = N * ws * args.steps
-    value = total_lps / (elapsed_ms * 1e-3)
+    if head_prec == lpb.LP_PREC_FP64:
+        fmas = algorithmic_fmas(batch, res["iters"])
+        achieved = 2.0 * fmas / (kernel_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "kernel": "fp64_resident_kernel", "achieved": achieved,
+                    "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+                    "traffic": None,
+                    "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF)",
+                    "work": "sum over LPs of pivots x (m+1)(n+1) FMAs"}
+    else:
+        # FP32 tableau pivots: (m+1)(n+1) FMAs each on the FP32 pipe
+        fmas = algorithmic_fmas(batch, res["iters"])
+        achieved = 2.0 * fmas / (kernel_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "kernel": "mixed_kernel", "achieved": achieved,
+                    "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP32_PEAK_GFLOPS,
+                    "traffic": None,
+                    "peak_note": "FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz",
+                    "work": "sum over LPs of FP32 pivots x (m+1)(n+1) FMAs (FP64 certificate work not counted)"}
 
     # ---- end to end through the C ABI with host buffers ----------------
     e2e = None
@@ -251,8 +311,7 @@ def run_ours(args):
         d2h = sum(v.numel() * v.element_size() for v in out.values())
 
         def e2e_step():
-            hh = lpb.lp_batch_create(batch.m, batch.n, batch.a_off, pinned["A"], batch.b_off, pinned["b"],
-                                     batch.c_off, pinned["c"], lpb.LPB_HOST, None, stream)
+            hh = create(head_prec, host=pinned)
             lpb.lp_batch_solve(hh, stream)
             lpb.lp_batch_results(hh, out["status"], out["iters"], out["obj"], out["x"], None, lpb.LPB_HOST)
             lpb.lp_batch_destroy(hh)
@@ -265,12 +324,7 @@ def run_ours(args):
         for _ in range(e2e_steps):
             e2e_step()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": N * ws * e2e_steps / dt, "unit": "LPs/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
@@ -284,24 +338,27 @@ def run_ours(args):
     lpb.lp_batch_destroy(h)
     if rank == 0:
         counts = np.bincount(res["status"], minlength=5)
+        launches = info["num_groups"]
         line = {
             "metric": METRIC, "value": value, "unit": "LPs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "num_lps_per_gpu": N, "precision": "fp64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head_prec == lpb.LP_PREC_FP64 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "num_lps_per_gpu": N,
+                       "precision": "fp64" if head_prec == lpb.LP_PREC_FP64 else
+                       "fp32 tableau + fp64 certificate (fp64 re-solve of uncertified LPs)",
                        "l2": f"inputs larger than L2 ({in_bytes / 1e9:.2f} GB of A,b,c per step vs 0.13 GB L2)",
-                       "launch_groups": info["num_groups"], "phase1_lps": info["num_phase1"],
+                       "launch_groups": launches, "phase1_lps": info["num_phase1"],
+                       "fp64_fallback_lps": info["num_fallback"],
                        "status_counts": {"optimal": int(counts[0]), "infeasible": int(counts[1]),
                                          "unbounded": int(counts[2]), "iter_limit": int(counts[3]),
                                          "numerical": int(counts[4])},
                        "mean_pivots": float(res["iters"].mean())},
-            "roofline": {"bound": "alu", "kernel": "fp64_resident_kernel", "achieved": achieved_gflops,
-                         "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved_gflops / FP64_PEAK_GFLOPS,
-                         "traffic": None,
-                         "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF)",
-                         "work": "sum over LPs of pivots x (m+1)(n+1) FMAs"},
+            "roofline": roofline,
+            "fp64_plain": fp64,
             "clocks": clocks,
-            "gpu_launches": args.steps * info["num_groups"],
+            "gpu_launches": args.steps * launches,
             "e2e": e2e,
             "cpu_baseline": cpu,
         }

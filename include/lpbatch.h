@@ -61,12 +61,21 @@ typedef enum {
     LPB_ENOTSOLVED = 5  /* results requested before any lp_batch_solve          */
 } lpb_err;
 
-/* Arithmetic of the tableau. */
-enum { LP_PREC_FP64 = 0 };
+/* Arithmetic of the tableau.
+ *  LP_PREC_FP64: FP64 tableau (the paper's double precision, Section 5).
+ *  LP_PREC_FP32_REFINE: FP32 tableau pivots; the basis it ends on is then
+ *    certified in FP64 (refined x_B = B^-1 b and duals from the original A, b,
+ *    c; primal and dual feasibility to 1e-9, duality gap, or a refined
+ *    unbounded ray).  LPs that are not certified, or that end infeasible, at
+ *    the iteration limit or in breakdown, are solved again with the FP64
+ *    tableau.  Reported x, y, obj of certified LPs are FP64 values of the
+ *    certified basis; iters counts the FP32 pivots.  No counterpart in the
+ *    paper. */
+enum { LP_PREC_FP64 = 0, LP_PREC_FP32_REFINE = 1 };
 
 /* Tolerances and limits.  Fill with lpb_default_opts() and then override. */
 typedef struct {
-    int32_t precision;   /* LP_PREC_FP64                                          */
+    int32_t precision;   /* LP_PREC_FP64 (default) or LP_PREC_FP32_REFINE         */
     int32_t max_iters;   /* pivots per LP, both phases; <= 0: 50*(m+n)             */
     double eps_opt;      /* default 1e-9                                          */
     double eps_piv;      /* default 1e-9                                          */
@@ -152,12 +161,21 @@ typedef struct {
     int32_t num_resident;      /* LPs whose tableau stays in one CTA's shared memory */
     int32_t num_streamed;      /* LPs whose tableau lives in a global workspace      */
     int32_t num_phase1;        /* LPs with some b_i < 0                              */
+    int32_t num_mixed;         /* LPs on the FP32 tableau + FP64 certificate path    */
+    int32_t num_fallback;      /* of those, re-solved in FP64 by the last solve      */
+    int32_t internal_errors;   /* internal-consistency failures seen by the kernels in
+                                  the last solve (0 in a correct run; the LP concerned
+                                  gets LP_NUMERICAL or is re-solved)                  */
+    int32_t internal_error_code; /* code of the first such failure (0 if none)       */
+    int32_t internal_error_lp;   /* its LP index (-1 if none)                        */
+    int32_t internal_error_detail[5]; /* kernel state at that failure (diagnostics)   */
     int64_t max_smem_bytes;    /* largest shared-memory footprint of a launch        */
     int64_t workspace_bytes;   /* global workspace of the streamed LPs               */
 } lp_batch_plan;
 
-/* Report the launch plan made by lp_batch_create. */
-lpb_err lp_batch_plan_info(const lp_batch *h, lp_batch_plan *plan);
+/* Report the launch plan made by lp_batch_create (and, for num_fallback, the
+ * outcome of the last solve: this waits for that solve). */
+lpb_err lp_batch_plan_info(lp_batch *h, lp_batch_plan *plan);
 
 /*
  * Solve a batch of LPs that all have the same size m x n without allocating

@@ -25,8 +25,13 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
                  "-I", INCLUDE, "-I", CSRC]
 # FP64 kernels must not contract a*b+c: their arithmetic mirrors the oracle op by op.
+# Their global loads are cached in L2 only (-dlcm=cg): the streamed kernel's
+# tableau lives in global memory and is rewritten every pivot; with loads
+# cached in L1 it was observed to read stale tableau values (pivot sequences
+# differing from the shared-memory kernel's after another kernel had changed
+# the L1/shared-memory split), and L1 gives that data no reuse anyway.
 PER_FILE = {
-    "lp_fp64_simplex.cu": ["--fmad=false"],
+    "lp_fp64_simplex.cu": ["--fmad=false", "-Xptxas", "-dlcm=cg"],
 }
 
 

@@ -123,6 +123,16 @@ struct lp_batch {
     size_t slot_bytes = 0;
     unsigned char* workspace = nullptr;
     int32_t* counter = nullptr;
+    // mixed precision: groups of the FP32 + certificate kernel, fallback queue
+    std::vector<Group> mixed_groups;
+    int32_t num_mixed = 0;
+    lpb::MixedParams mp{};
+    int32_t* fb_queue = nullptr;
+    int32_t* fb_len = nullptr;
+    int32_t* fb_counter = nullptr;
+    int32_t* diag = nullptr;  // 3 int32: internal-consistency failures of the last solve
+    int fb_threads = 0, fb_ctas = 0;
+    size_t fb_smem = 0;
 };
 
 namespace {
@@ -187,7 +197,8 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     lp_batch_opts o;
     lpb_default_opts(&o);
     if (opts) o = *opts;
-    if (o.precision != LP_PREC_FP64) return fail(LPB_EINVAL, "unsupported precision");
+    if (o.precision != LP_PREC_FP64 && o.precision != LP_PREC_FP32_REFINE)
+        return fail(LPB_EINVAL, "unsupported precision");
     if (o.schedule != LPB_SCHED_AUTO && o.schedule != LPB_SCHED_STREAMED) return fail(LPB_EINVAL, "unknown schedule");
     if (!(o.eps_opt >= 0) || !(o.eps_piv >= 0) || !(o.eps_feas >= 0) || !(o.tau >= 0))
         return fail(LPB_EINVAL, "tolerances must be >= 0");
@@ -286,11 +297,21 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     // Plan: LPs whose tableau fits in one CTA's shared memory are grouped by
     // (threads per CTA, footprint rounded up to 4 KiB), one launch per group;
     // the others go to the streamed kernel (global workspace slots).
-    std::map<std::pair<int, size_t>, std::vector<int32_t>> buckets;
+    std::map<std::pair<int, size_t>, std::vector<int32_t>> buckets, mixed_buckets;
     std::vector<int32_t> streamed;
+    const size_t queue_smem_cap = lpb::kMaxSmemPerBlock - 1024;
     for (int32_t k = 0; k < num_lps; ++k) {
         const size_t need = lpb::resident_smem_bytes(hm[k], hn[k], hk[k]);
         h->num_phase1 += hk[k] > 0;
+        if (o.precision == LP_PREC_FP32_REFINE && o.schedule == LPB_SCHED_AUTO && need <= queue_smem_cap) {
+            // FP32 tableau + FP64 certificate; the FP64 fallback runs resident
+            const size_t msmem = (lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]) + 1023) / 1024 * 1024;
+            const int threads = pick_threads(hm[k], hn[k], hk[k], o.block_threads);
+            mixed_buckets[{threads, msmem}].push_back(k);
+            h->fb_smem = std::max(h->fb_smem, need);
+            h->fb_threads = std::max(h->fb_threads, threads);
+            continue;
+        }
         if (need > lpb::kMaxSmemPerBlock || o.schedule == LPB_SCHED_STREAMED) {
             streamed.push_back(k);
             h->slot_bytes = std::max(h->slot_bytes, lpb::streamed_slot_bytes(hm[k], hn[k], hk[k]));
@@ -312,6 +333,16 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         order.insert(order.end(), kv.second.begin(), kv.second.end());
         h->groups.push_back(g);
     }
+    for (auto& kv : mixed_buckets) {
+        Group g;
+        g.offset = (int64_t)order.size();
+        g.count = (int32_t)kv.second.size();
+        g.threads = kv.first.first;
+        g.smem = kv.first.second;
+        order.insert(order.end(), kv.second.begin(), kv.second.end());
+        h->mixed_groups.push_back(g);
+        h->num_mixed += g.count;
+    }
     h->streamed_offset = (int64_t)order.size();
     h->num_streamed = (int32_t)streamed.size();
     order.insert(order.end(), streamed.begin(), streamed.end());
@@ -326,6 +357,26 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         if ((err = alloc(h, &h->workspace, (size_t)slots * h->slot_bytes, s)) || (err = alloc(h, &h->counter, 1, s)))
             return bail_cuda(err, "streamed workspace allocation");
     }
+    if (h->num_mixed > 0) {
+        h->mp.eps_opt32 = 1e-6f;
+        h->mp.eps_piv32 = 1e-6f;
+        h->mp.eps_feas32 = 1e-6f;
+        h->mp.cert_tol = 1e-9;
+        h->mp.conv_tol = std::ldexp(1.0, -43);  // componentwise backward error ~1.1e-13
+        h->mp.fwd_tol = 1e-12;
+        h->mp.max_refine = 6;
+        h->fb_smem = (h->fb_smem + 1023) / 1024 * 1024;
+        if ((err = alloc(h, &h->fb_queue, (size_t)h->num_mixed, s)) || (err = alloc(h, &h->fb_len, 1, s)) ||
+            (err = alloc(h, &h->fb_counter, 1, s)) || (err = cudaMemsetAsync(h->fb_len, 0, 4, s)))
+            return bail_cuda(err, "fallback queue allocation");
+        int sms = 0;
+        if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device)) ||
+            (err = lpb::fp64_kernels_prepare()) || (err = lpb::mixed_kernel_prepare()))
+            return bail_cuda(err, "device query");
+        h->fb_ctas = sms * lpb::fp64_resident_queue_ctas_per_sm(h->fb_threads, h->fb_smem);
+    }
+    if ((err = alloc(h, &h->diag, 8, s)) || (err = cudaMemsetAsync(h->diag, 0, 32, s)))
+        return bail_cuda(err, "diagnostic word allocation");
     if ((err = cudaMemcpyAsync(dorder, order.data(), nl * 4, cudaMemcpyHostToDevice, s)) ||
         (err = lpb::fp64_kernels_prepare()) || (err = cudaStreamSynchronize(s)))
         return bail_cuda(err, "plan upload");
@@ -338,6 +389,22 @@ lpb_err lp_batch_solve(lp_batch* h, void* stream) {
     if (!h) return fail(LPB_EINVAL, "handle is NULL");
     DeviceGuard guard(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        cudaError_t err = cudaMemsetAsync(h->diag, 0, 8 * sizeof(int32_t), s);
+        if (err != cudaSuccess) return cuda_fail(err, "diagnostic reset");
+    }
+    if (h->num_mixed > 0) {
+        cudaError_t err = cudaMemsetAsync(h->fb_len, 0, sizeof(int32_t), s);
+        if (err != cudaSuccess) return cuda_fail(err, "fallback queue reset");
+        for (const Group& g : h->mixed_groups) {
+            err = lpb::launch_mixed(h->d, h->tol, h->mp, h->d_order + g.offset, g.count, g.threads, g.smem,
+                                    h->fb_queue, h->fb_len, h->num_mixed, h->diag, s);
+            if (err != cudaSuccess) return cuda_fail(err, "mixed-precision launch");
+        }
+        err = lpb::launch_fp64_resident_queue(h->d, h->tol, h->fb_queue, h->fb_len, h->num_mixed, h->num_lps,
+                                              h->fb_counter, h->diag, h->fb_ctas, h->fb_threads, h->fb_smem, s);
+        if (err != cudaSuccess) return cuda_fail(err, "fallback launch");
+    }
     for (const Group& g : h->groups) {
         cudaError_t err = lpb::launch_fp64_resident(h->d, h->tol, h->d_order + g.offset, g.count, g.threads,
                                                     g.smem, s);
@@ -373,10 +440,31 @@ lpb_err lp_batch_results(lp_batch* h, int32_t* status, int32_t* iters, double* o
     return LPB_OK;
 }
 
-lpb_err lp_batch_plan_info(const lp_batch* h, lp_batch_plan* plan) {
+lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
     if (!h || !plan) return fail(LPB_EINVAL, "handle or plan is NULL");
-    plan->num_groups = (int32_t)h->groups.size() + (h->num_streamed > 0 ? 1 : 0);
+    plan->num_groups = (int32_t)(h->groups.size() + h->mixed_groups.size()) + (h->num_streamed > 0 ? 1 : 0) +
+                       (h->num_mixed > 0 ? 1 : 0);
     plan->num_resident = h->num_lps - h->num_streamed;
+    plan->num_mixed = h->num_mixed;
+    plan->num_fallback = 0;
+    plan->internal_errors = 0;
+    plan->internal_error_code = 0;
+    plan->internal_error_lp = -1;
+    for (int i = 0; i < 5; ++i) plan->internal_error_detail[i] = 0;
+    if (h->solved) {
+        DeviceGuard guard(h->device);
+        int32_t fb = 0, dg[8] = {0, 0, -1, 0, 0, 0, 0, 0};
+        cudaError_t err = cudaSuccess;
+        if (h->num_mixed > 0) err = cudaMemcpyAsync(&fb, h->fb_len, sizeof fb, cudaMemcpyDeviceToHost, h->last_stream);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(dg, h->diag, sizeof dg, cudaMemcpyDeviceToHost, h->last_stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(h->last_stream);
+        if (err != cudaSuccess) return cuda_fail(err, "plan counters");
+        plan->num_fallback = fb;
+        plan->internal_errors = dg[0];
+        plan->internal_error_code = dg[0] ? dg[1] : 0;
+        plan->internal_error_lp = dg[0] ? dg[2] : -1;
+        for (int i = 0; i < 5; ++i) plan->internal_error_detail[i] = dg[0] ? dg[3 + i] : 0;
+    }
     plan->num_streamed = h->num_streamed;
     plan->num_phase1 = h->num_phase1;
     plan->max_smem_bytes = (int64_t)h->max_smem;

@@ -1,0 +1,121 @@
+// lp_device.cuh -- device helpers shared by the simplex kernels: exact
+// order-preserving integer keys of FP64/FP32 values and block reductions built
+// on warp `redux` instructions.
+#pragma once
+
+#include <climits>
+
+#include "lp_internal.h"
+
+namespace lpb {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Internal-consistency failure seen by a kernel: counted in diag[0]; the
+// first failure's code and LP index are kept in diag[1], diag[2].  The
+// kernel skips the access it was about to make and gives up on the LP.
+__device__ __forceinline__ void record_internal_error(int32_t* diag, int code, int lp, int a = 0, int b = 0,
+                                                      int c = 0, int d = 0, int e = 0) {
+    if (!diag) return;
+    if (atomicAdd(diag, 1) == 0) {
+        diag[1] = code;
+        diag[2] = lp;
+        diag[3] = a; diag[4] = b; diag[5] = c; diag[6] = d; diag[7] = e;
+    }
+}
+
+// Order-preserving map of a (non-NaN) double to a signed 64-bit key:
+// a < b  <=>  okey(a) < okey(b);  -0 and +0 map to the same key.
+__device__ __forceinline__ long long okey(double v) {
+    long long b = __double_as_longlong(v);
+    b = (b == LLONG_MIN) ? 0LL : b;
+    return b ^ ((b >> 63) & LLONG_MAX);
+}
+__device__ __forceinline__ double kval(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & LLONG_MAX));
+}
+// Key of |v| (the plain bit pattern with the sign cleared).
+__device__ __forceinline__ long long abskey(double v) { return __double_as_longlong(v) & LLONG_MAX; }
+
+__device__ __forceinline__ long long warp_min_i64(long long v) {
+    const int hi = (int)(v >> 32);
+    const int mhi = __reduce_min_sync(kFull, hi);
+    const unsigned lo = (hi == mhi) ? (unsigned)(v & 0xffffffffLL) : 0xffffffffu;
+    const unsigned mlo = __reduce_min_sync(kFull, lo);
+    return (long long)(((unsigned long long)(unsigned)mhi << 32) | (unsigned long long)mlo);
+}
+
+// Float order key (int32): a < b <=> fkey(a) < fkey(b); -0 and +0 map alike.
+__device__ __forceinline__ int fkey(float f) {
+    int b = __float_as_int(f);
+    b = (b == INT_MIN) ? 0 : b;
+    return b ^ ((b >> 31) & INT_MAX);
+}
+__device__ __forceinline__ float fval(int k) { return __int_as_float(k ^ ((k >> 31) & INT_MAX)); }
+
+// Unbiased binary exponent of a double from its bits (-1023 for 0 and subnormals).
+__device__ __forceinline__ int dexp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF) - 1023; }
+
+// Block-wide reductions over per-warp `redux` results.  Each call writes
+// one slot per warp, waits at a barrier, reads every slot, and waits at a
+// second barrier before returning, so no later write can overtake a read of
+// the same slot whatever the calls that follow.
+struct Reducer {
+    long long* s64;   // kMaxWarps int64 slots
+    unsigned* s32;    // 2 x kMaxWarps uint32 slots (value, count)
+    int nw, warp, lane;
+
+    __device__ long long min_i64(long long v) {
+        v = warp_min_i64(v);
+        if (lane == 0) s64[warp] = v;
+        __syncthreads();
+        long long r = s64[0];
+        for (int w = 1; w < nw; ++w) r = min(r, s64[w]);
+        __syncthreads();
+        return r;
+    }
+    __device__ unsigned min_u32(unsigned v) {
+        v = __reduce_min_sync(kFull, v);
+        if (lane == 0) s32[warp] = v;
+        __syncthreads();
+        unsigned r = s32[0];
+        for (int w = 1; w < nw; ++w) r = min(r, s32[w]);
+        __syncthreads();
+        return r;
+    }
+    __device__ int min_i32(int v) {
+        return (int)(min_u32((unsigned)v ^ 0x80000000u) ^ 0x80000000u);
+    }
+    // Block-wide (sum of cnt, min of v).
+    __device__ void count_min(unsigned cnt, unsigned v, unsigned& cnt_out, unsigned& v_out) {
+        cnt = __reduce_add_sync(kFull, cnt);
+        v = __reduce_min_sync(kFull, v);
+        if (lane == 0) { s32[warp] = v; s32[kMaxWarps + warp] = cnt; }
+        __syncthreads();
+        unsigned c = 0, r = 0xffffffffu;
+        for (int w = 0; w < nw; ++w) { c += s32[kMaxWarps + w]; r = min(r, s32[w]); }
+        __syncthreads();
+        cnt_out = c;
+        v_out = r;
+    }
+    // Exclusive prefix count of `flag` over the block (in thread order) and
+    // the total; `flag` must be the same for all lanes' view of bal.
+    __device__ int prefix_count(bool flag, int& total) {
+        const unsigned bal = __ballot_sync(kFull, flag);
+        if (lane == 0) s32[warp] = (unsigned)__popc(bal);
+        __syncthreads();
+        int before = 0, tot = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int cw = (int)s32[w];
+            before += (w < warp) ? cw : 0;
+            tot += cw;
+        }
+        __syncthreads();
+        total = tot;
+        return before + __popc(bal & ((1u << lane) - 1u));
+    }
+};
+
+}  // namespace
+}  // namespace lpb

@@ -36,25 +36,11 @@
 
 #include <climits>
 
+#include "lp_device.cuh"
 #include "lp_internal.h"
 
 namespace lpb {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-// Order-preserving map of a (non-NaN) double to a signed 64-bit key:
-// a < b  <=>  okey(a) < okey(b);  -0 and +0 map to the same key.
-__device__ __forceinline__ long long okey(double v) {
-    long long b = __double_as_longlong(v);
-    b = (b == LLONG_MIN) ? 0LL : b;
-    return b ^ ((b >> 63) & LLONG_MAX);
-}
-__device__ __forceinline__ double kval(long long k) {
-    return __longlong_as_double(k ^ ((k >> 63) & LLONG_MAX));
-}
-// Key of |v| (the plain bit pattern with the sign cleared).
-__device__ __forceinline__ long long abskey(double v) { return __double_as_longlong(v) & LLONG_MAX; }
 
 // Tie window of Steps 1 and 2: v + tau * max(1, |v|) (product, then sum).
 __device__ __forceinline__ double tie_threshold(double v, double tau) {
@@ -62,25 +48,6 @@ __device__ __forceinline__ double tie_threshold(double v, double tau) {
     const double s = (ab < 0x3FF0000000000000LL) ? 1.0 : __longlong_as_double(ab);
     return __dadd_rn(v, __dmul_rn(tau, s));
 }
-
-__device__ __forceinline__ long long warp_min_i64(long long v) {
-    const int hi = (int)(v >> 32);
-    const int mhi = __reduce_min_sync(kFull, hi);
-    const unsigned lo = (hi == mhi) ? (unsigned)(v & 0xffffffffLL) : 0xffffffffu;
-    const unsigned mlo = __reduce_min_sync(kFull, lo);
-    return (long long)(((unsigned long long)(unsigned)mhi << 32) | (unsigned long long)mlo);
-}
-
-// Float order key (int32): a < b <=> fkey(a) < fkey(b); -0 and +0 map alike.
-__device__ __forceinline__ int fkey(float f) {
-    int b = __float_as_int(f);
-    b = (b == INT_MIN) ? 0 : b;
-    return b ^ ((b >> 31) & INT_MAX);
-}
-__device__ __forceinline__ float fval(int k) { return __int_as_float(k ^ ((k >> 31) & INT_MAX)); }
-
-// Unbiased binary exponent of a double from its bits (-1023 for 0 and subnormals).
-__device__ __forceinline__ int dexp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF) - 1023; }
 
 // Upper bound, in units of okey, of okey(thr) - okey(v) where thr is the tie
 // threshold v + tau*max(1,|v|) of a negative v (Step 1).  `wb` >=
@@ -97,54 +64,6 @@ __device__ __forceinline__ unsigned long long step1_window(long long kmin, long 
     if (sh > 30) return ~0ull;
     return (unsigned long long)wb << sh;
 }
-
-// Block-wide reductions.  Each kind of buffer alternates between two halves
-// so that a buffer is never rewritten before every thread has read it (two
-// uses of the same half are always separated by another barrier).
-struct Reducer {
-    long long* s64;   // 2 x kMaxWarps
-    unsigned* s32;    // 6 x kMaxWarps: 2 min buffers, 2 pair-min buffers, 2 pair-count buffers
-    int nw, warp, lane;
-    int b64 = 0, b32 = 0, bp = 0;
-
-    __device__ long long min_i64(long long v) {
-        v = warp_min_i64(v);
-        long long* s = s64 + b64 * kMaxWarps;
-        b64 ^= 1;
-        if (lane == 0) s[warp] = v;
-        __syncthreads();
-        long long r = s[0];
-        for (int w = 1; w < nw; ++w) r = min(r, s[w]);
-        return r;
-    }
-    __device__ unsigned min_u32(unsigned v) {
-        v = __reduce_min_sync(kFull, v);
-        unsigned* s = s32 + b32 * kMaxWarps;
-        b32 ^= 1;
-        if (lane == 0) s[warp] = v;
-        __syncthreads();
-        unsigned r = s[0];
-        for (int w = 1; w < nw; ++w) r = min(r, s[w]);
-        return r;
-    }
-    __device__ int min_i32(int v) {
-        return (int)(min_u32((unsigned)v ^ 0x80000000u) ^ 0x80000000u);
-    }
-    // Block-wide (sum of cnt, min of v) behind a single barrier.
-    __device__ void count_min(unsigned cnt, unsigned v, unsigned& cnt_out, unsigned& v_out) {
-        cnt = __reduce_add_sync(kFull, cnt);
-        v = __reduce_min_sync(kFull, v);
-        unsigned* sv = s32 + (2 + bp) * kMaxWarps;
-        unsigned* sc = s32 + (4 + bp) * kMaxWarps;
-        bp ^= 1;
-        if (lane == 0) { sv[warp] = v; sc[warp] = cnt; }
-        __syncthreads();
-        unsigned c = 0, r = 0xffffffffu;
-        for (int w = 0; w < nw; ++w) { c += sc[w]; r = min(r, sv[w]); }
-        cnt_out = c;
-        v_out = r;
-    }
-};
 
 struct Tab {
     double* T;        // R x LD, row-major; column 0 = right-hand side
@@ -163,8 +82,8 @@ struct Tab {
 __device__ __forceinline__ void pivot(Tab& tb, int Ract, int Cact, int l, int e) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int LD = tb.LD;
-    double* __restrict__ T = tb.T;
-    const double* __restrict__ colE = tb.colE;
+    double* T = tb.T;
+    const double* colE = tb.colE;
     const double pe = colE[l];
     double* Tl = T + (size_t)l * LD;
     for (int j = tid; j < Cact; j += nt) {
@@ -240,18 +159,10 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
     for (int i0 = 0; i0 < m; i0 += nt) {
         const int i = i0 + tid;
         const bool isneg = (i < m) && (bv[i] < 0.0);
-        const unsigned bal = __ballot_sync(kFull, isneg);
-        if (lane == 0) red.s32[warp] = (unsigned)__popc(bal);
-        __syncthreads();
-        int before = 0, tot = 0;
-        for (int w = 0; w < nw; ++w) {
-            const int cw = (int)red.s32[w];
-            before += (w < warp) ? cw : 0;
-            tot += cw;
-        }
+        int tot;
+        const int r = k + red.prefix_count(isneg, tot);
         if (i < m) {
             if (isneg) {
-                const int r = k + before + __popc(bal & ((1u << lane) - 1u));
                 neg[r] = i;
                 row_var[i] = nm + r;
             } else {
@@ -259,7 +170,6 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
             }
         }
         k += tot;
-        __syncthreads();
     }
 
     const BigLayout L = big_layout(m, n, k, kStreamed);
@@ -270,7 +180,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
     tb.row_var = row_var;
     tb.LD = L.LD;
     const int LD = L.LD;
-    double* __restrict__ T = tb.T;
+    double* T = tb.T;  // the tableau is written through several pointers: no restrict
     int Cvar = n + k;  // live variable columns 1..Cvar
 
     for (int j = tid; j <= Cvar; j += nt)
@@ -478,9 +388,36 @@ fp64_resident_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* _
     solve_one<false>(B, tol, order[blockIdx.x], smem, smem + SmallLayout::total);
 }
 
+// Resident kernel over a device-side list: persistent CTAs take the LPs
+// queue[0 .. *queue_len) through the atomic `counter` (0 at launch).  Used for
+// the LPs the mixed-precision kernel hands back.
+__global__ void __launch_bounds__(kMaxThreads)
+fp64_resident_queue_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ queue,
+                           const int32_t* __restrict__ queue_len, const int32_t queue_cap, const int32_t num_lps,
+                           int32_t* __restrict__ counter, int32_t* __restrict__ diag)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int next;
+    const int count = min(*queue_len, queue_cap);
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int idx = next;
+        __syncthreads();
+        if (idx >= count) break;
+        const int lp = queue[idx];
+        if (lp < 0 || lp >= num_lps) {
+            if (threadIdx.x == 0) record_internal_error(diag, 5, lp);
+            continue;
+        }
+        solve_one<false>(B, tol, lp, smem, smem + SmallLayout::total);
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kStreamedThreads, 2)
 fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order,
-                     const int32_t count, unsigned char* __restrict__ workspace, const size_t slot_bytes,
+                     const int32_t count, unsigned char* workspace, const size_t slot_bytes,
                      int32_t* __restrict__ counter)
 {
     __shared__ __align__(16) unsigned char small[SmallLayout::total];
@@ -500,8 +437,29 @@ fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* _
 }  // namespace
 
 cudaError_t fp64_kernels_prepare() {
-    return cudaFuncSetAttribute(fp64_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kMaxSmemPerBlock);
+    cudaError_t err = cudaFuncSetAttribute(fp64_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kMaxSmemPerBlock);
+    if (err != cudaSuccess) return err;
+    return cudaFuncSetAttribute(fp64_resident_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(kMaxSmemPerBlock - 1024));
+}
+
+int fp64_resident_queue_ctas_per_sm(int threads, size_t smem) {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fp64_resident_queue_kernel, threads, smem) != cudaSuccess)
+        return 1;
+    return blocks > 0 ? blocks : 1;
+}
+
+cudaError_t launch_fp64_resident_queue(const DeviceBatch& B, const Tolerances& tol, const int32_t* queue,
+                                       const int32_t* queue_len, int32_t queue_cap, int32_t num_lps,
+                                       int32_t* counter, int32_t* diag, int ctas, int threads,
+                                       size_t smem, cudaStream_t stream) {
+    cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
+    if (err != cudaSuccess) return err;
+    fp64_resident_queue_kernel<<<ctas, threads, smem, stream>>>(B, tol, queue, queue_len, queue_cap, num_lps,
+                                                                counter, diag);
+    return cudaGetLastError();
 }
 
 int fp64_streamed_ctas_per_sm() {

@@ -101,6 +101,62 @@ __host__ __device__ inline size_t streamed_slot_bytes(int m, int n, int k) {
     return (big_layout(m, n, k, true).total + 255) & ~size_t(255);
 }
 
+// Shared-memory layout of the mixed-precision kernel (after SmallLayout):
+// FP64 certification vectors and per-row arrays first (k-independent), then
+// the FP32 condensed tableau (R x LD floats, odd stride), its pivot-column copy
+// and the column labels.
+struct MixedLayout {
+    int R, LD;
+    size_t xb, yv, dv, res, rkey, row_var, neg, spos, slist;  // k-independent
+    size_t T, colE, col_var;                                 // k-dependent
+    size_t total;
+};
+
+__host__ __device__ inline MixedLayout mixed_layout(int m, int n, int k) {
+    MixedLayout L;
+    L.R = m + 1 + (k > 0 ? 1 : 0);
+    L.LD = (n + k + 1) | 1;
+    const size_t mn = (size_t)(m > n ? m : n);
+    size_t o = 0;
+    L.xb = o;      o += align16((size_t)m * 8);
+    L.yv = o;      o += align16((size_t)m * 8);
+    L.dv = o;      o += align16((size_t)m * 8);
+    L.res = o;     o += align16(mn * 8);
+    L.rkey = o;    o += align16((size_t)m * 4);
+    L.row_var = o; o += align16((size_t)m * 4);
+    L.neg = o;     o += align16((size_t)m * 4);
+    L.spos = o;    o += align16((size_t)m * 4);
+    L.slist = o;   o += align16((size_t)m * 4);
+    L.T = o;       o += align16((size_t)L.R * (size_t)L.LD * 4);
+    L.colE = o;    o += align16((size_t)L.R * 4);
+    L.col_var = o; o += align16((size_t)L.LD * 4);
+    L.total = o;
+    return L;
+}
+
+__host__ __device__ inline size_t mixed_smem_bytes(int m, int n, int k) {
+    return SmallLayout::total + mixed_layout(m, n, k).total;
+}
+
+// Tolerances of the FP32 simplex and of the FP64 certificate.
+struct MixedParams {
+    float eps_opt32, eps_piv32, eps_feas32;
+    double cert_tol;     // primal (x scaled by max(1,|b|_inf)) and dual feasibility tolerance
+    double conv_tol;     // refinement: every residual <= conv_tol * (|rhs| + |B||z|) ...
+    double fwd_tol;      // ... and the last correction <= fwd_tol * max(|z_i|, 1e-8 max|z|)
+    int32_t max_refine;  // refinement steps per vector
+};
+
+cudaError_t mixed_kernel_prepare();
+// One CTA per LP of order[0..count): FP32 simplex, FP64 certificate; LPs that
+// are not certified are appended to fb_queue (length *fb_len, zeroed by the
+// caller before the first mixed launch of a solve).
+// diag: 3 int32 (count, first code, first LP) of internal-consistency
+// failures (see record_internal_error); may be null.
+cudaError_t launch_mixed(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
+                         const int32_t* order, int32_t count, int threads, size_t smem,
+                         int32_t* fb_queue, int32_t* fb_len, int32_t fb_cap, int32_t* diag, cudaStream_t stream);
+
 // Launchers (lp_fp64_simplex.cu).
 constexpr int kStreamedThreads = 512;
 cudaError_t fp64_kernels_prepare();
@@ -114,6 +170,14 @@ cudaError_t launch_fp64_streamed(const DeviceBatch& B, const Tolerances& tol, co
                                  int32_t* counter, cudaStream_t stream);
 // CTAs of the streamed kernel that fit on one SM.
 int fp64_streamed_ctas_per_sm();
+// Resident kernel over a device-side LP list (persistent CTAs, atomic
+// `counter` zeroed on `stream` before the launch).  `smem` must cover every
+// listed LP's resident_smem_bytes and stay below kMaxSmemPerBlock - 1 KiB.
+cudaError_t launch_fp64_resident_queue(const DeviceBatch& B, const Tolerances& tol, const int32_t* queue,
+                                       const int32_t* queue_len, int32_t queue_cap, int32_t num_lps,
+                                       int32_t* counter, int32_t* diag, int ctas, int threads,
+                                       size_t smem, cudaStream_t stream);
+int fp64_resident_queue_ctas_per_sm(int threads, size_t smem);
 
 // Checks (lp_api.cu helpers in lp_prepare.cu): counts non-finite values of
 // A, b, c into *bad and the rows with b_i < 0 of every LP into k[].

@@ -1,0 +1,570 @@
+// lp_mixed.cu -- mixed-precision batched simplex: FP32 condensed tableau in
+// shared memory (one CTA per LP), then an FP64 certificate of the basis the
+// FP32 run ended on.
+//
+// The paper's method (Gurung & Ray, arXiv 1802.08557, Section 3: Steps 1-3 on
+// the tableau, two-phase method; Section 4: one CTA per LP) is run with FP32
+// tableau arithmetic: on GB300 the FP32 pipe is ~64x faster than the FP64 pipe.
+// The FP32 run only proposes a basis.  The answer comes from FP64:
+//  - B^-1 is read off the FP32 tableau (the column of slack n+c in the
+//    condensed tableau is B^-1 e_c; a basic slack's is a unit vector);
+//  - x_B = B^-1 b and y^T = c_B^T B^-1 are refined in FP64: residual in FP64
+//    from the original A, b, c, correction through the FP32 B^-1, until the
+//    correction is below conv_tol relative;
+//  - the certificate is checked in FP64: x_B >= -tol (primal), y >= -tol and
+//    A^T y - c >= -tol on non-basic structurals (dual), c^T x = b^T y;
+//    for an unbounded claim, a refined ray d (d >= -tol, c^T d > 0) from a
+//    primal-feasible point.
+// An LP whose claim is not certified (or that ends infeasible, at the
+// iteration limit or in breakdown) is appended to a device queue and solved
+// again by the FP64 kernel.  So every reported optimum comes from an FP64
+// basic solution of a basis proven optimal to cert_tol.
+//
+// This path has no counterpart in the paper (which is FP64 only).
+
+#include <climits>
+
+#include "lp_device.cuh"
+#include "lp_internal.h"
+
+namespace lpb {
+namespace {
+
+__device__ __forceinline__ float fabs32(float v) { return __int_as_float(__float_as_int(v) & INT_MAX); }
+
+// 64-bit key: signed `hi` compared first, then unsigned `lo`.
+__device__ __forceinline__ long long pack_key(int hi, unsigned lo) {
+    return (long long)(((unsigned long long)(unsigned)hi << 32) | (unsigned long long)lo);
+}
+
+struct Tab32 {
+    float* T;
+    float* colE;
+    int* col_var;
+    int* row_var;
+    int LD;
+};
+
+// Step 3 in FP32 (same structure as the FP64 pivot).
+__device__ __forceinline__ void pivot32(Tab32& tb, int Ract, int Cact, int l, int e) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int LD = tb.LD;
+    float* T = tb.T;
+    const float* colE = tb.colE;
+    const float pe = colE[l];
+    float* Tl = T + l * LD;
+    for (int j = tid; j < Cact; j += nt) {
+        const float v = (j == e) ? 1.0f : Tl[j];
+        Tl[j] = __fdiv_rn(v, pe);
+    }
+    if (tid == 0) {
+        const int ev = tb.col_var[e];
+        tb.col_var[e] = tb.row_var[l];
+        tb.row_var[l] = ev;
+    }
+    __syncthreads();
+    // update: thread (tr, tc) takes columns tc, tc+cw, ... and rows tr, tr+rg,
+    // ...; a warp shares its row, so colE[r] is a broadcast and the pivot-row
+    // value of the column stays in a register
+    const int cw = min(nt, (Cact + 31) & ~31);
+    const int rg = nt / cw;
+    const int tc = tid % cw, tr = tid / cw;
+    if (tr < rg) {
+        for (int j = tc; j < Cact; j += cw) {
+            const float pr = Tl[j];
+            const bool ecol = (j == e);
+            for (int r = tr; r < Ract; r += rg) {
+                if (r == l) continue;
+                float* t = T + r * LD + j;
+                const float old = ecol ? 0.0f : *t;
+                *t = __fmaf_rn(-colE[r], pr, old);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void retire_column32(Tab32& tb, int Ract, int e, int& Cvar) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (e != Cvar) {
+        for (int r = tid; r < Ract; r += nt) {
+            float* row = tb.T + r * tb.LD;
+            row[e] = row[Cvar];
+        }
+        if (tid == 0) tb.col_var[e] = tb.col_var[Cvar];
+    }
+    --Cvar;
+    __syncthreads();
+}
+
+// max |v| of a block (FP64), as a double.
+__device__ __forceinline__ double block_absmax(Reducer& red, double v) {
+    return __longlong_as_double(-red.min_i64(-abskey(v)));
+}
+
+__global__ void __launch_bounds__(kMaxThreads, 2)
+mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, const int32_t* __restrict__ order,
+             int32_t* __restrict__ fb_queue, int32_t* __restrict__ fb_len, const int32_t fb_cap,
+             int32_t* __restrict__ diag)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lp = order[blockIdx.x];
+    const int m = B.m[lp];
+    const int n = B.n[lp];
+    const int nm = n + m;
+    const double* __restrict__ A = B.A + B.a_off[lp];
+    const double* __restrict__ bv = B.b + B.b_off[lp];
+    const double* __restrict__ cv = B.c + B.c_off[lp];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    unsigned char* big = smem + SmallLayout::total;
+    Reducer red{reinterpret_cast<long long*>(smem + SmallLayout::red64),
+                reinterpret_cast<unsigned*>(smem + SmallLayout::red32), nw, warp, lane};
+
+    const MixedLayout L0 = mixed_layout(m, n, 0);
+    double* xb = reinterpret_cast<double*>(big + L0.xb);
+    double* yv = reinterpret_cast<double*>(big + L0.yv);
+    double* dv = reinterpret_cast<double*>(big + L0.dv);
+    double* res = reinterpret_cast<double*>(big + L0.res);
+    int* rkey = reinterpret_cast<int*>(big + L0.rkey);
+    int* row_var = reinterpret_cast<int*>(big + L0.row_var);
+    int* neg = reinterpret_cast<int*>(big + L0.neg);
+    int* spos = reinterpret_cast<int*>(big + L0.spos);
+    int* slist = reinterpret_cast<int*>(big + L0.slist);
+
+    // ---- tableau build (FP32), rows with b_i < 0 negated (two-phase) -------
+    int k = 0;
+    for (int i0 = 0; i0 < m; i0 += nt) {
+        const int i = i0 + tid;
+        const bool isneg = (i < m) && (bv[i] < 0.0);
+        int tot;
+        const int r = k + red.prefix_count(isneg, tot);
+        if (i < m) {
+            if (isneg) {
+                neg[r] = i;
+                row_var[i] = nm + r;
+            } else {
+                row_var[i] = n + i;
+            }
+        }
+        k += tot;
+    }
+    const MixedLayout L = mixed_layout(m, n, k);
+    Tab32 tb;
+    tb.T = reinterpret_cast<float*>(big + L.T);
+    tb.colE = reinterpret_cast<float*>(big + L.colE);
+    tb.col_var = reinterpret_cast<int*>(big + L.col_var);
+    tb.row_var = row_var;
+    tb.LD = L.LD;
+    const int LD = L.LD;
+    float* T = tb.T;  // the tableau is written through several pointers: no restrict
+    int Cvar = n + k;
+
+    for (int j = tid; j <= Cvar; j += nt)
+        tb.col_var[j] = (j == 0) ? -1 : (j <= n ? j - 1 : n + neg[j - 1 - n]);
+    for (int i = warp; i < m; i += nw) {
+        const bool isneg = row_var[i] >= nm;
+        const double* Ai = A + (size_t)i * n;
+        float* Ti = T + i * LD;
+        for (int j = lane; j <= Cvar; j += 32) {
+            float v;
+            if (j == 0) v = __double2float_rn(bv[i]);
+            else if (j <= n) v = __double2float_rn(Ai[j - 1]);
+            else v = (neg[j - 1 - n] == i) ? 1.0f : 0.0f;
+            Ti[j] = isneg ? -v : v;
+        }
+    }
+    {
+        float* Tm = T + m * LD;
+        for (int j = tid; j <= Cvar; j += nt) Tm[j] = (j >= 1 && j <= n) ? -__double2float_rn(cv[j - 1]) : 0.0f;
+    }
+    long long bkey = 0x3FF0000000000000LL, ckey = 0x3FF0000000000000LL;  // 1.0
+    for (int i = tid; i < m; i += nt) bkey = max(bkey, abskey(bv[i]));
+    for (int j = tid; j < n; j += nt) ckey = max(ckey, abskey(cv[j]));
+    const double bmax = __longlong_as_double(-red.min_i64(-bkey));  // barrier: fills done
+    const double cmax = __longlong_as_double(-red.min_i64(-ckey));
+    // FP32 range: every nonzero |a_ij|, |b_i|, |c_j| within [2^-60, 2^60]
+    unsigned out_of_range = 0;
+    {
+        auto outside = [](double v) {
+            const long long a = abskey(v);
+            return a != 0 && (a < 0x3C30000000000000LL || a > 0x43B0000000000000LL);
+        };
+        for (int idx = tid; idx < m * n; idx += nt) out_of_range += outside(A[idx]) ? 1u : 0u;
+        for (int i = tid; i < m; i += nt) out_of_range += outside(bv[i]) ? 1u : 0u;
+        for (int j = tid; j < n; j += nt) out_of_range += outside(cv[j]) ? 1u : 0u;
+        unsigned dummy;
+        red.count_min(out_of_range, 0u, out_of_range, dummy);
+    }
+    if (k > 0) {
+        float* Tw = T + (m + 1) * LD;
+        for (int j = tid; j <= Cvar; j += nt) {
+            float w = 0.0f;
+            for (int t = 0; t < k; ++t) w = __fsub_rn(w, T[neg[t] * LD + j]);
+            Tw[j] = w;
+        }
+        __syncthreads();
+    }
+
+    // ---- FP32 simplex (Steps 1-3, two-phase) ----------------------------
+    const int key_neg_eps_opt = fkey(-mp.eps_opt32);
+    const int max_iters = tol.max_iters > 0 ? tol.max_iters : 50 * (m + n);
+    int iters = 0;
+    int status = -1;
+    int phase = (k > 0) ? 1 : 2;
+    int e_unb = -1;
+    if (out_of_range) status = kNumerical;  // straight to the FP64 kernel
+
+    while (status < 0) {
+        const int orow = (phase == 1) ? m + 1 : m;
+        const int Ract = (phase == 1) ? m + 2 : m + 1;
+        const float* Trow = T + orow * LD;
+        bool end_phase1 = false;
+        // Step 1, one pass: min over (key of d_j, variable label) packed in 64
+        // bits -- the most negative reduced cost, exact ties to the lowest label
+        long long dloc = LLONG_MAX;
+        for (int j = 1 + tid; j <= Cvar; j += nt) {
+            const int v = tb.col_var[j];
+            if (v < nm) dloc = min(dloc, pack_key(fkey(Trow[j]), ((unsigned)v << 16) | (unsigned)j));
+        }
+        const long long dsel = red.min_i64(dloc);
+        const int dmin = (int)(dsel >> 32);
+        if (dsel == LLONG_MAX || dmin >= key_neg_eps_opt) {
+            if (phase == 2) { status = kOptimal; break; }
+            end_phase1 = true;
+        } else {
+            const int e = (int)(dsel & 0xffff);
+            if (e < 1 || e > Cvar) {
+                if (tid == 0) record_internal_error(diag, 1, lp, dmin, 0, iters, phase, (int)(dsel & 0xffffffff));
+                status = kNumerical;
+                break;
+            }
+            // Step 2, one pass: min over (key of ratio, row)
+            long long rloc = LLONG_MAX;
+            for (int i = tid; i < Ract; i += nt) {
+                const float t = T[i * LD + e];
+                tb.colE[i] = t;
+                if (i < m && t > mp.eps_piv32)
+                    rloc = min(rloc, pack_key(fkey(__fdiv_rn(T[i * LD], t)), (unsigned)i));
+            }
+            const long long rsel = red.min_i64(rloc);
+            if (rsel == LLONG_MAX) {
+                if (phase == 2) {
+                    status = kUnbounded;
+                    e_unb = e;
+                    break;
+                }
+                // phase I cannot be unbounded: in FP32 this is rounding noise
+                // in the auxiliary row; end phase I (the certificate decides)
+                end_phase1 = true;
+            } else {
+                const int l = (int)(rsel & 0xffffffff);
+                if (l < 0 || l >= m) {
+                    if (tid == 0) record_internal_error(diag, 2, lp, (int)(rsel >> 32), 0, iters, phase, l);
+                    status = kNumerical;
+                    break;
+                }
+                if (!isfinite(tb.colE[l])) { status = kNumerical; break; }
+                if (iters >= max_iters) { status = kIterLimit; break; }
+                pivot32(tb, Ract, Cvar + 1, l, e);
+                ++iters;
+                if (tb.col_var[e] >= nm) retire_column32(tb, Ract, e, Cvar);
+            }
+        }
+        if (end_phase1) {
+            const float wstar = -T[(m + 1) * LD];
+            if (wstar > mp.eps_feas32 * (float)bmax) { status = kInfeasible; break; }
+            for (int i = 0; i < m && status < 0; ++i) {
+                if (row_var[i] < nm) continue;
+                const float* Ti = T + i * LD;
+                unsigned sel = 0xffffffffu;
+                for (int j = 1 + tid; j <= Cvar; j += nt)
+                    if (tb.col_var[j] < nm && fabs32(Ti[j]) > mp.eps_piv32)
+                        sel = min(sel, ((unsigned)tb.col_var[j] << 16) | (unsigned)j);
+                sel = red.min_u32(sel);
+                if (sel == 0xffffffffu) continue;
+                if (iters >= max_iters) { status = kIterLimit; break; }
+                const int e = (int)(sel & 0xffffu);
+                if (e < 1 || e > Cvar) { record_internal_error(diag, 1, lp); status = kNumerical; break; }
+                for (int r = tid; r < m + 1; r += nt) tb.colE[r] = T[r * LD + e];
+                __syncthreads();
+                pivot32(tb, m + 1, Cvar + 1, i, e);
+                ++iters;
+                if (tb.col_var[e] >= nm) retire_column32(tb, m + 1, e, Cvar);
+            }
+            phase = 2;
+        }
+    }
+
+    // ---- FP64 certificate ---------------------------------------------------
+    bool ok = (status == kOptimal || status == kUnbounded);
+    int s = 0;  // basic structurals
+    if (ok) {
+        unsigned nart = 0, dummy;
+        for (int i = tid; i < m; i += nt) nart += (row_var[i] >= nm) ? 1u : 0u;
+        red.count_min(nart, 0u, nart, dummy);
+        ok = (nart == 0);
+    }
+    if (ok) {
+        // where each slack is: column position (> 0) or -(basic row + 1)
+        for (int j = 1 + tid; j <= Cvar; j += nt) {
+            const int v = tb.col_var[j];
+            if (v >= n && v < nm) spos[v - n] = j;
+        }
+        // compacted list of the rows whose basic variable is structural
+        for (int i0 = 0; i0 < m; i0 += nt) {
+            const int i = i0 + tid;
+            const int v = (i < m) ? row_var[i] : -1;
+            if (i < m && v >= n) spos[v - n] = -(i + 1);
+            const bool st = (i < m) && (v < n);
+            int tot;
+            const int pos = s + red.prefix_count(st, tot);
+            if (st) slist[pos] = i;
+            s += tot;
+        }
+        // every slack must be placed exactly once: a live column or a basic row
+        unsigned badpos = 0, dummy;
+        for (int c = tid; c < m; c += nt) {
+            const int p = spos[c];
+            badpos += (p == 0 || p > Cvar || -p - 1 >= m) ? 1u : 0u;
+        }
+        red.count_min(badpos, 0u, badpos, dummy);
+        if (badpos) {
+            if (tid == 0) record_internal_error(diag, 3, lp);
+            ok = false;
+        }
+        for (int i = tid; i < m; i += nt) xb[i] = (double)T[i * LD];
+        __syncthreads();
+    }
+    const double tol_p = mp.cert_tol * bmax;
+    const double tol_d = mp.cert_tol * cmax;
+
+    // Refine  B z = rhs  (z by tableau row), rhs = b or -(column of rhs_var):
+    // z += B^-1 r with the residual r in FP64 from the original data and B^-1
+    // the FP32 one of the tableau.  Converged when (a) every residual is within
+    // conv_tol of |rhs_c| + sum |B_c,i| |z_i| (backward error) and (b) the last
+    // correction moved no component by more than fwd_tol of max(|z_i|,
+    // 1e-8 max|z|) (forward error: an ill-conditioned basis stalls here and is
+    // left to the FP64 re-solve).
+    auto refine = [&](double* z, int rhs_var, bool& conv) {
+        conv = false;
+        double zloc = 0.0;
+        for (int i = tid; i < m; i += nt) zloc = (abskey(z[i]) > abskey(zloc)) ? z[i] : zloc;
+        const double zfloor = 1e-8 * block_absmax(red, zloc);
+        unsigned fwdbad = 1;  // no correction measured yet
+        for (int it = 0;; ++it) {
+            unsigned bad = 0;
+            for (int c = tid; c < m; c += nt) {
+                double r;
+                if (rhs_var < 0) r = bv[c];
+                else r = (rhs_var < n) ? -A[(size_t)c * n + rhs_var] : ((rhs_var - n == c) ? -1.0 : 0.0);
+                float mag = fabs32(__double2float_rn(r));
+                const double* Ac = A + (size_t)c * n;
+                for (int t = 0; t < s; ++t) {
+                    const int i = slist[t];
+                    const double a = Ac[row_var[i]];
+                    r = __fma_rn(-a, z[i], r);
+                    mag = __fmaf_rn(fabs32(__double2float_rn(a)), fabs32(__double2float_rn(z[i])), mag);
+                }
+                const int p = spos[c];
+                if (p < 0) {
+                    r = __dsub_rn(r, z[-p - 1]);
+                    mag = __fadd_rn(mag, fabs32(__double2float_rn(z[-p - 1])));
+                }
+                res[c] = r;
+                bad += (abskey(r) > abskey(mp.conv_tol * (double)mag)) ? 1u : 0u;
+            }
+            unsigned tot, dummy;
+            red.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
+            if (tot == 0) { conv = true; break; }
+            if (it == mp.max_refine) break;
+            fwdbad = 0;
+            for (int i = tid; i < m; i += nt) {
+                float acc = 0.0f;
+                for (int c = 0; c < m; ++c) {
+                    const int p = spos[c];
+                    if (p > 0) acc = __fmaf_rn(T[i * LD + p], __double2float_rn(res[c]), acc);
+                }
+                double d = (double)acc;
+                const int v = row_var[i];
+                if (v >= n) d = __dadd_rn(d, res[v - n]);
+                const double znew = __dadd_rn(z[i], d);
+                z[i] = znew;
+                const double lim = mp.fwd_tol * fmax(fabs(znew), zfloor);
+                fwdbad += (abskey(d) > abskey(lim)) ? 1u : 0u;
+            }
+            __syncthreads();
+        }
+    };
+
+    if (ok) {
+        bool conv;
+        refine(xb, -1, conv);
+        // primal feasibility of the basic solution
+        unsigned bad = 0, dummy;
+        for (int i = tid; i < m; i += nt) bad += (xb[i] < -tol_p) ? 1u : 0u;
+        red.count_min(bad, 0u, bad, dummy);
+        ok = conv && bad == 0;
+    }
+    if (ok && status == kOptimal) {
+        // dual: y_c = reduced cost of slack c; refine  y^T B = c_B^T
+        for (int c = tid; c < m; c += nt) {
+            const int p = spos[c];
+            yv[c] = (p > 0) ? (double)T[m * LD + p] : 0.0;
+        }
+        __syncthreads();
+        bool conv = false;
+        double yloc = 0.0;
+        for (int c = tid; c < m; c += nt) yloc = (abskey(yv[c]) > abskey(yloc)) ? yv[c] : yloc;
+        const double yfloor = 1e-8 * block_absmax(red, yloc);
+        unsigned fwdbad = 1;
+        for (int it = 0;; ++it) {
+            // rho_i = c_(v_i) - y^T col(v_i) for each basic variable (by tableau row)
+            unsigned bad = 0;
+            for (int t = tid; t < s; t += nt) {
+                const int i = slist[t];
+                const int v = row_var[i];
+                double r = cv[v];
+                float mag = fabs32(__double2float_rn(r));
+                for (int c = 0; c < m; ++c) {
+                    const double a = A[(size_t)c * n + v];
+                    r = __fma_rn(-yv[c], a, r);
+                    mag = __fmaf_rn(fabs32(__double2float_rn(a)), fabs32(__double2float_rn(yv[c])), mag);
+                }
+                res[i] = r;
+                bad += (abskey(r) > abskey(mp.conv_tol * (double)mag)) ? 1u : 0u;
+            }
+            for (int i = tid; i < m; i += nt) {
+                const int v = row_var[i];
+                if (v >= n) {
+                    res[i] = -yv[v - n];
+                    bad += (abskey(yv[v - n]) != 0) ? 1u : 0u;
+                }
+            }
+            unsigned tot, dummy;
+            red.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
+            if (tot == 0) { conv = true; break; }
+            if (it == mp.max_refine) break;
+            fwdbad = 0;
+            for (int c = tid; c < m; c += nt) {
+                const int p = spos[c];
+                double d;
+                if (p > 0) {
+                    float acc = 0.0f;
+                    for (int i = 0; i < m; ++i) acc = __fmaf_rn(__double2float_rn(res[i]), T[i * LD + p], acc);
+                    d = (double)acc;
+                } else {
+                    d = res[-p - 1];
+                }
+                const double ynew = __dadd_rn(yv[c], d);
+                yv[c] = ynew;
+                fwdbad += (abskey(d) > abskey(mp.fwd_tol * fmax(fabs(ynew), yfloor))) ? 1u : 0u;
+            }
+            __syncthreads();
+        }
+        // dual feasibility: y >= -tol and A^T y - c >= -tol on non-basic structurals
+        unsigned bad = 0, dummy;
+        for (int c = tid; c < m; c += nt) bad += (yv[c] < -tol_d) ? 1u : 0u;
+        for (int j = 1 + tid; j <= Cvar; j += nt) {
+            const int v = tb.col_var[j];
+            if (v < n) {
+                double d = -cv[v];
+                for (int c = 0; c < m; ++c) d = __fma_rn(yv[c], A[(size_t)c * n + v], d);
+                bad += (d < -tol_d) ? 1u : 0u;
+            }
+        }
+        red.count_min(bad, 0u, bad, dummy);
+        ok = conv && bad == 0;
+    }
+    if (ok && status == kUnbounded) {
+        // ray: entering variable up by 1, basic variables by d = -B^-1 a_e
+        const int ve = tb.col_var[e_unb];
+        for (int i = tid; i < m; i += nt) dv[i] = -(double)T[i * LD + e_unb];
+        __syncthreads();
+        bool conv;
+        refine(dv, ve, conv);
+        double loc = 0.0;
+        for (int i = tid; i < m; i += nt) loc = (abskey(dv[i]) > abskey(loc)) ? dv[i] : loc;
+        const double dmax = block_absmax(red, loc);
+        unsigned bad = 0, dummy;
+        for (int i = tid; i < m; i += nt) bad += (dv[i] < -mp.cert_tol * fmax(1.0, dmax)) ? 1u : 0u;
+        red.count_min(bad, 0u, bad, dummy);
+        // objective increase along the ray (warp 0, fixed order)
+        __shared__ double s_cd;
+        if (warp == 0) {
+            double part = 0.0;
+            for (int t = lane; t < s; t += 32) {
+                const int i = slist[t];
+                part = __fma_rn(cv[row_var[i]], dv[i], part);
+            }
+            for (int o = 16; o > 0; o >>= 1) part = __dadd_rn(part, __shfl_xor_sync(kFull, part, o));
+            if (lane == 0) s_cd = __dadd_rn(part, (ve < n) ? cv[ve] : 0.0);
+        }
+        __syncthreads();
+        ok = conv && bad == 0 && s_cd > mp.cert_tol * fmax(1.0, dmax) * cmax;
+    }
+
+    if (!ok) {
+        if (tid == 0) {
+            const int pos = atomicAdd(fb_len, 1);
+            if (pos < fb_cap) fb_queue[pos] = lp;
+            else record_internal_error(diag, 4, lp);
+        }
+        return;
+    }
+
+    // ---- certified: FP64 outputs ------------------------------------------------
+    double* __restrict__ x = B.x + B.x_off[lp];
+    double* __restrict__ y = B.y ? B.y + B.y_off[lp] : nullptr;
+    for (int j = 1 + tid; j <= Cvar; j += nt) {
+        const int v = tb.col_var[j];
+        if (v < n) x[v] = 0.0;
+    }
+    for (int i = tid; i < m; i += nt) {
+        const int v = row_var[i];
+        if (v < n) x[v] = xb[i];
+    }
+    if (y) {
+        for (int c = tid; c < m; c += nt) {
+            if (status == kOptimal) {
+                y[c] = yv[c];
+            } else {
+                const int p = spos[c];
+                y[c] = (p > 0) ? (double)T[m * LD + p] : 0.0;
+            }
+        }
+    }
+    __shared__ double s_obj;
+    if (warp == 0) {
+        double part = 0.0;
+        for (int t = lane; t < s; t += 32) {
+            const int i = slist[t];
+            part = __fma_rn(cv[row_var[i]], xb[i], part);
+        }
+        for (int o = 16; o > 0; o >>= 1) part = __dadd_rn(part, __shfl_xor_sync(kFull, part, o));
+        if (lane == 0) s_obj = part;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        B.status[lp] = status;
+        B.iters[lp] = iters;
+        B.obj[lp] = s_obj;
+    }
+}
+
+}  // namespace
+
+cudaError_t mixed_kernel_prepare() {
+    return cudaFuncSetAttribute(mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(kMaxSmemPerBlock - 1024));
+}
+
+cudaError_t launch_mixed(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
+                         const int32_t* order, int32_t count, int threads, size_t smem,
+                         int32_t* fb_queue, int32_t* fb_len, int32_t fb_cap, int32_t* diag, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    mixed_kernel<<<count, threads, smem, stream>>>(B, tol, mp, order, fb_queue, fb_len, fb_cap, diag);
+    return cudaGetLastError();
+}
+
+}  // namespace lpb

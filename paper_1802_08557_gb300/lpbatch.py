@@ -19,7 +19,7 @@ from . import build as _build
 LP_OPTIMAL, LP_INFEASIBLE, LP_UNBOUNDED, LP_ITER_LIMIT, LP_NUMERICAL = 0, 1, 2, 3, 4
 LPB_OK, LPB_EINVAL, LPB_ENOMEM, LPB_ECUDA, LPB_ETOOBIG, LPB_ENOTSOLVED = 0, 1, 2, 3, 4, 5
 LPB_HOST, LPB_DEVICE = 0, 1
-LP_PREC_FP64 = 0
+LP_PREC_FP64, LP_PREC_FP32_REFINE = 0, 1
 LPB_SCHED_AUTO, LPB_SCHED_STREAMED = 0, 1
 LPB_MAX_DIM = 16384
 
@@ -48,6 +48,12 @@ class LPBatchPlan(ctypes.Structure):
         ("num_resident", ctypes.c_int32),
         ("num_streamed", ctypes.c_int32),
         ("num_phase1", ctypes.c_int32),
+        ("num_mixed", ctypes.c_int32),
+        ("num_fallback", ctypes.c_int32),
+        ("internal_errors", ctypes.c_int32),
+        ("internal_error_code", ctypes.c_int32),
+        ("internal_error_lp", ctypes.c_int32),
+        ("internal_error_detail", ctypes.c_int32 * 5),
         ("max_smem_bytes", ctypes.c_int64),
         ("workspace_bytes", ctypes.c_int64),
     ]
@@ -180,7 +186,9 @@ def lp_batch_results(h, status=None, iters=None, obj=None, x=None, y=None, ptr_k
 def lp_batch_plan_info(h) -> dict:
     p = LPBatchPlan()
     _check(load().lp_batch_plan_info(h, ctypes.byref(p)), "lp_batch_plan_info")
-    return {name: getattr(p, name) for name, _ in LPBatchPlan._fields_}
+    out = {name: getattr(p, name) for name, _ in LPBatchPlan._fields_}
+    out["internal_error_detail"] = list(out["internal_error_detail"])
+    return out
 
 
 def lp_solve_uniform_noalloc(num_lps, m, n, A, b, c, status, iters, obj, x, y=None,

@@ -24,6 +24,7 @@ def gpu_solve(batch, device_data=True, opts=None):
         s.solve()
         r = s.results()
         r["plan"] = s.plan_info()
+        assert r["plan"]["internal_errors"] == 0, r["plan"]
     finally:
         s.close()
     return r

@@ -1,0 +1,117 @@
+"""GPU: FP32 tableau + FP64 certificate (LP_PREC_FP32_REFINE) against the
+FP64 oracle.  Status must equal the oracle's exactly; optimal objectives must
+agree within 1e-9 relative (the mixed path's accuracy target); every optimum
+returned must pass an FP64 duality certificate computed here in numpy."""
+import numpy as np
+import pytest
+
+from paper_1802_08557_gb300 import lpbatch as lpb
+from paper_1802_08557_gb300 import workloads as W
+from parity_util import gpu_solve, oracle_solve
+
+pytestmark = pytest.mark.gpu
+
+OBJ_RTOL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1802_08557_gb300 import build
+    build.build()
+    lpb.load()
+
+
+def mixed_opts(**kw):
+    return lpb.lpb_default_opts(precision=lpb.LP_PREC_FP32_REFINE, **kw)
+
+
+def check_mixed(batch, max_fallback_frac=1.0, cert_mask=None):
+    g = gpu_solve(batch, opts=mixed_opts())
+    r = oracle_solve(batch)
+    xo, yo = batch.x_offsets(), batch.y_offsets()
+    for k in range(batch.num_lps):
+        assert g["status"][k] == r["status"][k], f"LP {k}: status {g['status'][k]} vs oracle {r['status'][k]}"
+        if r["status"][k] != 0:
+            continue
+        A, b, c = batch.lp(k)
+        m, n = A.shape
+        go, ro = g["obj"][k], r["obj"][k]
+        assert abs(go - ro) <= OBJ_RTOL * max(1.0, abs(ro)), f"LP {k}: obj {go!r} vs {ro!r}"
+        if cert_mask is not None and not cert_mask[k]:
+            continue
+        x = g["x"][xo[k]:xo[k] + n]
+        y = g["y"][yo[k]:yo[k] + m]
+        sb = max(1.0, np.abs(b).max())
+        sc = max(1.0, np.abs(c).max())
+        assert x.min() >= -1e-9 * sb
+        assert np.all(A @ x <= b + 1e-9 * sb + 1e-12 * (np.abs(A) @ np.abs(x)))
+        assert y.min() >= -1e-9 * sc
+        assert np.all(A.T @ y >= c - 1e-9 * sc - 1e-12 * (np.abs(A).T @ np.abs(y)))
+        assert abs(float(c @ x) - float(b @ y)) <= 1e-9 * max(1.0, abs(float(c @ x)))
+    plan = g["plan"]
+    assert plan["internal_errors"] == 0, plan
+    assert plan["num_mixed"] > 0
+    assert plan["num_fallback"] <= max_fallback_frac * plan["num_mixed"], plan
+    return g, r
+
+
+def test_mixed_dense50x50_phase1():
+    batch = W.mixed_sign_dense(3000, 50, 50, start=777)
+    g, r = check_mixed(batch, max_fallback_frac=0.25)
+    assert set(np.unique(g["status"])) == {0, 1, 2}
+
+
+def test_mixed_dense5x5():
+    check_mixed(W.WORKLOADS["dense5x5_1k"](), max_fallback_frac=0.05)
+
+
+def test_mixed_support_function():
+    check_mixed(W.support_function(2000, start=3), max_fallback_frac=0.05)
+
+
+def test_mixed_shared_matrix_family():
+    check_mixed(W.shared_matrix_family(40, m=200, n=100), max_fallback_frac=0.25)
+
+
+def test_mixed_tiny_and_degenerate():
+    from test_oracle_pins import tiny_lps
+    check_mixed(W.pack("tiny", tiny_lps(4242, 600)))
+
+
+def test_mixed_extreme_scales_fall_back_correctly():
+    """LPs with data outside [2^-60, 2^60] go straight to the FP64 kernel
+    (their results are the FP64 simplex's: status and objective checked);
+    1e6-scaled ones stay on the mixed path and must be certified."""
+    rng = np.random.default_rng(9)
+    lps = []
+    scales = []
+    for t in range(60):
+        m, n = int(rng.integers(3, 15)), int(rng.integers(3, 15))
+        s = [1e30, 1e-30, 1e6][t % 3]
+        scales.append(s)
+        lps.append((rng.uniform(-1, 1, (m, n)) * s, rng.uniform(-0.5, 2, m), rng.uniform(-1, 1, n)))
+    in_range = np.array([s == 1e6 for s in scales])
+    g, r = check_mixed(W.pack("scales", lps), cert_mask=in_range)
+    assert g["plan"]["num_fallback"] >= int((~in_range).sum())
+
+
+@pytest.mark.slow
+def test_full_size_repeat_solves_are_identical():
+    """1e5 LPs of 50 x 50: solving twice gives bitwise identical results on
+    both paths, and no kernel reports an internal-consistency failure."""
+    batch = W.WORKLOADS["dense50x50_phase1_100k"]()
+    for opts in (lpb.lpb_default_opts(), mixed_opts()):
+        s = lpb.BatchSolver(batch, opts=opts)
+        try:
+            s.solve()
+            r1 = s.results()
+            p1 = s.plan_info()
+            s.solve()
+            r2 = s.results()
+            p2 = s.plan_info()
+        finally:
+            s.close()
+        assert p1["internal_errors"] == 0 and p2["internal_errors"] == 0, (p1, p2)
+        assert p1["num_fallback"] == p2["num_fallback"]
+        for key in ("status", "iters", "obj", "x", "y"):
+            np.testing.assert_array_equal(r1[key], r2[key], err_msg=key)
