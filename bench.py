@@ -351,6 +351,7 @@ def run_ours(args):
                        "l2": f"inputs larger than L2 ({in_bytes / 1e9:.2f} GB of A,b,c per step vs 0.13 GB L2)",
                        "launch_groups": launches, "phase1_lps": info["num_phase1"],
                        "fp64_fallback_lps": info["num_fallback"],
+                       "kernel_self_check_failures": info["internal_errors"],
                        "status_counts": {"optimal": int(counts[0]), "infeasible": int(counts[1]),
                                          "unbounded": int(counts[2]), "iter_limit": int(counts[3]),
                                          "numerical": int(counts[4])},

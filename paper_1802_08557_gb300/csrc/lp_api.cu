@@ -407,12 +407,13 @@ lpb_err lp_batch_solve(lp_batch* h, void* stream) {
     }
     for (const Group& g : h->groups) {
         cudaError_t err = lpb::launch_fp64_resident(h->d, h->tol, h->d_order + g.offset, g.count, g.threads,
-                                                    g.smem, s);
+                                                    g.smem, h->diag, s);
         if (err != cudaSuccess) return cuda_fail(err, "solver launch");
     }
     if (h->num_streamed > 0) {
         cudaError_t err = lpb::launch_fp64_streamed(h->d, h->tol, h->d_order + h->streamed_offset, h->num_streamed,
-                                                    h->streamed_slots, h->workspace, h->slot_bytes, h->counter, s);
+                                                    h->streamed_slots, h->workspace, h->slot_bytes, h->counter,
+                                                    h->diag, s);
         if (err != cudaSuccess) return cuda_fail(err, "streamed solver launch");
     }
     h->last_stream = s;

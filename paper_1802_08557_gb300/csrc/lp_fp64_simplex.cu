@@ -133,7 +133,7 @@ __device__ __forceinline__ void retire_column(Tab& tb, int Ract, int e, int& Cva
 // (streamed), laid out by big_layout.
 template <bool kStreamed>
 __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances& tol, const int lp,
-                                          unsigned char* small, unsigned char* big)
+                                          unsigned char* small, unsigned char* big, int32_t* diag)
 {
     const int m = B.m[lp];
     const int n = B.n[lp];
@@ -359,6 +359,24 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         if (tb.col_var[e] >= nm) retire_column(tb, Ract, e, Cvar);
     }
 
+    // ---- labels must name variables (self-check before they index global
+    // memory); a failure is recorded and the LP reported as LP_NUMERICAL ----
+    {
+        unsigned badl = 0, dummy;
+        const unsigned nvar = (unsigned)(nm + k);
+        for (int i = tid; i < m; i += nt) badl += ((unsigned)row_var[i] >= nvar) ? 1u : 0u;
+        for (int j = 1 + tid; j <= Cvar; j += nt) badl += ((unsigned)tb.col_var[j] >= nvar) ? 1u : 0u;
+        red.count_min(badl, 0u, badl, dummy);
+        if (badl) {
+            if (tid == 0) {
+                record_internal_error(diag, 6, lp, (int)badl, status, iters, phase, Cvar);
+                B.status[lp] = kNumerical;
+                B.iters[lp] = iters;
+            }
+            return;
+        }
+    }
+
     // ---- results: x (basic rows -> rhs, non-basic -> 0), y (slack reduced
     // costs of row `yrow`), objective corner, status, pivots -----------------
     double* __restrict__ x = B.x + B.x_off[lp];
@@ -366,13 +384,13 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
     const double* Ty = T + (size_t)yrow * LD;
     for (int j = 1 + tid; j <= Cvar; j += nt) {
         const int v = tb.col_var[j];
-        if (v < n) x[v] = 0.0;
-        else if (v < nm && y) y[v - n] = Ty[j];
+        if ((unsigned)v < (unsigned)n) x[v] = 0.0;
+        else if (v >= n && v < nm && y) y[v - n] = Ty[j];
     }
     for (int i = tid; i < m; i += nt) {
         const int v = row_var[i];
-        if (v < n) x[v] = T[(size_t)i * LD];
-        else if (v < nm && y) y[v - n] = 0.0;
+        if ((unsigned)v < (unsigned)n) x[v] = T[(size_t)i * LD];
+        else if (v >= n && v < nm && y) y[v - n] = 0.0;
     }
     if (tid == 0) {
         B.status[lp] = status;
@@ -381,17 +399,18 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
     }
 }
 
-__global__ void __launch_bounds__(kMaxThreads)
-fp64_resident_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order)
+__global__ void __launch_bounds__(kMaxThreads, 2)
+fp64_resident_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order,
+                     int32_t* __restrict__ diag)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    solve_one<false>(B, tol, order[blockIdx.x], smem, smem + SmallLayout::total);
+    solve_one<false>(B, tol, order[blockIdx.x], smem, smem + SmallLayout::total, diag);
 }
 
 // Resident kernel over a device-side list: persistent CTAs take the LPs
 // queue[0 .. *queue_len) through the atomic `counter` (0 at launch).  Used for
 // the LPs the mixed-precision kernel hands back.
-__global__ void __launch_bounds__(kMaxThreads)
+__global__ void __launch_bounds__(kMaxThreads, 2)
 fp64_resident_queue_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ queue,
                            const int32_t* __restrict__ queue_len, const int32_t queue_cap, const int32_t num_lps,
                            int32_t* __restrict__ counter, int32_t* __restrict__ diag)
@@ -410,7 +429,7 @@ fp64_resident_queue_kernel(const DeviceBatch B, const Tolerances tol, const int3
             if (threadIdx.x == 0) record_internal_error(diag, 5, lp);
             continue;
         }
-        solve_one<false>(B, tol, lp, smem, smem + SmallLayout::total);
+        solve_one<false>(B, tol, lp, smem, smem + SmallLayout::total, diag);
         __syncthreads();
     }
 }
@@ -418,7 +437,7 @@ fp64_resident_queue_kernel(const DeviceBatch B, const Tolerances tol, const int3
 __global__ void __launch_bounds__(kStreamedThreads, 2)
 fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order,
                      const int32_t count, unsigned char* workspace, const size_t slot_bytes,
-                     int32_t* __restrict__ counter)
+                     int32_t* __restrict__ counter, int32_t* __restrict__ diag)
 {
     __shared__ __align__(16) unsigned char small[SmallLayout::total];
     __shared__ int next;
@@ -429,7 +448,7 @@ fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* _
         const int idx = next;
         __syncthreads();
         if (idx >= count) break;
-        solve_one<true>(B, tol, order[idx], small, big);
+        solve_one<true>(B, tol, order[idx], small, big, diag);
         __syncthreads();
     }
 }
@@ -471,19 +490,19 @@ int fp64_streamed_ctas_per_sm() {
 
 cudaError_t launch_fp64_streamed(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
                                  int32_t count, int slots, unsigned char* workspace, size_t slot_bytes,
-                                 int32_t* counter, cudaStream_t stream) {
+                                 int32_t* counter, int32_t* diag, cudaStream_t stream) {
     if (count <= 0) return cudaSuccess;
     cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
     if (err != cudaSuccess) return err;
     fp64_streamed_kernel<<<slots, kStreamedThreads, 0, stream>>>(B, tol, order, count, workspace, slot_bytes,
-                                                                  counter);
+                                                                  counter, diag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fp64_resident(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
-                                 int32_t count, int threads, size_t smem, cudaStream_t stream) {
+                                 int32_t count, int threads, size_t smem, int32_t* diag, cudaStream_t stream) {
     if (count <= 0) return cudaSuccess;
-    fp64_resident_kernel<<<count, threads, smem, stream>>>(B, tol, order);
+    fp64_resident_kernel<<<count, threads, smem, stream>>>(B, tol, order, diag);
     return cudaGetLastError();
 }
 

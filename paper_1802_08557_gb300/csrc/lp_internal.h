@@ -160,14 +160,15 @@ cudaError_t launch_mixed(const DeviceBatch& B, const Tolerances& tol, const Mixe
 // Launchers (lp_fp64_simplex.cu).
 constexpr int kStreamedThreads = 512;
 cudaError_t fp64_kernels_prepare();
+// diag: 8 int32 internal-consistency record (see record_internal_error), or null.
 cudaError_t launch_fp64_resident(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
-                                 int32_t count, int threads, size_t smem, cudaStream_t stream);
+                                 int32_t count, int threads, size_t smem, int32_t* diag, cudaStream_t stream);
 // Persistent CTAs (grid = slots) take LPs of `order` from the atomic `counter`
 // (must be 0 at launch); each CTA keeps its tableau in workspace slot
 // blockIdx.x of `slot_bytes` bytes.
 cudaError_t launch_fp64_streamed(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
                                  int32_t count, int slots, unsigned char* workspace, size_t slot_bytes,
-                                 int32_t* counter, cudaStream_t stream);
+                                 int32_t* counter, int32_t* diag, cudaStream_t stream);
 // CTAs of the streamed kernel that fit on one SM.
 int fp64_streamed_ctas_per_sm();
 // Resident kernel over a device-side LP list (persistent CTAs, atomic

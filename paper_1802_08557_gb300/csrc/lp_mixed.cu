@@ -296,6 +296,20 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
         }
     }
 
+    // ---- labels must name variables: a corrupted one would become a wild
+    // global index below (self-check; the LP is then re-solved in FP64) -----
+    {
+        unsigned badl = 0, dummy;
+        const unsigned nvar = (unsigned)(nm + k);
+        for (int i = tid; i < m; i += nt) badl += ((unsigned)row_var[i] >= nvar) ? 1u : 0u;
+        for (int j = 1 + tid; j <= Cvar; j += nt) badl += ((unsigned)tb.col_var[j] >= nvar) ? 1u : 0u;
+        red.count_min(badl, 0u, badl, dummy);
+        if (badl) {
+            if (tid == 0) record_internal_error(diag, 6, lp, (int)badl, status, iters, phase, Cvar);
+            status = kNumerical;
+        }
+    }
+
     // ---- FP64 certificate ---------------------------------------------------
     bool ok = (status == kOptimal || status == kUnbounded);
     int s = 0;  // basic structurals
@@ -518,11 +532,11 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
     double* __restrict__ y = B.y ? B.y + B.y_off[lp] : nullptr;
     for (int j = 1 + tid; j <= Cvar; j += nt) {
         const int v = tb.col_var[j];
-        if (v < n) x[v] = 0.0;
+        if ((unsigned)v < (unsigned)n) x[v] = 0.0;
     }
     for (int i = tid; i < m; i += nt) {
         const int v = row_var[i];
-        if (v < n) x[v] = xb[i];
+        if ((unsigned)v < (unsigned)n) x[v] = xb[i];
     }
     if (y) {
         for (int c = tid; c < m; c += nt) {

@@ -152,6 +152,6 @@ extern "C" lpb_err lp_solve_uniform_noalloc(int32_t num_lps, int32_t m, int32_t 
     if ((err = cudaGetLastError()) != cudaSuccess) return LPB_ECUDA;
     DeviceBatch B{d.m, d.n, d.a_off, d.b_off, d.c_off, d.x_off, d.y_off, A, b, c, status, iters, obj, x, y};
     // launch_fp64_streamed zeroes the counter on `s` before the kernel.
-    err = launch_fp64_streamed(B, tol, d.order, num_lps, (int)slots, slots_base, slot_bytes, counter, s);
+    err = launch_fp64_streamed(B, tol, d.order, num_lps, (int)slots, slots_base, slot_bytes, counter, nullptr, s);
     return err == cudaSuccess ? LPB_OK : LPB_ECUDA;
 }
