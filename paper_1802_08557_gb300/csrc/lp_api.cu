@@ -87,6 +87,10 @@ long long step1_key_window(double tau) {
     return (long long)std::ceil(tau * std::ldexp(1.0, 54) * (1.0 + std::ldexp(1.0, -30))) + 4;
 }
 
+// Internal streams per batch: launch groups of one solve overlap on them, so
+// small groups do not wait for the large ones.
+constexpr int kLanes = 4;
+
 // Cap of the streamed kernel's global workspace (slots x largest tableau).
 constexpr int64_t kMaxWorkspaceBytes = int64_t(16) << 30;
 
@@ -130,7 +134,11 @@ struct lp_batch {
     int32_t* fb_queue = nullptr;
     int32_t* fb_len = nullptr;
     int32_t* fb_counter = nullptr;
-    int32_t* diag = nullptr;  // 3 int32: internal-consistency failures of the last solve
+    int32_t* diag = nullptr;  // 8 int32: internal-consistency failures of the last solve
+    // internal streams: the launch groups of a solve run concurrently on them
+    cudaStream_t lanes[kLanes] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kLanes] = {};
     int fb_threads = 0, fb_ctas = 0;
     size_t fb_smem = 0;
 };
@@ -148,9 +156,19 @@ cudaError_t alloc(lp_batch* h, T** p, size_t count, cudaStream_t s) {
 }
 
 void release(lp_batch* h, cudaStream_t s) {
+    for (int i = 0; i < kLanes; ++i)
+        if (h->lanes[i]) cudaStreamSynchronize(h->lanes[i]);
     for (void* p : h->allocs) cudaFreeAsync(p, s);
     h->allocs.clear();
     cudaStreamSynchronize(s);
+    for (int i = 0; i < kLanes; ++i) {
+        if (h->ev_join[i]) cudaEventDestroy(h->ev_join[i]);
+        if (h->lanes[i]) cudaStreamDestroy(h->lanes[i]);
+        h->ev_join[i] = nullptr;
+        h->lanes[i] = nullptr;
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    h->ev_fork = nullptr;
 }
 
 }  // namespace
@@ -377,6 +395,12 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     }
     if ((err = alloc(h, &h->diag, 8, s)) || (err = cudaMemsetAsync(h->diag, 0, 32, s)))
         return bail_cuda(err, "diagnostic word allocation");
+    if ((err = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)))
+        return bail_cuda(err, "event creation");
+    for (int i = 0; i < kLanes; ++i)
+        if ((err = cudaStreamCreateWithFlags(&h->lanes[i], cudaStreamNonBlocking)) ||
+            (err = cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming)))
+            return bail_cuda(err, "stream creation");
     if ((err = cudaMemcpyAsync(dorder, order.data(), nl * 4, cudaMemcpyHostToDevice, s)) ||
         (err = lpb::fp64_kernels_prepare()) || (err = cudaStreamSynchronize(s)))
         return bail_cuda(err, "plan upload");
@@ -389,32 +413,52 @@ lpb_err lp_batch_solve(lp_batch* h, void* stream) {
     if (!h) return fail(LPB_EINVAL, "handle is NULL");
     DeviceGuard guard(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    {
-        cudaError_t err = cudaMemsetAsync(h->diag, 0, 8 * sizeof(int32_t), s);
-        if (err != cudaSuccess) return cuda_fail(err, "diagnostic reset");
-    }
-    if (h->num_mixed > 0) {
-        cudaError_t err = cudaMemsetAsync(h->fb_len, 0, sizeof(int32_t), s);
-        if (err != cudaSuccess) return cuda_fail(err, "fallback queue reset");
-        for (const Group& g : h->mixed_groups) {
-            err = lpb::launch_mixed(h->d, h->tol, h->mp, h->d_order + g.offset, g.count, g.threads, g.smem,
-                                    h->fb_queue, h->fb_len, h->num_mixed, h->diag, s);
-            if (err != cudaSuccess) return cuda_fail(err, "mixed-precision launch");
+    cudaError_t err = cudaMemsetAsync(h->diag, 0, 8 * sizeof(int32_t), s);
+    if (err != cudaSuccess) return cuda_fail(err, "diagnostic reset");
+    if (h->num_mixed > 0 && (err = cudaMemsetAsync(h->fb_len, 0, sizeof(int32_t), s)))
+        return cuda_fail(err, "fallback queue reset");
+
+    // Fork: every launch group on an internal stream (largest first, round
+    // robin), all after the work already queued on the caller's stream.
+    struct Job { int kind; const Group* g; int64_t count; };  // kind 0 mixed, 1 resident, 2 streamed
+    std::vector<Job> jobs;
+    for (const Group& g : h->mixed_groups) jobs.push_back({0, &g, g.count});
+    for (const Group& g : h->groups) jobs.push_back({1, &g, g.count});
+    if (h->num_streamed > 0) jobs.push_back({2, nullptr, h->num_streamed});
+    std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& b) { return a.count > b.count; });
+    if ((err = cudaEventRecord(h->ev_fork, s))) return cuda_fail(err, "fork");
+    bool used[kLanes] = {};
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        const int lane = (int)(i % kLanes);
+        cudaStream_t ls = h->lanes[lane];
+        if (!used[lane]) {
+            if ((err = cudaStreamWaitEvent(ls, h->ev_fork, 0))) return cuda_fail(err, "fork wait");
+            used[lane] = true;
         }
+        const Job& j = jobs[i];
+        if (j.kind == 0)
+            err = lpb::launch_mixed(h->d, h->tol, h->mp, h->d_order + j.g->offset, j.g->count, j.g->threads,
+                                    j.g->smem, h->fb_queue, h->fb_len, h->num_mixed, h->diag, ls);
+        else if (j.kind == 1)
+            err = lpb::launch_fp64_resident(h->d, h->tol, h->d_order + j.g->offset, j.g->count, j.g->threads,
+                                            j.g->smem, h->diag, ls);
+        else
+            err = lpb::launch_fp64_streamed(h->d, h->tol, h->d_order + h->streamed_offset, h->num_streamed,
+                                            h->streamed_slots, h->workspace, h->slot_bytes, h->counter, h->diag, ls);
+        if (err != cudaSuccess) return cuda_fail(err, "solver launch");
+    }
+    // Join back onto the caller's stream.
+    for (int lane = 0; lane < kLanes; ++lane) {
+        if (!used[lane]) continue;
+        if ((err = cudaEventRecord(h->ev_join[lane], h->lanes[lane])) ||
+            (err = cudaStreamWaitEvent(s, h->ev_join[lane], 0)))
+            return cuda_fail(err, "join");
+    }
+    // LPs the mixed-precision kernel did not certify: FP64 re-solve.
+    if (h->num_mixed > 0) {
         err = lpb::launch_fp64_resident_queue(h->d, h->tol, h->fb_queue, h->fb_len, h->num_mixed, h->num_lps,
                                               h->fb_counter, h->diag, h->fb_ctas, h->fb_threads, h->fb_smem, s);
         if (err != cudaSuccess) return cuda_fail(err, "fallback launch");
-    }
-    for (const Group& g : h->groups) {
-        cudaError_t err = lpb::launch_fp64_resident(h->d, h->tol, h->d_order + g.offset, g.count, g.threads,
-                                                    g.smem, h->diag, s);
-        if (err != cudaSuccess) return cuda_fail(err, "solver launch");
-    }
-    if (h->num_streamed > 0) {
-        cudaError_t err = lpb::launch_fp64_streamed(h->d, h->tol, h->d_order + h->streamed_offset, h->num_streamed,
-                                                    h->streamed_slots, h->workspace, h->slot_bytes, h->counter,
-                                                    h->diag, s);
-        if (err != cudaSuccess) return cuda_fail(err, "streamed solver launch");
     }
     h->last_stream = s;
     h->solved = true;

@@ -355,18 +355,19 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
 
     // Refine  B z = rhs  (z by tableau row), rhs = b or -(column of rhs_var):
     // z += B^-1 r with the residual r in FP64 from the original data and B^-1
-    // the FP32 one of the tableau.  Converged when (a) every residual is within
-    // conv_tol of |rhs_c| + sum |B_c,i| |z_i| (backward error) and (b) the last
-    // correction moved no component by more than fwd_tol of max(|z_i|,
-    // 1e-8 max|z|) (forward error: an ill-conditioned basis stalls here and is
-    // left to the FP64 re-solve).
+    // the FP32 one of the tableau.  Converged when the residual the last
+    // correction was computed from is within conv_tol of |rhs_c| +
+    // sum |B_c,i| |z_i| (backward error) and that correction moved no
+    // component by more than fwd_tol of max(|z_i|, 1e-8 max|z|) (forward
+    // error: an ill-conditioned basis stalls and is left to the FP64 re-solve).
+    // The tolerance tests run in FP32 (converting costs no FP64-pipe time).
+    const float conv_tol32 = (float)mp.conv_tol, fwd_tol32 = (float)mp.fwd_tol;
     auto refine = [&](double* z, int rhs_var, bool& conv) {
         conv = false;
         double zloc = 0.0;
         for (int i = tid; i < m; i += nt) zloc = (abskey(z[i]) > abskey(zloc)) ? z[i] : zloc;
-        const double zfloor = 1e-8 * block_absmax(red, zloc);
-        unsigned fwdbad = 1;  // no correction measured yet
-        for (int it = 0;; ++it) {
+        const float zfloor = 1e-8f * __double2float_ru(block_absmax(red, zloc));
+        for (int it = 0; it <= mp.max_refine; ++it) {
             unsigned bad = 0;
             for (int c = tid; c < m; c += nt) {
                 double r;
@@ -386,28 +387,27 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                     mag = __fadd_rn(mag, fabs32(__double2float_rn(z[-p - 1])));
                 }
                 res[c] = r;
-                bad += (abskey(r) > abskey(mp.conv_tol * (double)mag)) ? 1u : 0u;
+                bad += (!(fabs32(__double2float_rn(r)) <= conv_tol32 * mag) || isinf(mag)) ? 1u : 0u;
             }
-            unsigned tot, dummy;
-            red.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
-            if (tot == 0) { conv = true; break; }
-            if (it == mp.max_refine) break;
-            fwdbad = 0;
+            __syncthreads();
+            unsigned fwdbad = 0;
             for (int i = tid; i < m; i += nt) {
                 float acc = 0.0f;
                 for (int c = 0; c < m; ++c) {
                     const int p = spos[c];
                     if (p > 0) acc = __fmaf_rn(T[i * LD + p], __double2float_rn(res[c]), acc);
                 }
-                double d = (double)acc;
                 const int v = row_var[i];
-                if (v >= n) d = __dadd_rn(d, res[v - n]);
+                // the correction: B^-1 r (FP32), plus r_c exactly for a basic slack
+                const double d = (v >= n) ? __dadd_rn((double)acc, res[v - n]) : (double)acc;
                 const double znew = __dadd_rn(z[i], d);
                 z[i] = znew;
-                const double lim = mp.fwd_tol * fmax(fabs(znew), zfloor);
-                fwdbad += (abskey(d) > abskey(lim)) ? 1u : 0u;
+                fwdbad += (!(fabs32(__double2float_rn(d)) <= fwd_tol32 * fmaxf(fabs32(__double2float_rn(znew)), zfloor)))
+                              ? 1u : 0u;
             }
-            __syncthreads();
+            unsigned tot, dummy;
+            red.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
+            if (tot == 0) { conv = true; break; }
         }
     };
 
@@ -430,9 +430,8 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
         bool conv = false;
         double yloc = 0.0;
         for (int c = tid; c < m; c += nt) yloc = (abskey(yv[c]) > abskey(yloc)) ? yv[c] : yloc;
-        const double yfloor = 1e-8 * block_absmax(red, yloc);
-        unsigned fwdbad = 1;
-        for (int it = 0;; ++it) {
+        const float yfloor = 1e-8f * __double2float_ru(block_absmax(red, yloc));
+        for (int it = 0; it <= mp.max_refine; ++it) {
             // rho_i = c_(v_i) - y^T col(v_i) for each basic variable (by tableau row)
             unsigned bad = 0;
             for (int t = tid; t < s; t += nt) {
@@ -446,7 +445,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                     mag = __fmaf_rn(fabs32(__double2float_rn(a)), fabs32(__double2float_rn(yv[c])), mag);
                 }
                 res[i] = r;
-                bad += (abskey(r) > abskey(mp.conv_tol * (double)mag)) ? 1u : 0u;
+                bad += (!(fabs32(__double2float_rn(r)) <= conv_tol32 * mag) || isinf(mag)) ? 1u : 0u;
             }
             for (int i = tid; i < m; i += nt) {
                 const int v = row_var[i];
@@ -455,11 +454,8 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                     bad += (abskey(yv[v - n]) != 0) ? 1u : 0u;
                 }
             }
-            unsigned tot, dummy;
-            red.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
-            if (tot == 0) { conv = true; break; }
-            if (it == mp.max_refine) break;
-            fwdbad = 0;
+            __syncthreads();
+            unsigned fwdbad = 0;
             for (int c = tid; c < m; c += nt) {
                 const int p = spos[c];
                 double d;
@@ -472,19 +468,35 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                 }
                 const double ynew = __dadd_rn(yv[c], d);
                 yv[c] = ynew;
-                fwdbad += (abskey(d) > abskey(mp.fwd_tol * fmax(fabs(ynew), yfloor))) ? 1u : 0u;
+                fwdbad += (!(fabs32(__double2float_rn(d)) <= fwd_tol32 * fmaxf(fabs32(__double2float_rn(ynew)), yfloor)))
+                              ? 1u : 0u;
             }
-            __syncthreads();
+            unsigned tot, dummy;
+            red.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
+            if (tot == 0) { conv = true; break; }
         }
-        // dual feasibility: y >= -tol and A^T y - c >= -tol on non-basic structurals
+        // dual feasibility: y >= -tol and A^T y - c >= -tol on non-basic
+        // structurals; each reduced cost is screened in FP32 with an error
+        // bound and computed in FP64 only when the screen cannot decide
         unsigned bad = 0, dummy;
         for (int c = tid; c < m; c += nt) bad += (yv[c] < -tol_d) ? 1u : 0u;
         for (int j = 1 + tid; j <= Cvar; j += nt) {
             const int v = tb.col_var[j];
             if (v < n) {
-                double d = -cv[v];
-                for (int c = 0; c < m; ++c) d = __fma_rn(yv[c], A[(size_t)c * n + v], d);
-                bad += (d < -tol_d) ? 1u : 0u;
+                float d32 = -__double2float_rn(cv[v]);
+                float mag = fabs32(d32);
+                for (int c = 0; c < m; ++c) {
+                    const float a = __double2float_rn(A[(size_t)c * n + v]);
+                    const float yc = __double2float_rn(yv[c]);
+                    d32 = __fmaf_rn(yc, a, d32);
+                    mag = __fmaf_rn(fabs32(yc), fabs32(a), mag);
+                }
+                // |d32 - d| <= (m + 2) * 2^-23 * mag covers the float roundings
+                if (!(d32 - (float)(m + 2) * 1.2e-7f * mag >= -(float)tol_d) || isinf(mag)) {
+                    double d = -cv[v];
+                    for (int c = 0; c < m; ++c) d = __fma_rn(yv[c], A[(size_t)c * n + v], d);
+                    bad += (d < -tol_d) ? 1u : 0u;
+                }
             }
         }
         red.count_min(bad, 0u, bad, dummy);
