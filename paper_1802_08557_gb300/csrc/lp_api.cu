@@ -87,6 +87,18 @@ long long step1_key_window(double tau) {
     return (long long)std::ceil(tau * std::ldexp(1.0, 54) * (1.0 + std::ldexp(1.0, -30))) + 4;
 }
 
+// Mixed-precision LPs with at most this many tableau entries are solved by
+// one warp each (no block barriers); larger ones by a CTA each.
+constexpr int64_t kWarpLpElems = 0;  // warp-per-LP measured slower on 50x50 (too few LPs fit per SM)
+
+// Threads per CTA of the mixed-precision kernel (measured best: 64 for
+// 50x50 tableaux; more for larger ones).
+int mixed_threads(int64_t elems) {
+    if (elems <= 8192) return 64;
+    if (elems <= 32768) return 128;
+    return 256;
+}
+
 // Internal streams per batch: launch groups of one solve overlap on them, so
 // small groups do not wait for the large ones.
 constexpr int kLanes = 4;
@@ -322,9 +334,16 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         const size_t need = lpb::resident_smem_bytes(hm[k], hn[k], hk[k]);
         h->num_phase1 += hk[k] > 0;
         if (o.precision == LP_PREC_FP32_REFINE && o.schedule == LPB_SCHED_AUTO && need <= queue_smem_cap) {
-            // FP32 tableau + FP64 certificate; the FP64 fallback runs resident
-            const size_t msmem = (lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]) + 1023) / 1024 * 1024;
-            const int threads = pick_threads(hm[k], hn[k], hk[k], o.block_threads);
+            // FP32 tableau + FP64 certificate; the FP64 fallback runs resident.
+            // Small tableaux: one warp per LP; larger ones: one CTA per LP.
+            const int64_t elems = (int64_t)(hm[k] + 2) * (hn[k] + hk[k] + 1);
+            const bool warp_lp = o.block_threads == 32 || (o.block_threads == 0 && elems <= kWarpLpElems);
+            const int threads = warp_lp ? 32
+                                        : (o.block_threads > 0 ? std::max(64, pick_threads(hm[k], hn[k], hk[k], o.block_threads))
+                                                               : mixed_threads(elems));
+            const size_t mbytes = warp_lp ? lpb::mixed_layout(hm[k], hn[k], hk[k]).total
+                                          : lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]);
+            const size_t msmem = (mbytes + 1023) / 1024 * 1024;
             mixed_buckets[{threads, msmem}].push_back(k);
             h->fb_smem = std::max(h->fb_smem, need);
             h->fb_threads = std::max(h->fb_threads, threads);

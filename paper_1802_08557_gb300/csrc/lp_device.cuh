@@ -117,5 +117,51 @@ struct Reducer {
     }
 };
 
+
+// The thread group that solves one LP, as a CTA: tid/nt index it, sync() is a
+// block barrier, reductions are the Reducer's.
+struct BlockGroup : Reducer {
+    int tid, nt;
+    __device__ BlockGroup(long long* s64_, unsigned* s32_)
+        : Reducer{s64_, s32_, (int)(blockDim.x >> 5), (int)(threadIdx.x >> 5), (int)(threadIdx.x & 31)},
+          tid((int)threadIdx.x), nt((int)blockDim.x) {}
+    __device__ void sync() { __syncthreads(); }
+};
+
+// The thread group that solves one LP, as a single warp: no block barriers;
+// sync() is __syncwarp (which also orders shared-memory accesses among the
+// lanes) and every reduction is one or two `redux` instructions.  Each
+// reduction starts with __syncwarp so that shared-memory writes made before
+// it are visible to every lane after it.
+struct WarpGroup {
+    int tid, nt, lane, warp, nw;
+    __device__ WarpGroup() : tid((int)(threadIdx.x & 31)), nt(32), lane((int)(threadIdx.x & 31)), warp(0), nw(1) {}
+    __device__ void sync() { __syncwarp(); }
+    __device__ long long min_i64(long long v) {
+        __syncwarp();
+        return warp_min_i64(v);
+    }
+    __device__ unsigned min_u32(unsigned v) {
+        __syncwarp();
+        return __reduce_min_sync(kFull, v);
+    }
+    __device__ int min_i32(int v) {
+        return (int)(min_u32((unsigned)v ^ 0x80000000u) ^ 0x80000000u);
+    }
+    __device__ void count_min(unsigned cnt, unsigned v, unsigned& cnt_out, unsigned& v_out) {
+        __syncwarp();
+        const unsigned c = __reduce_add_sync(kFull, cnt);
+        const unsigned r = __reduce_min_sync(kFull, v);
+        cnt_out = c;
+        v_out = r;
+    }
+    __device__ int prefix_count(bool flag, int& total) {
+        __syncwarp();
+        const unsigned bal = __ballot_sync(kFull, flag);
+        total = __popc(bal);
+        return __popc(bal & ((1u << lane) - 1u));
+    }
+};
+
 }  // namespace
 }  // namespace lpb

@@ -78,8 +78,10 @@ struct Tab {
 // row.  In column e (which now holds the leaving variable) the old entry of the
 // paper's full tableau is the unit column of a basic variable, i.e. 0 off the
 // pivot row and 1 on it, so r_e = 1/PE and t_ie <- fma(-t_ie, r_e, 0).
-// colE[0..Ract) must hold column e on entry.
-__device__ __forceinline__ void pivot(Tab& tb, int Ract, int Cact, int l, int e) {
+// colE[0..Ract) must hold column e on entry.  Returns the variable that left
+// the basis (now the label of column e), read by every thread between the two
+// barriers, where nothing writes it.
+__device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int LD = tb.LD;
     double* T = tb.T;
@@ -96,6 +98,7 @@ __device__ __forceinline__ void pivot(Tab& tb, int Ract, int Cact, int l, int e)
         tb.row_var[l] = ev;
     }
     __syncthreads();
+    const int left = tb.col_var[e];
     const int total = (Ract - 1) * Cact;
     int ii = tid / Cact;
     int jj = tid - ii * Cact;
@@ -111,6 +114,7 @@ __device__ __forceinline__ void pivot(Tab& tb, int Ract, int Cact, int l, int e)
         if (jj >= Cact) { jj -= Cact; ++ii; }
     }
     __syncthreads();
+    return left;
 }
 
 // A retired artificial (it just left the basis and may never re-enter) sits
@@ -171,6 +175,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         }
         k += tot;
     }
+    __syncthreads();  // neg[] and row_var[] are read by other threads below
 
     const BigLayout L = big_layout(m, n, k, kStreamed);
     Tab tb;
@@ -258,9 +263,9 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
                 const int e = (int)(sel & 0xffffu);
                 for (int r = tid; r < m + 1; r += nt) tb.colE[r] = T[(size_t)r * LD + e];
                 __syncthreads();
-                pivot(tb, m + 1, Cvar + 1, i, e);
+                const int left = pivot(tb, m + 1, Cvar + 1, i, e);
                 ++iters;
-                if (tb.col_var[e] >= nm) retire_column(tb, m + 1, e, Cvar);
+                if (left >= nm) retire_column(tb, m + 1, e, Cvar);
             }
             phase = 2;
             continue;
@@ -354,9 +359,9 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         if (iters >= max_iters) { status = kIterLimit; break; }
 
         // ---- Step 3: pivot ---------------------------------------------------
-        pivot(tb, Ract, Cvar + 1, l, e);
+        const int left = pivot(tb, Ract, Cvar + 1, l, e);
         ++iters;
-        if (tb.col_var[e] >= nm) retire_column(tb, Ract, e, Cvar);
+        if (left >= nm) retire_column(tb, Ract, e, Cvar);
     }
 
     // ---- labels must name variables (self-check before they index global

@@ -107,8 +107,8 @@ __host__ __device__ inline size_t streamed_slot_bytes(int m, int n, int k) {
 // and the column labels.
 struct MixedLayout {
     int R, LD;
-    size_t xb, yv, dv, res, rkey, row_var, neg, spos, slist;  // k-independent
-    size_t T, colE, col_var;                                 // k-dependent
+    size_t xb, yv, dv, res, row_var, neg, spos, slist;  // k-independent
+    size_t T, colE, col_var;                           // k-dependent
     size_t total;
 };
 
@@ -122,7 +122,6 @@ __host__ __device__ inline MixedLayout mixed_layout(int m, int n, int k) {
     L.yv = o;      o += align16((size_t)m * 8);
     L.dv = o;      o += align16((size_t)m * 8);
     L.res = o;     o += align16(mn * 8);
-    L.rkey = o;    o += align16((size_t)m * 4);
     L.row_var = o; o += align16((size_t)m * 4);
     L.neg = o;     o += align16((size_t)m * 4);
     L.spos = o;    o += align16((size_t)m * 4);

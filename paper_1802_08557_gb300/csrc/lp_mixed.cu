@@ -45,47 +45,56 @@ struct Tab32 {
     int LD;
 };
 
-// Step 3 in FP32 (same structure as the FP64 pivot).
-__device__ __forceinline__ void pivot32(Tab32& tb, int Ract, int Cact, int l, int e) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+// Step 3 in FP32 (same structure as the FP64 pivot); G is the thread group
+// that owns the LP (BlockGroup or WarpGroup).  Returns the variable that left
+// the basis, read between the two barriers, where nothing writes it.
+template <class G>
+__device__ __forceinline__ int pivot32(G& g, Tab32& tb, int Ract, int Cact, int l, int e) {
+    const int tid = g.tid, nt = g.nt;
     const int LD = tb.LD;
     float* T = tb.T;
     const float* colE = tb.colE;
-    const float pe = colE[l];
+    const float rinv = __frcp_rn(colE[l]);
     float* Tl = T + l * LD;
     for (int j = tid; j < Cact; j += nt) {
         const float v = (j == e) ? 1.0f : Tl[j];
-        Tl[j] = __fdiv_rn(v, pe);
+        Tl[j] = __fmul_rn(v, rinv);
     }
     if (tid == 0) {
         const int ev = tb.col_var[e];
         tb.col_var[e] = tb.row_var[l];
         tb.row_var[l] = ev;
     }
-    __syncthreads();
-    // update: thread (tr, tc) takes columns tc, tc+cw, ... and rows tr, tr+rg,
-    // ...; a warp shares its row, so colE[r] is a broadcast and the pivot-row
-    // value of the column stays in a register
-    const int cw = min(nt, (Cact + 31) & ~31);
-    const int rg = nt / cw;
-    const int tc = tid % cw, tr = tid / cw;
-    if (tr < rg) {
-        for (int j = tc; j < Cact; j += cw) {
-            const float pr = Tl[j];
-            const bool ecol = (j == e);
-            for (int r = tr; r < Ract; r += rg) {
-                if (r == l) continue;
-                float* t = T + r * LD + j;
-                const float old = ecol ? 0.0f : *t;
-                *t = __fmaf_rn(-colE[r], pr, old);
-            }
+    g.sync();
+    const int left = tb.col_var[e];
+    // update: thread (tr, tc) takes columns tc, tc+32, ... and the rows r = tr
+    // (mod rg) on both sides of the pivot row; a warp shares its row, so
+    // colE[r] is a broadcast and the column's pivot-row value stays in a
+    // register.  The entering column (now the leaving variable's) has no old
+    // value: -colE[r] * (1/PE).
+    const int rg = nt >> 5;
+    const int tc = tid & 31, tr = tid >> 5;
+    for (int j = tc; j < Cact; j += 32) {
+        const float pr = Tl[j];
+        float* col = T + j;
+        if (j == e) {
+            for (int r = tr; r < Ract; r += rg)
+                if (r != l) col[r * LD] = -colE[r] * pr;
+        } else {
+#pragma unroll 4
+            for (int r = tr; r < l; r += rg) col[r * LD] = __fmaf_rn(-colE[r], pr, col[r * LD]);
+            const int r0 = l + 1 + ((tr - (l + 1)) % rg + rg) % rg;
+#pragma unroll 4
+            for (int r = r0; r < Ract; r += rg) col[r * LD] = __fmaf_rn(-colE[r], pr, col[r * LD]);
         }
     }
-    __syncthreads();
+    g.sync();
+    return left;
 }
 
-__device__ __forceinline__ void retire_column32(Tab32& tb, int Ract, int e, int& Cvar) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+template <class G>
+__device__ __forceinline__ void retire_column32(G& g, Tab32& tb, int Ract, int e, int& Cvar) {
+    const int tid = g.tid, nt = g.nt;
     if (e != Cvar) {
         for (int r = tid; r < Ract; r += nt) {
             float* row = tb.T + r * tb.LD;
@@ -94,39 +103,37 @@ __device__ __forceinline__ void retire_column32(Tab32& tb, int Ract, int e, int&
         if (tid == 0) tb.col_var[e] = tb.col_var[Cvar];
     }
     --Cvar;
-    __syncthreads();
+    g.sync();
 }
 
-// max |v| of a block (FP64), as a double.
-__device__ __forceinline__ double block_absmax(Reducer& red, double v) {
-    return __longlong_as_double(-red.min_i64(-abskey(v)));
+// max |v| over the group (FP64), as a double.
+template <class G>
+__device__ __forceinline__ double block_absmax(G& g, double v) {
+    return __longlong_as_double(-g.min_i64(-abskey(v)));
 }
 
-__global__ void __launch_bounds__(kMaxThreads, 2)
-mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, const int32_t* __restrict__ order,
-             int32_t* __restrict__ fb_queue, int32_t* __restrict__ fb_len, const int32_t fb_cap,
-             int32_t* __restrict__ diag)
+// One LP on the FP32 tableau, then its FP64 certificate.  `big` is the
+// LP's shared-memory area (mixed_layout); G is the group of threads that owns
+// the LP.
+template <class G>
+__device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
+                                            const int lp, unsigned char* big, int32_t* fb_queue, int32_t* fb_len,
+                                            const int32_t fb_cap, int32_t* diag)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lp = order[blockIdx.x];
     const int m = B.m[lp];
     const int n = B.n[lp];
     const int nm = n + m;
     const double* __restrict__ A = B.A + B.a_off[lp];
     const double* __restrict__ bv = B.b + B.b_off[lp];
     const double* __restrict__ cv = B.c + B.c_off[lp];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    unsigned char* big = smem + SmallLayout::total;
-    Reducer red{reinterpret_cast<long long*>(smem + SmallLayout::red64),
-                reinterpret_cast<unsigned*>(smem + SmallLayout::red32), nw, warp, lane};
+    const int tid = g.tid, nt = g.nt;
+    const int lane = g.lane, warp = g.warp;
 
     const MixedLayout L0 = mixed_layout(m, n, 0);
     double* xb = reinterpret_cast<double*>(big + L0.xb);
     double* yv = reinterpret_cast<double*>(big + L0.yv);
     double* dv = reinterpret_cast<double*>(big + L0.dv);
     double* res = reinterpret_cast<double*>(big + L0.res);
-    int* rkey = reinterpret_cast<int*>(big + L0.rkey);
     int* row_var = reinterpret_cast<int*>(big + L0.row_var);
     int* neg = reinterpret_cast<int*>(big + L0.neg);
     int* spos = reinterpret_cast<int*>(big + L0.spos);
@@ -138,7 +145,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
         const int i = i0 + tid;
         const bool isneg = (i < m) && (bv[i] < 0.0);
         int tot;
-        const int r = k + red.prefix_count(isneg, tot);
+        const int r = k + g.prefix_count(isneg, tot);
         if (i < m) {
             if (isneg) {
                 neg[r] = i;
@@ -149,6 +156,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
         }
         k += tot;
     }
+    g.sync();  // neg[] and row_var[] are read by other threads below
     const MixedLayout L = mixed_layout(m, n, k);
     Tab32 tb;
     tb.T = reinterpret_cast<float*>(big + L.T);
@@ -162,7 +170,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
 
     for (int j = tid; j <= Cvar; j += nt)
         tb.col_var[j] = (j == 0) ? -1 : (j <= n ? j - 1 : n + neg[j - 1 - n]);
-    for (int i = warp; i < m; i += nw) {
+    for (int i = warp; i < m; i += g.nw) {
         const bool isneg = row_var[i] >= nm;
         const double* Ai = A + (size_t)i * n;
         float* Ti = T + i * LD;
@@ -181,8 +189,8 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
     long long bkey = 0x3FF0000000000000LL, ckey = 0x3FF0000000000000LL;  // 1.0
     for (int i = tid; i < m; i += nt) bkey = max(bkey, abskey(bv[i]));
     for (int j = tid; j < n; j += nt) ckey = max(ckey, abskey(cv[j]));
-    const double bmax = __longlong_as_double(-red.min_i64(-bkey));  // barrier: fills done
-    const double cmax = __longlong_as_double(-red.min_i64(-ckey));
+    const double bmax = __longlong_as_double(-g.min_i64(-bkey));  // barrier: fills done
+    const double cmax = __longlong_as_double(-g.min_i64(-ckey));
     // FP32 range: every nonzero |a_ij|, |b_i|, |c_j| within [2^-60, 2^60]
     unsigned out_of_range = 0;
     {
@@ -194,7 +202,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
         for (int i = tid; i < m; i += nt) out_of_range += outside(bv[i]) ? 1u : 0u;
         for (int j = tid; j < n; j += nt) out_of_range += outside(cv[j]) ? 1u : 0u;
         unsigned dummy;
-        red.count_min(out_of_range, 0u, out_of_range, dummy);
+        g.count_min(out_of_range, 0u, out_of_range, dummy);
     }
     if (k > 0) {
         float* Tw = T + (m + 1) * LD;
@@ -203,7 +211,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
             for (int t = 0; t < k; ++t) w = __fsub_rn(w, T[neg[t] * LD + j]);
             Tw[j] = w;
         }
-        __syncthreads();
+        g.sync();
     }
 
     // ---- FP32 simplex (Steps 1-3, two-phase) ----------------------------
@@ -227,7 +235,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
             const int v = tb.col_var[j];
             if (v < nm) dloc = min(dloc, pack_key(fkey(Trow[j]), ((unsigned)v << 16) | (unsigned)j));
         }
-        const long long dsel = red.min_i64(dloc);
+        const long long dsel = g.min_i64(dloc);
         const int dmin = (int)(dsel >> 32);
         if (dsel == LLONG_MAX || dmin >= key_neg_eps_opt) {
             if (phase == 2) { status = kOptimal; break; }
@@ -245,9 +253,9 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                 const float t = T[i * LD + e];
                 tb.colE[i] = t;
                 if (i < m && t > mp.eps_piv32)
-                    rloc = min(rloc, pack_key(fkey(__fdiv_rn(T[i * LD], t)), (unsigned)i));
+                    rloc = min(rloc, pack_key(fkey(__fdividef(T[i * LD], t)), (unsigned)i));
             }
-            const long long rsel = red.min_i64(rloc);
+            const long long rsel = g.min_i64(rloc);
             if (rsel == LLONG_MAX) {
                 if (phase == 2) {
                     status = kUnbounded;
@@ -266,9 +274,9 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                 }
                 if (!isfinite(tb.colE[l])) { status = kNumerical; break; }
                 if (iters >= max_iters) { status = kIterLimit; break; }
-                pivot32(tb, Ract, Cvar + 1, l, e);
+                const int left = pivot32(g, tb, Ract, Cvar + 1, l, e);
                 ++iters;
-                if (tb.col_var[e] >= nm) retire_column32(tb, Ract, e, Cvar);
+                if (left >= nm) retire_column32(g, tb, Ract, e, Cvar);
             }
         }
         if (end_phase1) {
@@ -281,16 +289,20 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                 for (int j = 1 + tid; j <= Cvar; j += nt)
                     if (tb.col_var[j] < nm && fabs32(Ti[j]) > mp.eps_piv32)
                         sel = min(sel, ((unsigned)tb.col_var[j] << 16) | (unsigned)j);
-                sel = red.min_u32(sel);
+                sel = g.min_u32(sel);
                 if (sel == 0xffffffffu) continue;
                 if (iters >= max_iters) { status = kIterLimit; break; }
                 const int e = (int)(sel & 0xffffu);
-                if (e < 1 || e > Cvar) { record_internal_error(diag, 1, lp); status = kNumerical; break; }
+                if (e < 1 || e > Cvar) {
+                    if (tid == 0) record_internal_error(diag, 1, lp, 0, 0, iters, phase, (int)sel);
+                    status = kNumerical;
+                    break;
+                }
                 for (int r = tid; r < m + 1; r += nt) tb.colE[r] = T[r * LD + e];
-                __syncthreads();
-                pivot32(tb, m + 1, Cvar + 1, i, e);
+                g.sync();
+                const int left = pivot32(g, tb, m + 1, Cvar + 1, i, e);
                 ++iters;
-                if (tb.col_var[e] >= nm) retire_column32(tb, m + 1, e, Cvar);
+                if (left >= nm) retire_column32(g, tb, m + 1, e, Cvar);
             }
             phase = 2;
         }
@@ -303,7 +315,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
         const unsigned nvar = (unsigned)(nm + k);
         for (int i = tid; i < m; i += nt) badl += ((unsigned)row_var[i] >= nvar) ? 1u : 0u;
         for (int j = 1 + tid; j <= Cvar; j += nt) badl += ((unsigned)tb.col_var[j] >= nvar) ? 1u : 0u;
-        red.count_min(badl, 0u, badl, dummy);
+        g.count_min(badl, 0u, badl, dummy);
         if (badl) {
             if (tid == 0) record_internal_error(diag, 6, lp, (int)badl, status, iters, phase, Cvar);
             status = kNumerical;
@@ -316,7 +328,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
     if (ok) {
         unsigned nart = 0, dummy;
         for (int i = tid; i < m; i += nt) nart += (row_var[i] >= nm) ? 1u : 0u;
-        red.count_min(nart, 0u, nart, dummy);
+        g.count_min(nart, 0u, nart, dummy);
         ok = (nart == 0);
     }
     if (ok) {
@@ -332,7 +344,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
             if (i < m && v >= n) spos[v - n] = -(i + 1);
             const bool st = (i < m) && (v < n);
             int tot;
-            const int pos = s + red.prefix_count(st, tot);
+            const int pos = s + g.prefix_count(st, tot);
             if (st) slist[pos] = i;
             s += tot;
         }
@@ -342,13 +354,13 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
             const int p = spos[c];
             badpos += (p == 0 || p > Cvar || -p - 1 >= m) ? 1u : 0u;
         }
-        red.count_min(badpos, 0u, badpos, dummy);
+        g.count_min(badpos, 0u, badpos, dummy);
         if (badpos) {
             if (tid == 0) record_internal_error(diag, 3, lp);
             ok = false;
         }
         for (int i = tid; i < m; i += nt) xb[i] = (double)T[i * LD];
-        __syncthreads();
+        g.sync();
     }
     const double tol_p = mp.cert_tol * bmax;
     const double tol_d = mp.cert_tol * cmax;
@@ -366,7 +378,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
         conv = false;
         double zloc = 0.0;
         for (int i = tid; i < m; i += nt) zloc = (abskey(z[i]) > abskey(zloc)) ? z[i] : zloc;
-        const float zfloor = 1e-8f * __double2float_ru(block_absmax(red, zloc));
+        const float zfloor = 1e-8f * __double2float_ru(block_absmax(g, zloc));
         for (int it = 0; it <= mp.max_refine; ++it) {
             unsigned bad = 0;
             for (int c = tid; c < m; c += nt) {
@@ -389,7 +401,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                 res[c] = r;
                 bad += (!(fabs32(__double2float_rn(r)) <= conv_tol32 * mag) || isinf(mag)) ? 1u : 0u;
             }
-            __syncthreads();
+            g.sync();
             unsigned fwdbad = 0;
             for (int i = tid; i < m; i += nt) {
                 float acc = 0.0f;
@@ -406,7 +418,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                               ? 1u : 0u;
             }
             unsigned tot, dummy;
-            red.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
+            g.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
             if (tot == 0) { conv = true; break; }
         }
     };
@@ -417,7 +429,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
         // primal feasibility of the basic solution
         unsigned bad = 0, dummy;
         for (int i = tid; i < m; i += nt) bad += (xb[i] < -tol_p) ? 1u : 0u;
-        red.count_min(bad, 0u, bad, dummy);
+        g.count_min(bad, 0u, bad, dummy);
         ok = conv && bad == 0;
     }
     if (ok && status == kOptimal) {
@@ -426,11 +438,11 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
             const int p = spos[c];
             yv[c] = (p > 0) ? (double)T[m * LD + p] : 0.0;
         }
-        __syncthreads();
+        g.sync();
         bool conv = false;
         double yloc = 0.0;
         for (int c = tid; c < m; c += nt) yloc = (abskey(yv[c]) > abskey(yloc)) ? yv[c] : yloc;
-        const float yfloor = 1e-8f * __double2float_ru(block_absmax(red, yloc));
+        const float yfloor = 1e-8f * __double2float_ru(block_absmax(g, yloc));
         for (int it = 0; it <= mp.max_refine; ++it) {
             // rho_i = c_(v_i) - y^T col(v_i) for each basic variable (by tableau row)
             unsigned bad = 0;
@@ -454,7 +466,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                     bad += (abskey(yv[v - n]) != 0) ? 1u : 0u;
                 }
             }
-            __syncthreads();
+            g.sync();
             unsigned fwdbad = 0;
             for (int c = tid; c < m; c += nt) {
                 const int p = spos[c];
@@ -472,7 +484,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                               ? 1u : 0u;
             }
             unsigned tot, dummy;
-            red.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
+            g.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
             if (tot == 0) { conv = true; break; }
         }
         // dual feasibility: y >= -tol and A^T y - c >= -tol on non-basic
@@ -499,22 +511,22 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
                 }
             }
         }
-        red.count_min(bad, 0u, bad, dummy);
+        g.count_min(bad, 0u, bad, dummy);
         ok = conv && bad == 0;
     }
     if (ok && status == kUnbounded) {
         // ray: entering variable up by 1, basic variables by d = -B^-1 a_e
         const int ve = tb.col_var[e_unb];
         for (int i = tid; i < m; i += nt) dv[i] = -(double)T[i * LD + e_unb];
-        __syncthreads();
+        g.sync();
         bool conv;
         refine(dv, ve, conv);
         double loc = 0.0;
         for (int i = tid; i < m; i += nt) loc = (abskey(dv[i]) > abskey(loc)) ? dv[i] : loc;
-        const double dmax = block_absmax(red, loc);
+        const double dmax = block_absmax(g, loc);
         unsigned bad = 0, dummy;
         for (int i = tid; i < m; i += nt) bad += (dv[i] < -mp.cert_tol * fmax(1.0, dmax)) ? 1u : 0u;
-        red.count_min(bad, 0u, bad, dummy);
+        g.count_min(bad, 0u, bad, dummy);
         // objective increase along the ray (warp 0, fixed order)
         __shared__ double s_cd;
         if (warp == 0) {
@@ -526,7 +538,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
             for (int o = 16; o > 0; o >>= 1) part = __dadd_rn(part, __shfl_xor_sync(kFull, part, o));
             if (lane == 0) s_cd = __dadd_rn(part, (ve < n) ? cv[ve] : 0.0);
         }
-        __syncthreads();
+        g.sync();
         ok = conv && bad == 0 && s_cd > mp.cert_tol * fmax(1.0, dmax) * cmax;
     }
 
@@ -570,7 +582,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
         for (int o = 16; o > 0; o >>= 1) part = __dadd_rn(part, __shfl_xor_sync(kFull, part, o));
         if (lane == 0) s_obj = part;
     }
-    __syncthreads();
+    g.sync();
     if (tid == 0) {
         B.status[lp] = status;
         B.iters[lp] = iters;
@@ -578,10 +590,36 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
     }
 }
 
+__global__ void __launch_bounds__(kMaxThreads, 2)
+mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, const int32_t* __restrict__ order,
+             int32_t* __restrict__ fb_queue, int32_t* __restrict__ fb_len, const int32_t fb_cap,
+             int32_t* __restrict__ diag)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    BlockGroup g(reinterpret_cast<long long*>(smem + SmallLayout::red64),
+                 reinterpret_cast<unsigned*>(smem + SmallLayout::red32));
+    mixed_solve(g, B, tol, mp, order[blockIdx.x], smem + SmallLayout::total, fb_queue, fb_len, fb_cap, diag);
+}
+
+// One warp per LP (blockDim = 32): for small tableaux, where a whole CTA per
+// LP mostly waits at barriers.
+__global__ void __launch_bounds__(32, 32)
+mixed_warp_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, const int32_t* __restrict__ order,
+                  int32_t* __restrict__ fb_queue, int32_t* __restrict__ fb_len, const int32_t fb_cap,
+                  int32_t* __restrict__ diag)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    WarpGroup g;
+    mixed_solve(g, B, tol, mp, order[blockIdx.x], smem, fb_queue, fb_len, fb_cap, diag);
+}
+
 }  // namespace
 
 cudaError_t mixed_kernel_prepare() {
-    return cudaFuncSetAttribute(mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t err = cudaFuncSetAttribute(mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(kMaxSmemPerBlock - 1024));
+    if (err != cudaSuccess) return err;
+    return cudaFuncSetAttribute(mixed_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(kMaxSmemPerBlock - 1024));
 }
 
@@ -589,7 +627,10 @@ cudaError_t launch_mixed(const DeviceBatch& B, const Tolerances& tol, const Mixe
                          const int32_t* order, int32_t count, int threads, size_t smem,
                          int32_t* fb_queue, int32_t* fb_len, int32_t fb_cap, int32_t* diag, cudaStream_t stream) {
     if (count <= 0) return cudaSuccess;
-    mixed_kernel<<<count, threads, smem, stream>>>(B, tol, mp, order, fb_queue, fb_len, fb_cap, diag);
+    if (threads == 32)
+        mixed_warp_kernel<<<count, 32, smem, stream>>>(B, tol, mp, order, fb_queue, fb_len, fb_cap, diag);
+    else
+        mixed_kernel<<<count, threads, smem, stream>>>(B, tol, mp, order, fb_queue, fb_len, fb_cap, diag);
     return cudaGetLastError();
 }
 

@@ -115,3 +115,40 @@ def test_full_size_repeat_solves_are_identical():
         assert p1["num_fallback"] == p2["num_fallback"]
         for key in ("status", "iters", "obj", "x", "y"):
             np.testing.assert_array_equal(r1[key], r2[key], err_msg=key)
+
+
+@pytest.mark.parametrize("threads", [32, 128])
+def test_mixed_warp_and_block_variants(threads):
+    """The FP32 stage runs one warp per LP for small tableaux and one CTA per
+    LP for larger ones; both must certify the same answers as the oracle."""
+    batch = W.mixed_sign_dense(800, 50, 50, start=31337)
+    g = gpu_solve(batch, opts=mixed_opts(block_threads=threads))
+    r = oracle_solve(batch)
+    np.testing.assert_array_equal(g["status"], r["status"])
+    opt = r["status"] == 0
+    np.testing.assert_allclose(g["obj"][opt], r["obj"][opt], rtol=OBJ_RTOL, atol=OBJ_RTOL)
+    big = W.shared_matrix_family(12, m=200, n=100, start=5)
+    g = gpu_solve(big, opts=mixed_opts(block_threads=threads))
+    r = oracle_solve(big)
+    np.testing.assert_array_equal(g["status"], r["status"])
+    np.testing.assert_allclose(g["obj"], r["obj"], rtol=OBJ_RTOL, atol=OBJ_RTOL)
+
+
+@pytest.mark.parametrize("threads", [32, 64, 128, 256])
+def test_repeat_solves_identical_per_group_size(threads):
+    """Every thread-group size gives the same bits on a repeat solve (the
+    phase-I LPs exercise the artificial-column retirement and the ranking of
+    negative rows, both of which order shared-memory accesses across warps)."""
+    batch = W.mixed_sign_dense(20000, 50, 50, start=777)
+    s = lpb.BatchSolver(batch, opts=mixed_opts(block_threads=threads))
+    try:
+        s.solve()
+        r1, p1 = s.results(), s.plan_info()
+        s.solve()
+        r2, p2 = s.results(), s.plan_info()
+    finally:
+        s.close()
+    assert p1["internal_errors"] == 0 and p2["internal_errors"] == 0
+    assert p1["num_fallback"] == p2["num_fallback"]
+    for key in ("status", "iters", "obj", "x", "y"):
+        np.testing.assert_array_equal(r1[key], r2[key], err_msg=key)
