@@ -81,7 +81,8 @@ typedef struct {
     double eps_piv;      /* default 1e-9                                          */
     double eps_feas;     /* default 1e-9                                          */
     double tau;          /* relative tie window, default 1e-12                    */
-    int32_t block_threads; /* threads per LP of the resident kernel; 0 = from the LP size */
+    int32_t block_threads; /* threads per LP (one CTA per LP); 0 = from the LP size;
+                              with LP_PREC_FP32_REFINE, 32 = one warp per LP       */
     int32_t schedule;    /* LPB_SCHED_AUTO or LPB_SCHED_STREAMED                   */
 } lp_batch_opts;
 

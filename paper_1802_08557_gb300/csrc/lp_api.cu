@@ -87,18 +87,6 @@ long long step1_key_window(double tau) {
     return (long long)std::ceil(tau * std::ldexp(1.0, 54) * (1.0 + std::ldexp(1.0, -30))) + 4;
 }
 
-// Mixed-precision LPs with at most this many tableau entries are solved by
-// one warp each (no block barriers); larger ones by a CTA each.
-constexpr int64_t kWarpLpElems = 0;  // warp-per-LP measured slower on 50x50 (too few LPs fit per SM)
-
-// Threads per CTA of the mixed-precision kernel (measured best: 64 for
-// 50x50 tableaux; more for larger ones).
-int mixed_threads(int64_t elems) {
-    if (elems <= 8192) return 64;
-    if (elems <= 32768) return 128;
-    return 256;
-}
-
 // Internal streams per batch: launch groups of one solve overlap on them, so
 // small groups do not wait for the large ones.
 constexpr int kLanes = 4;
@@ -114,6 +102,19 @@ int pick_threads(int m, int n, int k, int requested) {
     if (e <= 8192) return 128;
     if (e <= 32768) return 256;
     return 512;
+}
+
+// Threads per CTA of the mixed-precision kernel; 0 requested = from the
+// tableau size (measured best: 64 for 50x50 tableaux, more for larger ones).
+// A request that rounds to 32 selects the one-warp-per-LP variant (no block
+// barriers; measured slower on 50x50: shared memory caps the LPs per SM, so
+// one warp each leaves fewer warps in flight).
+int mixed_threads(int m, int n, int k, int requested) {
+    if (requested > 0) return pick_threads(m, n, k, requested);
+    const int64_t e = (int64_t)(m + 1 + (k > 0)) * (n + k + 1);
+    if (e <= 8192) return 64;
+    if (e <= 32768) return 128;
+    return 256;
 }
 
 }  // namespace
@@ -335,14 +336,9 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         h->num_phase1 += hk[k] > 0;
         if (o.precision == LP_PREC_FP32_REFINE && o.schedule == LPB_SCHED_AUTO && need <= queue_smem_cap) {
             // FP32 tableau + FP64 certificate; the FP64 fallback runs resident.
-            // Small tableaux: one warp per LP; larger ones: one CTA per LP.
-            const int64_t elems = (int64_t)(hm[k] + 2) * (hn[k] + hk[k] + 1);
-            const bool warp_lp = o.block_threads == 32 || (o.block_threads == 0 && elems <= kWarpLpElems);
-            const int threads = warp_lp ? 32
-                                        : (o.block_threads > 0 ? std::max(64, pick_threads(hm[k], hn[k], hk[k], o.block_threads))
-                                                               : mixed_threads(elems));
-            const size_t mbytes = warp_lp ? lpb::mixed_layout(hm[k], hn[k], hk[k]).total
-                                          : lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]);
+            const int threads = mixed_threads(hm[k], hn[k], hk[k], o.block_threads);
+            const size_t mbytes = threads == 32 ? lpb::mixed_layout(hm[k], hn[k], hk[k]).total
+                                                : lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]);
             const size_t msmem = (mbytes + 1023) / 1024 * 1024;
             mixed_buckets[{threads, msmem}].push_back(k);
             h->fb_smem = std::max(h->fb_smem, need);
