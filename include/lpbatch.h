@@ -178,6 +178,23 @@ typedef struct {
  * outcome of the last solve: this waits for that solve). */
 lpb_err lp_batch_plan_info(lp_batch *h, lp_batch_plan *plan);
 
+/* Device timing of the stages of lp_batch_solve, off by default.  enable != 0
+ * creates CUDA events (timing-capable) that every later solve records on the
+ * caller's stream; enable == 0 waits for the last solve and frees them.  No
+ * counterpart in the paper (which times whole runs, Section 5). */
+lpb_err lp_batch_set_timing(lp_batch *h, int32_t enable);
+
+/* Mean device time, in ms, of the solves recorded since timing was enabled
+ * or since the previous call (at most the last 64 of them):
+ *   stage_ms[0]  every launch group of the solve, from the fork off the
+ *                caller's stream to the join back onto it;
+ *   stage_ms[1]  the FP64 re-solve of the LPs the mixed-precision kernel did
+ *                not certify (about 0 without LP_PREC_FP32_REFINE).
+ * Waits for the last recorded solve.  *num_solves = how many solves the means
+ * cover (0: nothing recorded, stage_ms untouched).  LPB_EINVAL when timing is
+ * not enabled. */
+lpb_err lp_batch_stage_times(lp_batch *h, float *stage_ms, int32_t *num_solves);
+
 /*
  * Solve a batch of LPs that all have the same size m x n without allocating
  * any memory.  There is no counterpart in the paper: it is for callers that

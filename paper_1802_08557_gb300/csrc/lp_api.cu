@@ -91,6 +91,9 @@ long long step1_key_window(double tau) {
 // small groups do not wait for the large ones.
 constexpr int kLanes = 4;
 
+// Solves whose stage times lp_batch_stage_times can average.
+constexpr int kTimingRing = 64;
+
 // Cap of the streamed kernel's global workspace (slots x largest tableau).
 constexpr int64_t kMaxWorkspaceBytes = int64_t(16) << 30;
 
@@ -154,6 +157,10 @@ struct lp_batch {
     cudaEvent_t ev_join[kLanes] = {};
     int fb_threads = 0, fb_ctas = 0;
     size_t fb_smem = 0;
+    // optional stage timing: event triples (start, groups joined, re-solve
+    // done) for the last kTimingRing solves
+    std::vector<cudaEvent_t> tev;
+    int64_t timed_solves = 0;
 };
 
 namespace {
@@ -182,6 +189,8 @@ void release(lp_batch* h, cudaStream_t s) {
     }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     h->ev_fork = nullptr;
+    for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+    h->tev.clear();
 }
 
 }  // namespace
@@ -441,6 +450,8 @@ lpb_err lp_batch_solve(lp_batch* h, void* stream) {
     for (const Group& g : h->groups) jobs.push_back({1, &g, g.count});
     if (h->num_streamed > 0) jobs.push_back({2, nullptr, h->num_streamed});
     std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& b) { return a.count > b.count; });
+    cudaEvent_t* tev = h->tev.empty() ? nullptr : &h->tev[3 * (size_t)(h->timed_solves % kTimingRing)];
+    if (tev && (err = cudaEventRecord(tev[0], s))) return cuda_fail(err, "timing");
     if ((err = cudaEventRecord(h->ev_fork, s))) return cuda_fail(err, "fork");
     bool used[kLanes] = {};
     for (size_t i = 0; i < jobs.size(); ++i) {
@@ -469,11 +480,16 @@ lpb_err lp_batch_solve(lp_batch* h, void* stream) {
             (err = cudaStreamWaitEvent(s, h->ev_join[lane], 0)))
             return cuda_fail(err, "join");
     }
+    if (tev && (err = cudaEventRecord(tev[1], s))) return cuda_fail(err, "timing");
     // LPs the mixed-precision kernel did not certify: FP64 re-solve.
     if (h->num_mixed > 0) {
         err = lpb::launch_fp64_resident_queue(h->d, h->tol, h->fb_queue, h->fb_len, h->num_mixed, h->num_lps,
                                               h->fb_counter, h->diag, h->fb_ctas, h->fb_threads, h->fb_smem, s);
         if (err != cudaSuccess) return cuda_fail(err, "fallback launch");
+    }
+    if (tev) {
+        if ((err = cudaEventRecord(tev[2], s))) return cuda_fail(err, "timing");
+        ++h->timed_solves;
     }
     h->last_stream = s;
     h->solved = true;
@@ -497,6 +513,59 @@ lpb_err lp_batch_results(lp_batch* h, int32_t* status, int32_t* iters, double* o
     if (x && (err = cudaMemcpyAsync(x, h->d.x, (size_t)h->total_x * 8, kind, s))) return cuda_fail(err, "copy x");
     if (y && (err = cudaMemcpyAsync(y, h->d.y, (size_t)h->total_y * 8, kind, s))) return cuda_fail(err, "copy y");
     if ((err = cudaStreamSynchronize(s))) return cuda_fail(err, "solve");
+    return LPB_OK;
+}
+
+lpb_err lp_batch_set_timing(lp_batch* h, int32_t enable) {
+    g_last_error.clear();
+    if (!h) return fail(LPB_EINVAL, "handle is NULL");
+    DeviceGuard guard(h->device);
+    if (!enable) {
+        if (h->solved && !h->tev.empty()) cudaStreamSynchronize(h->last_stream);
+        for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+        h->tev.clear();
+        h->timed_solves = 0;
+        return LPB_OK;
+    }
+    if (!h->tev.empty()) return LPB_OK;
+    h->tev.assign(3 * (size_t)kTimingRing, nullptr);
+    for (cudaEvent_t& e : h->tev) {
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) {
+            for (cudaEvent_t& f : h->tev)
+                if (f) cudaEventDestroy(f);
+            h->tev.clear();
+            return cuda_fail(err, "timing events");
+        }
+    }
+    h->timed_solves = 0;
+    return LPB_OK;
+}
+
+lpb_err lp_batch_stage_times(lp_batch* h, float* stage_ms, int32_t* num_solves) {
+    g_last_error.clear();
+    if (!h || !stage_ms || !num_solves) return fail(LPB_EINVAL, "handle, stage_ms or num_solves is NULL");
+    *num_solves = 0;
+    if (h->tev.empty()) return fail(LPB_EINVAL, "stage timing is not enabled (lp_batch_set_timing)");
+    const int64_t n = std::min<int64_t>(h->timed_solves, kTimingRing);
+    if (n == 0) return LPB_OK;
+    DeviceGuard guard(h->device);
+    const int64_t last = (h->timed_solves - 1) % kTimingRing;
+    cudaError_t err = cudaEventSynchronize(h->tev[3 * last + 2]);
+    if (err != cudaSuccess) return cuda_fail(err, "timing wait");
+    double sum0 = 0.0, sum1 = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        float a = 0.0f, b = 0.0f;
+        if ((err = cudaEventElapsedTime(&a, h->tev[3 * i], h->tev[3 * i + 1])) ||
+            (err = cudaEventElapsedTime(&b, h->tev[3 * i + 1], h->tev[3 * i + 2])))
+            return cuda_fail(err, "timing read");
+        sum0 += a;
+        sum1 += b;
+    }
+    stage_ms[0] = (float)(sum0 / (double)n);
+    stage_ms[1] = (float)(sum1 / (double)n);
+    *num_solves = (int32_t)n;
+    h->timed_solves = 0;
     return LPB_OK;
 }
 

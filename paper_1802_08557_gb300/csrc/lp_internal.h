@@ -103,8 +103,8 @@ __host__ __device__ inline size_t streamed_slot_bytes(int m, int n, int k) {
 
 // Shared-memory layout of the mixed-precision kernel (after SmallLayout):
 // FP64 certification vectors and per-row arrays first (k-independent), then
-// the FP32 condensed tableau (R x LD floats, odd stride), its pivot-column copy
-// and the column labels.
+// the FP32 condensed tableau (R x LD floats, LD a multiple of 4), its
+// pivot-column copy and the column labels.
 struct MixedLayout {
     int R, LD;
     size_t xb, yv, dv, res, row_var, neg, spos, slist;  // k-independent
@@ -115,7 +115,7 @@ struct MixedLayout {
 __host__ __device__ inline MixedLayout mixed_layout(int m, int n, int k) {
     MixedLayout L;
     L.R = m + 1 + (k > 0 ? 1 : 0);
-    L.LD = (n + k + 1) | 1;
+    L.LD = (n + k + 1 + 3) & ~3;  // 16-byte rows for the quad update
     const size_t mn = (size_t)(m > n ? m : n);
     size_t o = 0;
     L.xb = o;      o += align16((size_t)m * 8);

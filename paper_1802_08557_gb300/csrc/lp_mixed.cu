@@ -45,21 +45,50 @@ struct Tab32 {
     int LD;
 };
 
-// Step 3 in FP32 (same structure as the FP64 pivot); G is the thread group
-// that owns the LP (BlockGroup or WarpGroup).  Returns the variable that left
-// the basis, read between the two barriers, where nothing writes it.
+// Thread layout of the pivot update over quads of 4 columns: thread tid takes
+// quads q0, q0 + qstep, ... and rows r0, r0 + rg, ...  It depends only on the
+// number of active columns, so it is recomputed only when that changes.
+struct QuadMap {
+    int cact, q0, qstep, r0, rg;
+};
+
+__device__ __forceinline__ QuadMap quad_map(int tid, int nt, int Cact) {
+    QuadMap m;
+    m.cact = Cact;
+    const int nq = (Cact + 3) >> 2;
+    if (nq >= nt) {
+        m.q0 = tid; m.qstep = nt; m.r0 = 0; m.rg = 1;
+    } else {
+        m.rg = nt / nq;
+        m.r0 = tid / nq;
+        m.q0 = tid - m.r0 * nq; m.qstep = nq;
+        if (m.r0 >= m.rg) m.q0 = nq;  // idle in the update
+    }
+    return m;
+}
+
+// Step 3 in FP32; G is the thread group that owns the LP (BlockGroup or
+// WarpGroup).  Returns the variable that left the basis, read between the two
+// barriers, where nothing writes it.
+//  phase A: pivot row l times 1/PE (its column e becomes 1/PE); column e of
+//           every other row set to 0, so that the uniform update of phase B
+//           gives fma(-t_ie, 1/PE, 0) = -t_ie/PE there (the leaving variable's
+//           column);
+//  phase B: t_rj = fma(-t_re, r_j, t_rj) for r != l over quads of 4 columns
+//           (16-byte loads and stores; LD is a multiple of 4), 4 rows per
+//           batch with every load of a batch issued before its stores.
+//  Columns of the last quad beyond Cact are padding: updated, never read.
 template <class G>
-__device__ __forceinline__ int pivot32(G& g, Tab32& tb, int Ract, int Cact, int l, int e) {
+__device__ __forceinline__ int pivot32(G& g, Tab32& tb, int Ract, int Cact, int l, int e, const QuadMap& qm) {
     const int tid = g.tid, nt = g.nt;
     const int LD = tb.LD;
     float* T = tb.T;
     const float* colE = tb.colE;
     const float rinv = __frcp_rn(colE[l]);
     float* Tl = T + l * LD;
-    for (int j = tid; j < Cact; j += nt) {
-        const float v = (j == e) ? 1.0f : Tl[j];
-        Tl[j] = __fmul_rn(v, rinv);
-    }
+    for (int j = tid; j < Cact; j += nt) Tl[j] = (j == e) ? rinv : __fmul_rn(Tl[j], rinv);
+    for (int r = tid; r < Ract; r += nt)
+        if (r != l) T[r * LD + e] = 0.0f;
     if (tid == 0) {
         const int ev = tb.col_var[e];
         tb.col_var[e] = tb.row_var[l];
@@ -67,25 +96,39 @@ __device__ __forceinline__ int pivot32(G& g, Tab32& tb, int Ract, int Cact, int 
     }
     g.sync();
     const int left = tb.col_var[e];
-    // update: thread (tr, tc) takes columns tc, tc+32, ... and the rows r = tr
-    // (mod rg) on both sides of the pivot row; a warp shares its row, so
-    // colE[r] is a broadcast and the column's pivot-row value stays in a
-    // register.  The entering column (now the leaving variable's) has no old
-    // value: -colE[r] * (1/PE).
-    const int rg = nt >> 5;
-    const int tc = tid & 31, tr = tid >> 5;
-    for (int j = tc; j < Cact; j += 32) {
-        const float pr = Tl[j];
-        float* col = T + j;
-        if (j == e) {
-            for (int r = tr; r < Ract; r += rg)
-                if (r != l) col[r * LD] = -colE[r] * pr;
-        } else {
-#pragma unroll 4
-            for (int r = tr; r < l; r += rg) col[r * LD] = __fmaf_rn(-colE[r], pr, col[r * LD]);
-            const int r0 = l + 1 + ((tr - (l + 1)) % rg + rg) % rg;
-#pragma unroll 4
-            for (int r = r0; r < Ract; r += rg) col[r * LD] = __fmaf_rn(-colE[r], pr, col[r * LD]);
+    const int nq = (Cact + 3) >> 2;
+    const int qstep = qm.qstep, r0 = qm.r0, rg = qm.rg;
+    for (int q = qm.q0; q < nq; q += qstep) {
+        const float4 p = *reinterpret_cast<const float4*>(Tl + 4 * q);
+        float* base = T + 4 * q;
+        int r = r0;
+        for (; r + 3 * rg < Ract; r += 4 * rg) {
+            float4* a0 = reinterpret_cast<float4*>(base + r * LD);
+            float4* a1 = reinterpret_cast<float4*>(base + (r + rg) * LD);
+            float4* a2 = reinterpret_cast<float4*>(base + (r + 2 * rg) * LD);
+            float4* a3 = reinterpret_cast<float4*>(base + (r + 3 * rg) * LD);
+            float4 v0 = *a0, v1 = *a1, v2 = *a2, v3 = *a3;
+            const float c0 = -colE[r], c1 = -colE[r + rg], c2 = -colE[r + 2 * rg], c3 = -colE[r + 3 * rg];
+            v0.x = __fmaf_rn(c0, p.x, v0.x); v0.y = __fmaf_rn(c0, p.y, v0.y);
+            v0.z = __fmaf_rn(c0, p.z, v0.z); v0.w = __fmaf_rn(c0, p.w, v0.w);
+            v1.x = __fmaf_rn(c1, p.x, v1.x); v1.y = __fmaf_rn(c1, p.y, v1.y);
+            v1.z = __fmaf_rn(c1, p.z, v1.z); v1.w = __fmaf_rn(c1, p.w, v1.w);
+            v2.x = __fmaf_rn(c2, p.x, v2.x); v2.y = __fmaf_rn(c2, p.y, v2.y);
+            v2.z = __fmaf_rn(c2, p.z, v2.z); v2.w = __fmaf_rn(c2, p.w, v2.w);
+            v3.x = __fmaf_rn(c3, p.x, v3.x); v3.y = __fmaf_rn(c3, p.y, v3.y);
+            v3.z = __fmaf_rn(c3, p.z, v3.z); v3.w = __fmaf_rn(c3, p.w, v3.w);
+            if (r != l) *a0 = v0;
+            if (r + rg != l) *a1 = v1;
+            if (r + 2 * rg != l) *a2 = v2;
+            if (r + 3 * rg != l) *a3 = v3;
+        }
+        for (; r < Ract; r += rg) {
+            float4* a0 = reinterpret_cast<float4*>(base + r * LD);
+            float4 v0 = *a0;
+            const float c0 = -colE[r];
+            v0.x = __fmaf_rn(c0, p.x, v0.x); v0.y = __fmaf_rn(c0, p.y, v0.y);
+            v0.z = __fmaf_rn(c0, p.z, v0.z); v0.w = __fmaf_rn(c0, p.w, v0.w);
+            if (r != l) *a0 = v0;
         }
     }
     g.sync();
@@ -170,15 +213,36 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
 
     for (int j = tid; j <= Cvar; j += nt)
         tb.col_var[j] = (j == 0) ? -1 : (j <= n ? j - 1 : n + neg[j - 1 - n]);
+    // FP32 range: every nonzero |a_ij|, |b_i|, |c_j| within [2^-60, 2^60]
+    auto outside = [](double v) {
+        const long long a = abskey(v);
+        return a != 0 && (a < 0x3C30000000000000LL || a > 0x43B0000000000000LL);
+    };
+    unsigned out_of_range = 0;
+    {
+        // A into rows 0..m-1, columns 1..n: one flat pass over the LP's A with
+        // several independent loads in flight per thread
+        const int mn = m * n;
+        const int di = nt / n, dj = nt - di * n;
+        int i = tid / n, j = tid - i * n;
+#pragma unroll 4
+        for (int idx = tid; idx < mn; idx += nt) {
+            const double a = A[idx];
+            out_of_range += outside(a) ? 1u : 0u;
+            const float v = __double2float_rn(a);
+            T[i * LD + 1 + j] = (row_var[i] >= nm) ? -v : v;
+            i += di;
+            j += dj;
+            if (j >= n) { j -= n; ++i; }
+        }
+    }
+    // column 0 (b) and the slack columns of the negated rows
     for (int i = warp; i < m; i += g.nw) {
         const bool isneg = row_var[i] >= nm;
-        const double* Ai = A + (size_t)i * n;
         float* Ti = T + i * LD;
-        for (int j = lane; j <= Cvar; j += 32) {
-            float v;
-            if (j == 0) v = __double2float_rn(bv[i]);
-            else if (j <= n) v = __double2float_rn(Ai[j - 1]);
-            else v = (neg[j - 1 - n] == i) ? 1.0f : 0.0f;
+        for (int t = lane; t <= k; t += 32) {
+            const int j = (t == 0) ? 0 : n + t;
+            const float v = (t == 0) ? __double2float_rn(bv[i]) : ((neg[t - 1] == i) ? 1.0f : 0.0f);
             Ti[j] = isneg ? -v : v;
         }
     }
@@ -187,20 +251,17 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
         for (int j = tid; j <= Cvar; j += nt) Tm[j] = (j >= 1 && j <= n) ? -__double2float_rn(cv[j - 1]) : 0.0f;
     }
     long long bkey = 0x3FF0000000000000LL, ckey = 0x3FF0000000000000LL;  // 1.0
-    for (int i = tid; i < m; i += nt) bkey = max(bkey, abskey(bv[i]));
-    for (int j = tid; j < n; j += nt) ckey = max(ckey, abskey(cv[j]));
+    for (int i = tid; i < m; i += nt) {
+        bkey = max(bkey, abskey(bv[i]));
+        out_of_range += outside(bv[i]) ? 1u : 0u;
+    }
+    for (int j = tid; j < n; j += nt) {
+        ckey = max(ckey, abskey(cv[j]));
+        out_of_range += outside(cv[j]) ? 1u : 0u;
+    }
     const double bmax = __longlong_as_double(-g.min_i64(-bkey));  // barrier: fills done
     const double cmax = __longlong_as_double(-g.min_i64(-ckey));
-    // FP32 range: every nonzero |a_ij|, |b_i|, |c_j| within [2^-60, 2^60]
-    unsigned out_of_range = 0;
     {
-        auto outside = [](double v) {
-            const long long a = abskey(v);
-            return a != 0 && (a < 0x3C30000000000000LL || a > 0x43B0000000000000LL);
-        };
-        for (int idx = tid; idx < m * n; idx += nt) out_of_range += outside(A[idx]) ? 1u : 0u;
-        for (int i = tid; i < m; i += nt) out_of_range += outside(bv[i]) ? 1u : 0u;
-        for (int j = tid; j < n; j += nt) out_of_range += outside(cv[j]) ? 1u : 0u;
         unsigned dummy;
         g.count_min(out_of_range, 0u, out_of_range, dummy);
     }
@@ -221,6 +282,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
     int status = -1;
     int phase = (k > 0) ? 1 : 2;
     int e_unb = -1;
+    QuadMap qm = quad_map(tid, nt, Cvar + 1);
     if (out_of_range) status = kNumerical;  // straight to the FP64 kernel
 
     while (status < 0) {
@@ -274,7 +336,8 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
                 }
                 if (!isfinite(tb.colE[l])) { status = kNumerical; break; }
                 if (iters >= max_iters) { status = kIterLimit; break; }
-                const int left = pivot32(g, tb, Ract, Cvar + 1, l, e);
+                if (qm.cact != Cvar + 1) qm = quad_map(tid, nt, Cvar + 1);
+                const int left = pivot32(g, tb, Ract, Cvar + 1, l, e, qm);
                 ++iters;
                 if (left >= nm) retire_column32(g, tb, Ract, e, Cvar);
             }
@@ -300,7 +363,8 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
                 }
                 for (int r = tid; r < m + 1; r += nt) tb.colE[r] = T[r * LD + e];
                 g.sync();
-                const int left = pivot32(g, tb, m + 1, Cvar + 1, i, e);
+                if (qm.cact != Cvar + 1) qm = quad_map(tid, nt, Cvar + 1);
+                const int left = pivot32(g, tb, m + 1, Cvar + 1, i, e, qm);
                 ++iters;
                 if (left >= nm) retire_column32(g, tb, m + 1, e, Cvar);
             }
@@ -387,6 +451,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
                 else r = (rhs_var < n) ? -A[(size_t)c * n + rhs_var] : ((rhs_var - n == c) ? -1.0 : 0.0);
                 float mag = fabs32(__double2float_rn(r));
                 const double* Ac = A + (size_t)c * n;
+#pragma unroll 4
                 for (int t = 0; t < s; ++t) {
                     const int i = slist[t];
                     const double a = Ac[row_var[i]];
@@ -405,6 +470,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
             unsigned fwdbad = 0;
             for (int i = tid; i < m; i += nt) {
                 float acc = 0.0f;
+#pragma unroll 4
                 for (int c = 0; c < m; ++c) {
                     const int p = spos[c];
                     if (p > 0) acc = __fmaf_rn(T[i * LD + p], __double2float_rn(res[c]), acc);
@@ -451,6 +517,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
                 const int v = row_var[i];
                 double r = cv[v];
                 float mag = fabs32(__double2float_rn(r));
+#pragma unroll 4
                 for (int c = 0; c < m; ++c) {
                     const double a = A[(size_t)c * n + v];
                     r = __fma_rn(-yv[c], a, r);
@@ -473,6 +540,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
                 double d;
                 if (p > 0) {
                     float acc = 0.0f;
+#pragma unroll 4
                     for (int i = 0; i < m; ++i) acc = __fmaf_rn(__double2float_rn(res[i]), T[i * LD + p], acc);
                     d = (double)acc;
                 } else {
@@ -497,6 +565,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
             if (v < n) {
                 float d32 = -__double2float_rn(cv[v]);
                 float mag = fabs32(d32);
+#pragma unroll 4
                 for (int c = 0; c < m; ++c) {
                     const float a = __double2float_rn(A[(size_t)c * n + v]);
                     const float yc = __double2float_rn(yv[c]);
@@ -506,6 +575,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
                 // |d32 - d| <= (m + 2) * 2^-23 * mag covers the float roundings
                 if (!(d32 - (float)(m + 2) * 1.2e-7f * mag >= -(float)tol_d) || isinf(mag)) {
                     double d = -cv[v];
+#pragma unroll 4
                     for (int c = 0; c < m; ++c) d = __fma_rn(yv[c], A[(size_t)c * n + v], d);
                     bad += (d < -tol_d) ? 1u : 0u;
                 }

@@ -25,8 +25,8 @@ LPB_MAX_DIM = 16384
 
 # Every symbol include/lpbatch.h declares.
 EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_results",
-            "lp_batch_plan_info", "lp_batch_destroy", "lpb_strerror", "lpb_last_error",
-            "lp_solve_uniform_noalloc")
+            "lp_batch_plan_info", "lp_batch_set_timing", "lp_batch_stage_times", "lp_batch_destroy",
+            "lpb_strerror", "lpb_last_error", "lp_solve_uniform_noalloc")
 
 
 class LPBatchOpts(ctypes.Structure):
@@ -100,6 +100,10 @@ def load(path: str | None = None):
         L.lp_batch_results.restype = ctypes.c_int
         L.lp_batch_plan_info.argtypes = [_vp, ctypes.POINTER(LPBatchPlan)]
         L.lp_batch_plan_info.restype = ctypes.c_int
+        L.lp_batch_set_timing.argtypes = [_vp, _i32]
+        L.lp_batch_set_timing.restype = ctypes.c_int
+        L.lp_batch_stage_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_i32)]
+        L.lp_batch_stage_times.restype = ctypes.c_int
         L.lp_batch_destroy.argtypes = [_vp]
         L.lp_batch_destroy.restype = ctypes.c_int
         L.lpb_strerror.argtypes = [ctypes.c_int]
@@ -189,6 +193,19 @@ def lp_batch_plan_info(h) -> dict:
     out = {name: getattr(p, name) for name, _ in LPBatchPlan._fields_}
     out["internal_error_detail"] = list(out["internal_error_detail"])
     return out
+
+
+def lp_batch_set_timing(h, enable: bool = True):
+    _check(load().lp_batch_set_timing(h, 1 if enable else 0), "lp_batch_set_timing")
+
+
+def lp_batch_stage_times(h):
+    """(mean ms of all launch groups, mean ms of the FP64 re-solve, solves
+    covered) since timing was enabled or last read."""
+    ms = (ctypes.c_float * 2)()
+    n = _i32(0)
+    _check(load().lp_batch_stage_times(h, ms, ctypes.byref(n)), "lp_batch_stage_times")
+    return float(ms[0]), float(ms[1]), int(n.value)
 
 
 def lp_solve_uniform_noalloc(num_lps, m, n, A, b, c, status, iters, obj, x, y=None,

@@ -152,3 +152,25 @@ def test_repeat_solves_identical_per_group_size(threads):
     assert p1["num_fallback"] == p2["num_fallback"]
     for key in ("status", "iters", "obj", "x", "y"):
         np.testing.assert_array_equal(r1[key], r2[key], err_msg=key)
+
+
+def test_stage_timing_reports_both_stages():
+    """lp_batch_set_timing / lp_batch_stage_times: CUDA-event times of the
+    launch groups and of the FP64 re-solve, averaged over the solves since
+    timing was enabled; an error when timing is off."""
+    batch = W.mixed_sign_dense(400, 50, 50, start=99)
+    s = lpb.BatchSolver(batch, opts=mixed_opts())
+    try:
+        with pytest.raises(lpb.LPBError):
+            lpb.lp_batch_stage_times(s.h)
+        lpb.lp_batch_set_timing(s.h, True)
+        s.solve()
+        s.solve()
+        main_ms, fb_ms, n = lpb.lp_batch_stage_times(s.h)
+        assert n == 2 and main_ms > 0.0 and fb_ms >= 0.0
+        assert lpb.lp_batch_stage_times(s.h)[2] == 0  # read resets the count
+        lpb.lp_batch_set_timing(s.h, False)
+        s.solve()
+        assert s.plan_info()["internal_errors"] == 0
+    finally:
+        s.close()
