@@ -35,6 +35,8 @@ DEFAULT_WORKLOAD = "dense50x50_phase1_100k"
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz.
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
+# HBM bandwidth of a GB300 measured with a STREAM-style copy (read + write bytes)
+HBM_PEAK_GBS = 6784.5
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -49,6 +51,8 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=20000, help="LPs timed for the CPU oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-hyperbox", action="store_true", help="skip the hyperbox LP (Eq. 7) measurement")
+    p.add_argument("--hyperbox-dirs", type=int, default=1 << 22, help="directions of the hyperbox measurement")
     p.add_argument("--precision", default="fp32r", choices=["fp32r", "fp64"],
                    help="headline path: FP32 tableau + FP64 certificate (default) or plain FP64")
     return p.parse_args()
@@ -187,6 +191,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
 
     from paper_1802_08557_gb300 import build, lpbatch as lpb
+    from paper_1802_08557_gb300 import workloads as W
     build.build()
     lpb.load()
 
@@ -308,6 +313,44 @@ def run_ours(args):
                     "timing": "CUDA events around the solve's launch groups (all mixed_kernel launches, "
                               "fork to join), mean of the timed steps"}
 
+    # ---- hyperbox LPs (Section 4.4, Eq. 7): support function of one box ----
+    hyperbox = None
+    if not args.no_hyperbox:
+        hb_num, hb_dim = args.hyperbox_dirs, 28
+        Lh, loh, hih = W.hyperbox_directions(hb_num, hb_dim, start=rank * hb_num)
+        dL = torch.from_numpy(Lh).to(dev)
+        dlo, dhi = torch.from_numpy(loh).to(dev), torch.from_numpy(hih).to(dev)
+        dobj = torch.empty(hb_num, dtype=torch.float64, device=dev)
+        del Lh
+        for _ in range(max(3, args.warmup)):
+            lpb.lp_hyperbox_solve(dL, dlo, dhi, dobj, None, ptr_kind=lpb.LPB_DEVICE, stream=stream)
+        torch.cuda.synchronize()
+        hb_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+        barrier()
+        for s_ in range(args.steps):
+            hb_ev[s_][0].record(stream)
+            lpb.lp_hyperbox_solve(dL, dlo, dhi, dobj, None, ptr_kind=lpb.LPB_DEVICE, stream=stream)
+            hb_ev[s_][1].record(stream)
+        torch.cuda.synchronize()
+        hb_ms = max_over_ranks(statistics.mean(e0.elapsed_time(e1) for e0, e1 in hb_ev))
+        flops = 2.0 * hb_num * hb_dim
+        bytes_ = 8.0 * hb_num * (hb_dim + 1)
+        hyperbox = {
+            "workload": f"hyperbox{hb_dim}_dirs{hb_num}", "value": hb_num * ws / (hb_ms * 1e-3), "unit": "LPs/s",
+            "ms_per_step": hb_ms,
+            "roofline": {"bound": "alu", "kernel": "hyperbox_tile_kernel",
+                         "achieved": flops / (hb_ms * 1e-3) / 1e9, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                         "frac": flops / (hb_ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS, "traffic": None,
+                         "hbm_gbs": bytes_ / (hb_ms * 1e-3) / 1e9, "hbm_peak_gbs": HBM_PEAK_GBS,
+                         "hbm_frac": bytes_ / (hb_ms * 1e-3) / 1e9 / HBM_PEAK_GBS,
+                         "work": "one FP64 FMA per direction coordinate (the FP64 pipe binds before HBM: "
+                                 "1 FMA per 8 bytes read)"},
+            "timing": "CUDA events around each call on the launching stream, mean of the timed steps; "
+                      "inputs (0.94 GB) larger than L2",
+        }
+        del dL, dlo, dhi, dobj
+
     # ---- end to end through the C ABI with host buffers ----------------
     e2e = None
     if not args.no_e2e:
@@ -368,6 +411,7 @@ def run_ours(args):
                        "mean_pivots": float(res["iters"].mean())},
             "roofline": roofline,
             "fp64_plain": fp64,
+            "hyperbox": hyperbox,
             "clocks": clocks,
             "gpu_launches": args.steps * launches,
             "e2e": e2e,

@@ -232,6 +232,44 @@ lpb_err lp_solve_uniform_noalloc(int32_t num_lps, int32_t m, int32_t n,
                                  int32_t *status, int32_t *iters, double *obj, double *x, double *y,
                                  const lp_batch_opts *opts, void *stream);
 
+/* Largest dimension lp_hyperbox_solve accepts. */
+#define LPB_MAX_HYPERBOX_DIM (1 << 20)
+
+/*
+ * Hyperbox LPs (Section 4.4, Eq. 7): for each direction l_k, k < num_lps,
+ *
+ *     obj[k] = max  l_k . x   over the box  lo <= x <= hi
+ *            = sum_i l_ki h_ki,   h_ki = lo_i where l_ki < 0, hi_i otherwise,
+ *
+ * and x[k] = h_k, a maximiser (the hi bound where l_ki is 0 or -0).
+ *
+ *  num_lps, dim   number of directions (>= 0) and their dimension
+ *                 (1 <= dim <= LPB_MAX_HYPERBOX_DIM).
+ *  lo, hi         the box: dim values each when box_per_lp == 0 (one box for
+ *                 every direction), num_lps*dim values laid out like L when
+ *                 box_per_lp != 0.  lo_i <= hi_i is the caller's to ensure.
+ *  L              num_lps*dim directions, row-major (direction k at k*dim).
+ *  obj            [num_lps] output; x [num_lps*dim] output or NULL.
+ *  ptr_kind       LPB_DEVICE: every array is memory of the current device and
+ *                 the call is asynchronous on `stream` (returns once the work
+ *                 is enqueued); LPB_HOST: host arrays, copied through device
+ *                 buffers; the call returns when the results are in obj / x.
+ *  stream         cudaStream_t (NULL = legacy default).
+ *
+ * All values must be finite.  The sum is taken in FP64 with a fused
+ * multiply-add per term, in ascending i for dim <= 64 and as 32 lane sums
+ * combined by a fixed tree above: within dim * 2^-53 * sum_i |l_ki h_ki| of the
+ * exact value.  Arrays that are 16-byte aligned are staged with bulk
+ * asynchronous copies; others are read with plain loads (same results).
+ * If the GPU fails to complete a staged copy within about one second (a
+ * hardware or driver fault, not an input condition), the affected outputs are
+ * NaN.  Errors: LPB_EINVAL (bad argument, a LPB_DEVICE pointer that is not
+ * device memory), LPB_ETOOBIG, LPB_ENOMEM, LPB_ECUDA.  No counterpart of the
+ * host/device choice in the paper (which solves these LPs inside its tool).
+ */
+lpb_err lp_hyperbox_solve(int32_t num_lps, int32_t dim, const double *lo, const double *hi, int32_t box_per_lp,
+                          const double *L, double *obj, double *x, int32_t ptr_kind, void *stream);
+
 /* Free the batch (waits for its pending work).  NULL is accepted. */
 lpb_err lp_batch_destroy(lp_batch *h);
 

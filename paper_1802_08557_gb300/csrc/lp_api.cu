@@ -601,6 +601,64 @@ lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
     return LPB_OK;
 }
 
+lpb_err lp_hyperbox_solve(int32_t num_lps, int32_t dim, const double* lo, const double* hi, int32_t box_per_lp,
+                          const double* L, double* obj, double* x, int32_t ptr_kind, void* stream) {
+    g_last_error.clear();
+    if (num_lps < 0 || dim < 1) return fail(LPB_EINVAL, "num_lps must be >= 0 and dim >= 1");
+    if (dim > LPB_MAX_HYPERBOX_DIM) return fail(LPB_ETOOBIG, "dim exceeds LPB_MAX_HYPERBOX_DIM");
+    if (!lo || !hi || !L || !obj) return fail(LPB_EINVAL, "lo, hi, L and obj must not be NULL");
+    if (ptr_kind != LPB_HOST && ptr_kind != LPB_DEVICE) return fail(LPB_EINVAL, "ptr_kind must be LPB_HOST or LPB_DEVICE");
+    if (num_lps == 0) return LPB_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n_el = (size_t)num_lps * (size_t)dim;
+    const size_t box_el = box_per_lp ? n_el : (size_t)dim;
+    cudaError_t err;
+    if (ptr_kind == LPB_DEVICE) {
+        // every array must be memory the current device can address
+        int dev = 0;
+        if ((err = cudaGetDevice(&dev))) return cuda_fail(err, "cudaGetDevice");
+        const void* ptrs[] = {lo, hi, L, obj, x};
+        for (const void* p : ptrs) {
+            if (!p) continue;
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, p) != cudaSuccess || at.type == cudaMemoryTypeUnregistered ||
+                at.type == cudaMemoryTypeHost || (at.type == cudaMemoryTypeDevice && at.device != dev)) {
+                cudaGetLastError();
+                return fail(LPB_EINVAL, "LPB_DEVICE pointer is not device memory of the current device");
+            }
+        }
+        if ((err = lpb::launch_hyperbox(L, lo, hi, box_per_lp != 0, obj, x, num_lps, dim, s)))
+            return cuda_fail(err, "hyperbox launch");
+        return LPB_OK;
+    }
+    // host arrays: stage through stream-ordered device buffers
+    double *dL = nullptr, *dlo = nullptr, *dhi = nullptr, *dobj = nullptr, *dx = nullptr;
+    auto cleanup = [&]() {
+        for (double* p : {dL, dlo, dhi, dobj, dx})
+            if (p) cudaFreeAsync(p, s);
+        cudaStreamSynchronize(s);
+    };
+    if ((err = cudaMallocAsync((void**)&dL, n_el * 8, s)) || (err = cudaMallocAsync((void**)&dlo, box_el * 8, s)) ||
+        (err = cudaMallocAsync((void**)&dhi, box_el * 8, s)) ||
+        (err = cudaMallocAsync((void**)&dobj, (size_t)num_lps * 8, s)) ||
+        (x && (err = cudaMallocAsync((void**)&dx, n_el * 8, s)))) {
+        cleanup();
+        return err == cudaErrorMemoryAllocation ? fail(LPB_ENOMEM, "device buffers") : cuda_fail(err, "device buffers");
+    }
+    if ((err = cudaMemcpyAsync(dL, L, n_el * 8, cudaMemcpyHostToDevice, s)) ||
+        (err = cudaMemcpyAsync(dlo, lo, box_el * 8, cudaMemcpyHostToDevice, s)) ||
+        (err = cudaMemcpyAsync(dhi, hi, box_el * 8, cudaMemcpyHostToDevice, s)) ||
+        (err = lpb::launch_hyperbox(dL, dlo, dhi, box_per_lp != 0, dobj, dx, num_lps, dim, s)) ||
+        (err = cudaMemcpyAsync(obj, dobj, (size_t)num_lps * 8, cudaMemcpyDeviceToHost, s)) ||
+        (x && (err = cudaMemcpyAsync(x, dx, n_el * 8, cudaMemcpyDeviceToHost, s)))) {
+        cleanup();
+        return cuda_fail(err, "hyperbox solve");
+    }
+    cleanup();
+    if ((err = cudaGetLastError())) return cuda_fail(err, "hyperbox solve");
+    return LPB_OK;
+}
+
 lpb_err lp_batch_destroy(lp_batch* h) {
     if (!h) return LPB_OK;
     DeviceGuard guard(h->device);

@@ -181,6 +181,12 @@ int fp64_resident_queue_ctas_per_sm(int threads, size_t smem);
 
 // Checks (lp_api.cu helpers in lp_prepare.cu): counts non-finite values of
 // A, b, c into *bad and the rows with b_i < 0 of every LP into k[].
+// Hyperbox LPs (Section 4.4, Eq. 7): obj[k] = max of L[k].x over the box
+// (lo, hi shared when !box_per_lp, else one box per LP laid out like L); x
+// (optional) the maximiser.  Device pointers; asynchronous on `stream`.
+cudaError_t launch_hyperbox(const double* L, const double* lo, const double* hi, bool box_per_lp, double* obj,
+                            double* x, int64_t num_lps, int dim, cudaStream_t stream);
+
 cudaError_t launch_prepare(const DeviceBatch& B, int32_t num_lps, int64_t a_len, int64_t b_len,
                            int64_t c_len, int32_t* k, unsigned long long* bad, cudaStream_t stream);
 

@@ -26,7 +26,7 @@ LPB_MAX_DIM = 16384
 # Every symbol include/lpbatch.h declares.
 EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_results",
             "lp_batch_plan_info", "lp_batch_set_timing", "lp_batch_stage_times", "lp_batch_destroy",
-            "lpb_strerror", "lpb_last_error", "lp_solve_uniform_noalloc")
+            "lpb_strerror", "lpb_last_error", "lp_solve_uniform_noalloc", "lp_hyperbox_solve")
 
 
 class LPBatchOpts(ctypes.Structure):
@@ -100,6 +100,8 @@ def load(path: str | None = None):
         L.lp_batch_results.restype = ctypes.c_int
         L.lp_batch_plan_info.argtypes = [_vp, ctypes.POINTER(LPBatchPlan)]
         L.lp_batch_plan_info.restype = ctypes.c_int
+        L.lp_hyperbox_solve.argtypes = [_i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _i32, _vp]
+        L.lp_hyperbox_solve.restype = ctypes.c_int
         L.lp_batch_set_timing.argtypes = [_vp, _i32]
         L.lp_batch_set_timing.restype = ctypes.c_int
         L.lp_batch_stage_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_i32)]
@@ -206,6 +208,15 @@ def lp_batch_stage_times(h):
     n = _i32(0)
     _check(load().lp_batch_stage_times(h, ms, ctypes.byref(n)), "lp_batch_stage_times")
     return float(ms[0]), float(ms[1]), int(n.value)
+
+
+def lp_hyperbox_solve(L, lo, hi, obj, x=None, box_per_lp: bool = False, ptr_kind: int = LPB_HOST, stream=None):
+    """Eq. 7 for every row of ``L`` (num_lps x dim): obj[k] = max of L[k].x
+    over the box, x[k] the maximiser (see include/lpbatch.h).  Arrays are
+    numpy (LPB_HOST) or CUDA tensors (LPB_DEVICE), C-contiguous float64."""
+    num_lps, dim = (int(L.shape[0]), int(L.shape[1])) if len(L.shape) == 2 else (0, 0)
+    _check(load().lp_hyperbox_solve(num_lps, dim, _addr(lo), _addr(hi), 1 if box_per_lp else 0, _addr(L),
+                                    _addr(obj), _addr(x), ptr_kind, _stream_handle(stream)), "lp_hyperbox_solve")
 
 
 def lp_solve_uniform_noalloc(num_lps, m, n, A, b, c, status, iters, obj, x, y=None,

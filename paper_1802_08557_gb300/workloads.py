@@ -203,6 +203,29 @@ def support_function(num_dirs: int, dim: int = 10, halfspaces: int = 40, wid: in
         A=Afull.reshape(-1).copy(), b=bb.copy(), c=C.reshape(-1), kind=np.zeros(N, np.int8))
 
 
+def hyperbox_directions(num_dirs: int, dim: int = 28, wid: int = 6, start: int = 0):
+    """Support function of one hyperbox (Section 4.4, Eq. 7) sampled in
+    ``num_dirs`` directions uniform on the unit sphere of R^dim (normalised
+    Gaussians), the shape of the paper's state-space exploration LPs (Section
+    6: a 28-variable helicopter model, a 5-dimensional system).  Box: lo~U[-2,0],
+    hi = lo + U[0.5,3].  Returns (L [num_dirs x dim], lo [dim], hi [dim]).
+    Directions are drawn in blocks of 4096 from generators keyed by the index
+    of the block's first direction, so a block is reproducible alone."""
+    seed = workload_seed(wid)
+    g = lp_generator(seed, SHARED_INDEX)
+    lo = g.uniform(-2.0, 0.0, dim)
+    hi = lo + g.uniform(0.5, 3.0, dim)
+    L = np.empty((num_dirs, dim))
+    blk = 4096
+    for b0 in range(0, num_dirs, blk):
+        gb = lp_generator(seed, start + b0)
+        n = min(blk, num_dirs - b0)
+        v = gb.standard_normal((n, dim))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        L[b0:b0 + n] = v
+    return L, lo, hi
+
+
 # ---------------------------------------------------------------------------
 # Uneven batch (sizes log-uniform)
 # ---------------------------------------------------------------------------

@@ -89,3 +89,15 @@ def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(lpb, "_lib", None)
     with pytest.raises(ImportError):
         lpb.load(str(tmp_path / "missing.so"))
+
+
+def test_hyperbox_argument_errors_before_device_work(lib):
+    L, lo, hi, obj = np.ones(8), np.zeros(4), np.ones(4), np.zeros(2)
+    args = lambda num, dim, Lp=L.ctypes.data, kind=lpb.LPB_HOST: (num, dim, lo.ctypes.data, hi.ctypes.data, 0, Lp,
+                                                                    obj.ctypes.data, None, kind, None)
+    assert lib.lp_hyperbox_solve(*args(2, 0)) == lpb.LPB_EINVAL
+    assert lib.lp_hyperbox_solve(*args(-1, 4)) == lpb.LPB_EINVAL
+    assert lib.lp_hyperbox_solve(*args(2, (1 << 20) + 1)) == lpb.LPB_ETOOBIG
+    assert lib.lp_hyperbox_solve(*args(2, 4, Lp=None)) == lpb.LPB_EINVAL
+    assert lib.lp_hyperbox_solve(*args(2, 4, kind=9)) == lpb.LPB_EINVAL
+    assert lib.lp_hyperbox_solve(*args(0, 4)) == lpb.LPB_OK  # empty batch: nothing to do
