@@ -270,6 +270,57 @@ lpb_err lp_solve_uniform_noalloc(int32_t num_lps, int32_t m, int32_t n,
 lpb_err lp_hyperbox_solve(int32_t num_lps, int32_t dim, const double *lo, const double *hi, int32_t box_per_lp,
                           const double *L, double *obj, double *x, int32_t ptr_kind, void *stream);
 
+/*
+ * Warm-start network.  No counterpart in the paper (whose solver always
+ * starts from the slack basis): a perceptron n_in -> n_h1 -> n_h2 -> n_out with
+ * ReLU hidden layers that maps an LP's data to one logit per constraint ("is
+ * this constraint active at the optimum"), trained on LPs this library has
+ * solved (lp_batch_solve_warm uses it).
+ *
+ * Precision: every matrix product has BF16 operands (round to nearest even)
+ * and FP32 accumulation on the tensor cores; biases, pre-activations, the loss
+ * and all gradients are FP32; master weights and Adam moments FP32.  Inputs are
+ * scaled as (x - mean) * inv_std before the first product.  The loss is the
+ * mean over the batch and the outputs of the weighted binary cross entropy
+ * (weight pos_weight on targets 1, 1 on targets 0).
+ *
+ * Parameters travel as one FP32 array: W1 (n_h1 x n_in, row-major), b1, W2
+ * (n_h2 x n_h1), b2, W3 (n_out x n_h2), b3.  Device arrays must belong to the
+ * device that was current at lp_mlp_create; a host pointer is refused
+ * (LPB_EINVAL) before any launch.
+ */
+#define LPB_MAX_MLP_WIDTH 8192
+#define LPB_MAX_MLP_BATCH (1 << 20)
+
+typedef struct lp_mlp lp_mlp;   /* opaque; owned by the library */
+
+/* Create a network with He-uniform weights (rounded to BF16 values; splitmix64
+ * stream from `seed`), zero biases, identity input scaling; max_batch = the
+ * largest batch of lp_mlp_train_step / lp_mlp_gradients (lp_mlp_forward takes
+ * any batch, in chunks of max_batch).  Allocates on the current device. */
+lpb_err lp_mlp_create(lp_mlp **out, int32_t n_in, int32_t n_h1, int32_t n_h2, int32_t n_out, int32_t max_batch,
+                      uint64_t seed);
+lpb_err lp_mlp_num_params(const lp_mlp *net, int64_t *count);
+/* Host copies of the parameters (layout above).  Setting them restarts Adam. */
+lpb_err lp_mlp_set_params(lp_mlp *net, const float *params);
+lpb_err lp_mlp_get_params(lp_mlp *net, float *params);
+/* Input scaling (host arrays of n_in values). */
+lpb_err lp_mlp_set_scaling(lp_mlp *net, const float *mean, const float *inv_std);
+/* logits [batch x n_out] (device, FP32) of x [batch x n_in] (device, FP32,
+ * unscaled); asynchronous on stream. */
+lpb_err lp_mlp_forward(lp_mlp *net, const float *x, int64_t batch, float *logits, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * batch (x [batch x n_in], targets y [batch x n_out] in {0,1}, device FP32).
+ * loss (host, may be NULL) receives the batch loss before the step; asking
+ * for it waits for the step. */
+lpb_err lp_mlp_train_step(lp_mlp *net, const float *x, const float *y, int32_t batch, float lr, float pos_weight,
+                          double *loss, void *stream);
+/* Forward + backward without an update: the gradient of the loss (host,
+ * parameter layout) and the loss; waits for the GPU. */
+lpb_err lp_mlp_gradients(lp_mlp *net, const float *x, const float *y, int32_t batch, float pos_weight,
+                         float *grads, double *loss, void *stream);
+lpb_err lp_mlp_destroy(lp_mlp *net);
+
 /* Free the batch (waits for its pending work).  NULL is accepted. */
 lpb_err lp_batch_destroy(lp_batch *h);
 

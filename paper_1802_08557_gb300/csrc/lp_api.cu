@@ -20,18 +20,30 @@
 #include "lp_internal.h"
 #include "lpbatch.h"
 
-namespace {
+namespace lpb {
 
 thread_local std::string g_last_error;
 
-lpb_err fail(lpb_err e, const std::string& msg) {
+lpb_err api_fail(lpb_err e, const std::string& msg) {
     g_last_error = msg;
     return e;
 }
 
-lpb_err cuda_fail(cudaError_t err, const char* what) {
-    return fail(LPB_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
+lpb_err api_cuda_fail(cudaError_t err, const char* what) {
+    return api_fail(LPB_ECUDA, std::string(what) + ": " + cudaGetErrorString(err));
 }
+
+void api_clear_error() { g_last_error.clear(); }
+
+}  // namespace lpb
+
+namespace {
+
+using lpb::g_last_error;
+
+lpb_err fail(lpb_err e, const std::string& msg) { return lpb::api_fail(e, msg); }
+
+lpb_err cuda_fail(cudaError_t err, const char* what) { return lpb::api_cuda_fail(err, what); }
 
 // One stream-ordered memory pool per device that keeps freed memory cached,
 // so that create/destroy cycles do not return memory to the driver.

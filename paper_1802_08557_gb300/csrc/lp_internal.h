@@ -7,6 +7,10 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
+#include "lpbatch.h"
+
 namespace lpb {
 
 // Device-side view of a batch: per-LP sizes and element offsets, the data,
@@ -181,6 +185,12 @@ int fp64_resident_queue_ctas_per_sm(int threads, size_t smem);
 
 // Checks (lp_api.cu helpers in lp_prepare.cu): counts non-finite values of
 // A, b, c into *bad and the rows with b_i < 0 of every LP into k[].
+// Error reporting of the C ABI: records the text returned by lpb_last_error
+// (per host thread) and returns the code.
+lpb_err api_fail(lpb_err e, const std::string& msg);
+lpb_err api_cuda_fail(cudaError_t err, const char* what);
+void api_clear_error();
+
 // Hyperbox LPs (Section 4.4, Eq. 7): obj[k] = max of L[k].x over the box
 // (lo, hi shared when !box_per_lp, else one box per LP laid out like L); x
 // (optional) the maximiser.  Device pointers; asynchronous on `stream`.

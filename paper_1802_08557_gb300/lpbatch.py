@@ -26,7 +26,9 @@ LPB_MAX_DIM = 16384
 # Every symbol include/lpbatch.h declares.
 EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_results",
             "lp_batch_plan_info", "lp_batch_set_timing", "lp_batch_stage_times", "lp_batch_destroy",
-            "lpb_strerror", "lpb_last_error", "lp_solve_uniform_noalloc", "lp_hyperbox_solve")
+            "lpb_strerror", "lpb_last_error", "lp_solve_uniform_noalloc", "lp_hyperbox_solve",
+            "lp_mlp_create", "lp_mlp_num_params", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_set_scaling",
+            "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients", "lp_mlp_destroy")
 
 
 class LPBatchOpts(ctypes.Structure):
@@ -100,6 +102,21 @@ def load(path: str | None = None):
         L.lp_batch_results.restype = ctypes.c_int
         L.lp_batch_plan_info.argtypes = [_vp, ctypes.POINTER(LPBatchPlan)]
         L.lp_batch_plan_info.restype = ctypes.c_int
+        L.lp_mlp_create.argtypes = [ctypes.POINTER(_vp), _i32, _i32, _i32, _i32, _i32, ctypes.c_uint64]
+        L.lp_mlp_num_params.argtypes = [_vp, ctypes.POINTER(_i64)]
+        L.lp_mlp_set_params.argtypes = [_vp, _vp]
+        L.lp_mlp_get_params.argtypes = [_vp, _vp]
+        L.lp_mlp_set_scaling.argtypes = [_vp, _vp, _vp]
+        L.lp_mlp_forward.argtypes = [_vp, _vp, _i64, _vp, _vp]
+        L.lp_mlp_train_step.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float,
+                                        ctypes.POINTER(ctypes.c_double), _vp]
+        L.lp_mlp_gradients.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, _vp, ctypes.POINTER(ctypes.c_double),
+                                       _vp]
+        L.lp_mlp_destroy.argtypes = [_vp]
+        for f in ("lp_mlp_create", "lp_mlp_num_params", "lp_mlp_set_params", "lp_mlp_get_params",
+                  "lp_mlp_set_scaling", "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients",
+                  "lp_mlp_destroy"):
+            getattr(L, f).restype = ctypes.c_int
         L.lp_hyperbox_solve.argtypes = [_i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _i32, _vp]
         L.lp_hyperbox_solve.restype = ctypes.c_int
         L.lp_batch_set_timing.argtypes = [_vp, _i32]
@@ -217,6 +234,63 @@ def lp_hyperbox_solve(L, lo, hi, obj, x=None, box_per_lp: bool = False, ptr_kind
     num_lps, dim = (int(L.shape[0]), int(L.shape[1])) if len(L.shape) == 2 else (0, 0)
     _check(load().lp_hyperbox_solve(num_lps, dim, _addr(lo), _addr(hi), 1 if box_per_lp else 0, _addr(L),
                                     _addr(obj), _addr(x), ptr_kind, _stream_handle(stream)), "lp_hyperbox_solve")
+
+
+class Mlp:
+    """Owner of one warm-start network handle (see include/lpbatch.h)."""
+
+    def __init__(self, n_in: int, n_h1: int, n_h2: int, n_out: int, max_batch: int, seed: int = 0):
+        self.sizes = (n_in, n_h1, n_h2, n_out)
+        self.h = _vp()
+        _check(load().lp_mlp_create(ctypes.byref(self.h), n_in, n_h1, n_h2, n_out, max_batch, seed),
+               "lp_mlp_create")
+        n = _i64(0)
+        _check(load().lp_mlp_num_params(self.h, ctypes.byref(n)), "lp_mlp_num_params")
+        self.num_params = int(n.value)
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.num_params, np.float32)
+        _check(load().lp_mlp_get_params(self.h, p.ctypes.data), "lp_mlp_get_params")
+        return p
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == self.num_params
+        _check(load().lp_mlp_set_params(self.h, p.ctypes.data), "lp_mlp_set_params")
+
+    def set_scaling(self, mean: np.ndarray, inv_std: np.ndarray):
+        mean = np.ascontiguousarray(mean, np.float32)
+        inv_std = np.ascontiguousarray(inv_std, np.float32)
+        _check(load().lp_mlp_set_scaling(self.h, mean.ctypes.data, inv_std.ctypes.data), "lp_mlp_set_scaling")
+
+    def forward(self, x, logits, stream=None):
+        _check(load().lp_mlp_forward(self.h, _addr(x), int(x.shape[0]), _addr(logits), _stream_handle(stream)),
+               "lp_mlp_forward")
+
+    def train_step(self, x, y, lr: float, pos_weight: float = 1.0, want_loss: bool = False, stream=None):
+        loss = ctypes.c_double(0.0)
+        _check(load().lp_mlp_train_step(self.h, _addr(x), _addr(y), int(x.shape[0]), lr, pos_weight,
+                                        ctypes.byref(loss) if want_loss else None, _stream_handle(stream)),
+               "lp_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def gradients(self, x, y, pos_weight: float = 1.0, stream=None):
+        g = np.empty(self.num_params, np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(load().lp_mlp_gradients(self.h, _addr(x), _addr(y), int(x.shape[0]), pos_weight, g.ctypes.data,
+                                       ctypes.byref(loss), _stream_handle(stream)), "lp_mlp_gradients")
+        return g, loss.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().lp_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lp_solve_uniform_noalloc(num_lps, m, n, A, b, c, status, iters, obj, x, y=None,

@@ -101,3 +101,13 @@ def test_hyperbox_argument_errors_before_device_work(lib):
     assert lib.lp_hyperbox_solve(*args(2, 4, Lp=None)) == lpb.LPB_EINVAL
     assert lib.lp_hyperbox_solve(*args(2, 4, kind=9)) == lpb.LPB_EINVAL
     assert lib.lp_hyperbox_solve(*args(0, 4)) == lpb.LPB_OK  # empty batch: nothing to do
+
+
+def test_mlp_argument_errors_before_device_work(lib):
+    h = ctypes.c_void_p()
+    assert lib.lp_mlp_create(None, 4, 4, 4, 4, 8, 0) == lpb.LPB_EINVAL
+    assert lib.lp_mlp_create(ctypes.byref(h), 0, 4, 4, 4, 8, 0) == lpb.LPB_EINVAL
+    assert lib.lp_mlp_create(ctypes.byref(h), 4, 4, 4, 4, 0, 0) == lpb.LPB_EINVAL
+    assert lib.lp_mlp_create(ctypes.byref(h), 1 << 14, 4, 4, 4, 8, 0) == lpb.LPB_ETOOBIG
+    assert not h.value
+    assert lib.lp_mlp_destroy(None) == lpb.LPB_OK
