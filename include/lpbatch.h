@@ -170,6 +170,9 @@ typedef struct {
     int32_t internal_error_code; /* code of the first such failure (0 if none)       */
     int32_t internal_error_lp;   /* its LP index (-1 if none)                        */
     int32_t internal_error_detail[5]; /* kernel state at that failure (diagnostics)   */
+    int32_t num_warm_certified;/* last lp_batch_solve_warm: LPs certified from the
+                                  network's proposal (the rest: num_fallback)     */
+    int32_t num_warm_rounds;   /* last lp_batch_solve_warm: restricted LPs solved    */
     int64_t max_smem_bytes;    /* largest shared-memory footprint of a launch        */
     int64_t workspace_bytes;   /* global workspace of the streamed LPs               */
 } lp_batch_plan;
@@ -320,6 +323,31 @@ lpb_err lp_mlp_train_step(lp_mlp *net, const float *x, const float *y, int32_t b
 lpb_err lp_mlp_gradients(lp_mlp *net, const float *x, const float *y, int32_t batch, float pos_weight,
                          float *grads, double *loss, void *stream);
 lpb_err lp_mlp_destroy(lp_mlp *net);
+
+/*
+ * Solve the batch from the warm-start network's proposal.  For every LP the
+ * network scores the constraints from (b, c); the LP restricted to the rows
+ * scored above `threshold` (a probability in (0, 1); at most 32 rows) is
+ * solved by the simplex method and its optimum checked on the full LP in FP64
+ * from the original data (every row feasible to 1e-9*max(1,|b|_inf), duals >=
+ * 0 and every reduced cost >= 0 to 1e-9*max(1,|c|_inf), c^T x = b_R^T y to
+ * 1e-9 relative).  Violated rows are added and the restricted LP solved again
+ * (up to 8 rounds).  A certified LP is reported LP_OPTIMAL with that x, the
+ * duals y (0 off the restricted rows), obj = c^T x and iters = the restricted
+ * pivots; every other LP is solved cold by the FP64 path (same results as
+ * lp_batch_solve with LP_PREC_FP64).  Requirements: all LPs of one size m x n,
+ * a network with m + n inputs (b then c) and m outputs on the batch's device,
+ * and every LP's FP64 tableau within one CTA's shared memory (LPB_ETOOBIG
+ * otherwise).  Asynchronous like lp_batch_solve; lp_batch_plan_info reports
+ * num_warm_certified, num_warm_rounds and num_fallback. */
+lpb_err lp_batch_solve_warm(lp_batch *h, lp_mlp *net, float threshold, void *stream);
+
+/* Training data from a batch of equal-size LPs (device arrays):
+ * features x [num_lps x (m+n)] = (b, c) as FP32 (the network's input), and,
+ * after a solve, labels [num_lps x m] = 1.0 where the LP is optimal and its
+ * dual y_i > 0 (constraint i active), else 0.0.  Asynchronous on stream. */
+lpb_err lp_batch_features(lp_batch *h, float *x, void *stream);
+lpb_err lp_batch_active_labels(lp_batch *h, float *labels, void *stream);
 
 /* Free the batch (waits for its pending work).  NULL is accepted. */
 lpb_err lp_batch_destroy(lp_batch *h);

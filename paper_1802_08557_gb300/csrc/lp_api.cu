@@ -173,6 +173,17 @@ struct lp_batch {
     // done) for the last kTimingRing solves
     std::vector<cudaEvent_t> tev;
     int64_t timed_solves = 0;
+    // learned warm start (lp_batch_solve_warm): every LP's size when all are
+    // equal (else -1), what the cold FP64 re-solve of any LP needs, and the
+    // buffers, allocated by the first warm solve
+    int32_t uniform_m = -1, uniform_n = -1;
+    size_t cold_smem = 0;
+    int cold_threads = 0;
+    float* warm_x = nullptr;       // features [num_lps x (m+n)]
+    float* warm_logits = nullptr;  // [num_lps x m]
+    int32_t* warm_q = nullptr;     // LPs for the cold FP64 solve
+    int32_t* warm_stats = nullptr; // [0] queue length, [1] certified, [2] rounds, [3] queue counter
+    bool last_warm = false;
 };
 
 namespace {
@@ -352,9 +363,14 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     std::map<std::pair<int, size_t>, std::vector<int32_t>> buckets, mixed_buckets;
     std::vector<int32_t> streamed;
     const size_t queue_smem_cap = lpb::kMaxSmemPerBlock - 1024;
+    h->uniform_m = hm[0];
+    h->uniform_n = hn[0];
     for (int32_t k = 0; k < num_lps; ++k) {
         const size_t need = lpb::resident_smem_bytes(hm[k], hn[k], hk[k]);
         h->num_phase1 += hk[k] > 0;
+        if (hm[k] != h->uniform_m || hn[k] != h->uniform_n) h->uniform_m = h->uniform_n = -1;
+        h->cold_smem = std::max(h->cold_smem, need);
+        h->cold_threads = std::max(h->cold_threads, pick_threads(hm[k], hn[k], hk[k], 0));
         if (o.precision == LP_PREC_FP32_REFINE && o.schedule == LPB_SCHED_AUTO && need <= queue_smem_cap) {
             // FP32 tableau + FP64 certificate; the FP64 fallback runs resident.
             const int threads = mixed_threads(hm[k], hn[k], hk[k], o.block_threads);
@@ -363,7 +379,7 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
             const size_t msmem = (mbytes + 1023) / 1024 * 1024;
             mixed_buckets[{threads, msmem}].push_back(k);
             h->fb_smem = std::max(h->fb_smem, need);
-            h->fb_threads = std::max(h->fb_threads, threads);
+            h->fb_threads = std::max(h->fb_threads, pick_threads(hm[k], hn[k], hk[k], 0));  // FP64 kernel's own choice
             continue;
         }
         if (need > lpb::kMaxSmemPerBlock || o.schedule == LPB_SCHED_STREAMED) {
@@ -505,7 +521,88 @@ lpb_err lp_batch_solve(lp_batch* h, void* stream) {
     }
     h->last_stream = s;
     h->solved = true;
+    h->last_warm = false;
     return LPB_OK;
+}
+
+lpb_err lp_batch_solve_warm(lp_batch* h, lp_mlp* net, float threshold, void* stream) {
+    g_last_error.clear();
+    if (!h || !net) return fail(LPB_EINVAL, "handle or network is NULL");
+    if (!(threshold > 0.0f && threshold < 1.0f)) return fail(LPB_EINVAL, "threshold must be in (0, 1)");
+    if (h->uniform_m < 0) return fail(LPB_EINVAL, "a warm solve needs LPs of one size");
+    const int m = h->uniform_m, n = h->uniform_n;
+    int n_in = 0, n_out = 0, net_dev = -1;
+    lpb::mlp_shape(net, &n_in, &n_out, &net_dev);
+    if (n_in != m + n || n_out != m) return fail(LPB_EINVAL, "network widths must be m + n inputs and m outputs");
+    if (net_dev != h->device) return fail(LPB_EINVAL, "network and batch are on different devices");
+    if (h->cold_smem > lpb::kMaxSmemPerBlock - 1024)
+        return fail(LPB_ETOOBIG, "a warm solve needs every LP's FP64 tableau to fit in shared memory");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t err;
+    const int32_t N = h->num_lps;
+    if (!h->warm_x) {
+        if ((err = alloc(h, &h->warm_x, (size_t)N * (m + n), s)) || (err = alloc(h, &h->warm_logits, (size_t)N * m, s)) ||
+            (err = alloc(h, &h->warm_q, (size_t)N, s)) || (err = alloc(h, &h->warm_stats, 4, s)) ||
+            (err = lpb::fp64_kernels_prepare())) {
+            h->warm_x = nullptr;
+            return cuda_fail(err, "warm-start buffers");
+        }
+    }
+    const int kmax = std::min(m, 32);
+    const float logit_thr = (float)std::log((double)threshold / (1.0 - (double)threshold));
+    int sms = 0;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device))) return cuda_fail(err, "device query");
+    const size_t cold_smem = (h->cold_smem + 1023) / 1024 * 1024;
+    const int ctas = sms * lpb::fp64_resident_queue_ctas_per_sm(h->cold_threads, cold_smem);
+    if ((err = cudaMemsetAsync(h->diag, 0, 8 * sizeof(int32_t), s)) ||
+        (err = cudaMemsetAsync(h->warm_stats, 0, 4 * sizeof(int32_t), s)) ||
+        (err = lpb::launch_warm_features(h->d, N, m, n, h->warm_x, s)))
+        return cuda_fail(err, "warm-start features");
+    lpb_err r = lp_mlp_forward(net, h->warm_x, N, h->warm_logits, stream);
+    if (r != LPB_OK) return r;
+    if ((err = lpb::launch_warm(h->d, h->warm_logits, N, m, n, kmax, /*max_rounds=*/8, /*max_iters=*/50 * (kmax + n),
+                                logit_thr, h->tol.eps_opt, h->tol.eps_piv, /*cert_tol=*/1e-9, h->warm_q,
+                                h->warm_stats, N, h->warm_stats + 1, h->warm_stats + 2, h->diag, s)) ||
+        (err = lpb::launch_fp64_resident_queue(h->d, h->tol, h->warm_q, h->warm_stats, N, N, h->warm_stats + 3,
+                                               h->diag, ctas, h->cold_threads, cold_smem, s)))
+        return cuda_fail(err, "warm solve");
+    h->last_stream = s;
+    h->solved = true;
+    h->last_warm = true;
+    return LPB_OK;
+}
+
+lpb_err lp_batch_features(lp_batch* h, float* x, void* stream) {
+    g_last_error.clear();
+    if (!h || !x) return fail(LPB_EINVAL, "handle or x is NULL");
+    if (h->uniform_m < 0) return fail(LPB_EINVAL, "features need LPs of one size");
+    DeviceGuard guard(h->device);
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, x) != cudaSuccess ||
+        !(at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == h->device))) {
+        cudaGetLastError();
+        return fail(LPB_EINVAL, "x must be device memory of the batch's device");
+    }
+    cudaError_t err = lpb::launch_warm_features(h->d, h->num_lps, h->uniform_m, h->uniform_n, x,
+                                                static_cast<cudaStream_t>(stream));
+    return err ? cuda_fail(err, "features") : LPB_OK;
+}
+
+lpb_err lp_batch_active_labels(lp_batch* h, float* labels, void* stream) {
+    g_last_error.clear();
+    if (!h || !labels) return fail(LPB_EINVAL, "handle or labels is NULL");
+    if (h->uniform_m < 0) return fail(LPB_EINVAL, "labels need LPs of one size");
+    if (!h->solved) return fail(LPB_ENOTSOLVED, "lp_batch_solve has not been called");
+    DeviceGuard guard(h->device);
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, labels) != cudaSuccess ||
+        !(at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == h->device))) {
+        cudaGetLastError();
+        return fail(LPB_EINVAL, "labels must be device memory of the batch's device");
+    }
+    cudaError_t err = lpb::launch_warm_labels(h->d, h->num_lps, h->uniform_m, labels, static_cast<cudaStream_t>(stream));
+    return err ? cuda_fail(err, "labels") : LPB_OK;
 }
 
 lpb_err lp_batch_results(lp_batch* h, int32_t* status, int32_t* iters, double* obj, double* x, double* y,
@@ -588,19 +685,26 @@ lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
     plan->num_resident = h->num_lps - h->num_streamed;
     plan->num_mixed = h->num_mixed;
     plan->num_fallback = 0;
+    plan->num_warm_certified = 0;
+    plan->num_warm_rounds = 0;
     plan->internal_errors = 0;
     plan->internal_error_code = 0;
     plan->internal_error_lp = -1;
     for (int i = 0; i < 5; ++i) plan->internal_error_detail[i] = 0;
     if (h->solved) {
         DeviceGuard guard(h->device);
-        int32_t fb = 0, dg[8] = {0, 0, -1, 0, 0, 0, 0, 0};
+        int32_t fb = 0, dg[8] = {0, 0, -1, 0, 0, 0, 0, 0}, ws[4] = {0, 0, 0, 0};
         cudaError_t err = cudaSuccess;
-        if (h->num_mixed > 0) err = cudaMemcpyAsync(&fb, h->fb_len, sizeof fb, cudaMemcpyDeviceToHost, h->last_stream);
+        if (h->last_warm)
+            err = cudaMemcpyAsync(ws, h->warm_stats, sizeof ws, cudaMemcpyDeviceToHost, h->last_stream);
+        else if (h->num_mixed > 0)
+            err = cudaMemcpyAsync(&fb, h->fb_len, sizeof fb, cudaMemcpyDeviceToHost, h->last_stream);
         if (err == cudaSuccess) err = cudaMemcpyAsync(dg, h->diag, sizeof dg, cudaMemcpyDeviceToHost, h->last_stream);
         if (err == cudaSuccess) err = cudaStreamSynchronize(h->last_stream);
         if (err != cudaSuccess) return cuda_fail(err, "plan counters");
-        plan->num_fallback = fb;
+        plan->num_fallback = h->last_warm ? ws[0] : fb;
+        plan->num_warm_certified = h->last_warm ? ws[1] : 0;
+        plan->num_warm_rounds = h->last_warm ? ws[2] : 0;
         plan->internal_errors = dg[0];
         plan->internal_error_code = dg[0] ? dg[1] : 0;
         plan->internal_error_lp = dg[0] ? dg[2] : -1;

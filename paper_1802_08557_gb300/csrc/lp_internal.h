@@ -185,6 +185,20 @@ int fp64_resident_queue_ctas_per_sm(int threads, size_t smem);
 
 // Checks (lp_api.cu helpers in lp_prepare.cu): counts non-finite values of
 // A, b, c into *bad and the rows with b_i < 0 of every LP into k[].
+// Learned warm start (lp_warm.cu): features [num_lps x (m+n)] = (b, c) as
+// FP32; the restricted-LP solve and FP64 check of each LP from the network's
+// logits (uncertified LPs appended to fb_queue); labels [num_lps x m] = 1 where
+// an optimal LP's dual y_i > 0.
+cudaError_t launch_warm_features(const DeviceBatch& B, int32_t num_lps, int32_t m, int32_t n, float* x,
+                                 cudaStream_t s);
+cudaError_t launch_warm(const DeviceBatch& B, const float* logits, int32_t num_lps, int32_t m, int32_t n,
+                        int32_t kmax, int32_t max_rounds, int32_t max_iters, float threshold, double eps_opt,
+                        double eps_piv, double cert_tol, int32_t* fb_queue, int32_t* fb_len, int32_t fb_cap,
+                        int32_t* certified, int32_t* rounds, int32_t* diag, cudaStream_t s);
+cudaError_t launch_warm_labels(const DeviceBatch& B, int32_t num_lps, int32_t m, float* labels, cudaStream_t s);
+// Input and output widths and the device of a warm-start network.
+void mlp_shape(const lp_mlp* net, int* n_in, int* n_out, int* device);
+
 // Error reporting of the C ABI: records the text returned by lpb_last_error
 // (per host thread) and returns the code.
 lpb_err api_fail(lpb_err e, const std::string& msg);

@@ -549,6 +549,16 @@ lpb_err copy_params(lp_mlp* net, float* host, bool to_host) {
 
 }  // namespace
 
+namespace lpb {
+
+void mlp_shape(const lp_mlp* net, int* n_in, int* n_out, int* device) {
+    *n_in = net->m.n_in;
+    *n_out = net->m.n_out;
+    *device = net->device;
+}
+
+}  // namespace lpb
+
 extern "C" {
 
 lpb_err lp_mlp_create(lp_mlp** out, int32_t n_in, int32_t n_h1, int32_t n_h2, int32_t n_out, int32_t max_batch,

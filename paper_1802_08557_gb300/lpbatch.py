@@ -28,7 +28,8 @@ EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_r
             "lp_batch_plan_info", "lp_batch_set_timing", "lp_batch_stage_times", "lp_batch_destroy",
             "lpb_strerror", "lpb_last_error", "lp_solve_uniform_noalloc", "lp_hyperbox_solve",
             "lp_mlp_create", "lp_mlp_num_params", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_set_scaling",
-            "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients", "lp_mlp_destroy")
+            "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients", "lp_mlp_destroy", "lp_batch_solve_warm",
+            "lp_batch_features", "lp_batch_active_labels")
 
 
 class LPBatchOpts(ctypes.Structure):
@@ -56,6 +57,8 @@ class LPBatchPlan(ctypes.Structure):
         ("internal_error_code", ctypes.c_int32),
         ("internal_error_lp", ctypes.c_int32),
         ("internal_error_detail", ctypes.c_int32 * 5),
+        ("num_warm_certified", ctypes.c_int32),
+        ("num_warm_rounds", ctypes.c_int32),
         ("max_smem_bytes", ctypes.c_int64),
         ("workspace_bytes", ctypes.c_int64),
     ]
@@ -113,6 +116,12 @@ def load(path: str | None = None):
         L.lp_mlp_gradients.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, _vp, ctypes.POINTER(ctypes.c_double),
                                        _vp]
         L.lp_mlp_destroy.argtypes = [_vp]
+        L.lp_batch_solve_warm.argtypes = [_vp, _vp, ctypes.c_float, _vp]
+        L.lp_batch_solve_warm.restype = ctypes.c_int
+        L.lp_batch_features.argtypes = [_vp, _vp, _vp]
+        L.lp_batch_features.restype = ctypes.c_int
+        L.lp_batch_active_labels.argtypes = [_vp, _vp, _vp]
+        L.lp_batch_active_labels.restype = ctypes.c_int
         for f in ("lp_mlp_create", "lp_mlp_num_params", "lp_mlp_set_params", "lp_mlp_get_params",
                   "lp_mlp_set_scaling", "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients",
                   "lp_mlp_destroy"):
@@ -302,6 +311,19 @@ def lp_solve_uniform_noalloc(num_lps, m, n, A, b, c, status, iters, obj, x, y=No
                                            _addr(status), _addr(iters), _addr(obj), _addr(x), _addr(y),
                                            ctypes.byref(opts) if opts is not None else None,
                                            _stream_handle(stream))
+
+
+def lp_batch_solve_warm(h, net, threshold: float = 0.2, stream=None):
+    """Warm solve from the network's proposal (see include/lpbatch.h)."""
+    _check(load().lp_batch_solve_warm(h, net.h, threshold, _stream_handle(stream)), "lp_batch_solve_warm")
+
+
+def lp_batch_features(h, x, stream=None):
+    _check(load().lp_batch_features(h, _addr(x), _stream_handle(stream)), "lp_batch_features")
+
+
+def lp_batch_active_labels(h, labels, stream=None):
+    _check(load().lp_batch_active_labels(h, _addr(labels), _stream_handle(stream)), "lp_batch_active_labels")
 
 
 def lp_batch_destroy(h):

@@ -278,6 +278,34 @@ def shared_matrix_family(num_lps: int, m: int = 200, n: int = 100, wid: int = 5,
         A=A.reshape(-1).copy(), b=B.reshape(-1), c=C.reshape(-1), kind=kind)
 
 
+def shared_matrix_family_blocks(num_lps: int, m: int = 200, n: int = 100, wid: int = 5,
+                                start: int = 0) -> LPBatch:
+    """The same family as shared_matrix_family (same A and b0), drawn in blocks
+    of 4096 LPs per generator for large training sets.  The block generators
+    are keyed apart from the per-LP ones, so these LPs are not copies of
+    shared_matrix_family's."""
+    seed = workload_seed(wid)
+    g = lp_generator(seed, SHARED_INDEX)
+    A = g.uniform(0.0, 1.0, size=(m, n))
+    b0 = g.uniform(1.0, 100.0, size=m)
+    B = np.empty((num_lps, m))
+    C = np.empty((num_lps, n))
+    blk = 4096
+    for k0 in range(0, num_lps, blk):
+        gb = lp_generator(seed ^ 0xB10C_0000_0000, start + k0)
+        cnt = min(blk, num_lps - k0)
+        B[k0:k0 + cnt] = b0 * (1.0 + 0.1 * gb.standard_normal((cnt, m)))
+        C[k0:k0 + cnt] = gb.uniform(0.0, 1.0, size=(cnt, n))
+    kind = np.where((B < 0).any(axis=1), KIND_PHASE1, KIND_FEASIBLE_START).astype(np.int8)
+    N = num_lps
+    return LPBatch(
+        name=f"shared_matrix_{m}x{n}_blocks",
+        m=np.full(N, m, np.int32), n=np.full(N, n, np.int32),
+        a_off=np.zeros(N, np.int64), b_off=np.arange(N, dtype=np.int64) * m,
+        c_off=np.arange(N, dtype=np.int64) * n,
+        A=A.reshape(-1).copy(), b=B.reshape(-1), c=C.reshape(-1), kind=kind)
+
+
 # ---------------------------------------------------------------------------
 # Named workloads (sizes of the five benchmark configurations)
 # ---------------------------------------------------------------------------
