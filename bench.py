@@ -37,6 +37,8 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
 # HBM bandwidth of a GB300 measured with a STREAM-style copy (read + write bytes)
 HBM_PEAK_GBS = 6784.5
+# dense BF16 tensor throughput of a GB300 measured with a cuBLAS GEMM (burst)
+BF16_PEAK_TFLOPS = 1958.9
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -52,6 +54,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-hyperbox", action="store_true", help="skip the hyperbox LP (Eq. 7) measurement")
+    p.add_argument("--no-warm", action="store_true", help="skip the learned warm-start measurement")
+    p.add_argument("--warm-train", type=int, default=1_000_000, help="self-solved LPs the network is trained on")
+    p.add_argument("--warm-test", type=int, default=100_000, help="test LPs of the warm-start measurement")
     p.add_argument("--hyperbox-dirs", type=int, default=1 << 22, help="directions of the hyperbox measurement")
     p.add_argument("--precision", default="fp32r", choices=["fp32r", "fp64"],
                    help="headline path: FP32 tableau + FP64 certificate (default) or plain FP64")
@@ -351,6 +356,75 @@ def run_ours(args):
         }
         del dL, dlo, dhi, dobj
 
+    # ---- learned warm start on the shared-A family (200 x 100) ----------------
+    warm = None
+    if not args.no_warm:
+        from paper_1802_08557_gb300 import warmstart as WS
+        t0 = time.perf_counter()
+        train_set = W.shared_matrix_family_blocks(args.warm_train, start=rank * args.warm_train)
+        net, tinfo = WS.train(train_set, epochs=2.0, batch_size=1024, seed=0)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        del train_set
+        test_set = W.shared_matrix_family(args.warm_test, start=rank * args.warm_test)
+        hw = lpb.BatchSolver(test_set, opts=lpb.lpb_default_opts(precision=lpb.LP_PREC_FP64), stream=stream)
+        # cold FP64
+        e_cold, _, _, st_cold = timed(hw.h, args.steps, args.warmup)
+        rc = hw.results()
+        # warm: network + restricted solves + cold FP64 for the rest, every step
+        for _ in range(max(3, args.warmup)):
+            lpb.lp_batch_solve_warm(hw.h, net, 0.2, stream)
+        torch.cuda.synchronize()
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        w0.record(stream)
+        for _ in range(args.steps):
+            lpb.lp_batch_solve_warm(hw.h, net, 0.2, stream)
+        w1.record(stream)
+        torch.cuda.synchronize()
+        e_warm = max_over_ranks(w0.elapsed_time(w1))
+        rw = hw.results()
+        pw = hw.plan_info()
+        # the network alone: forward over the test set's features
+        feats = torch.empty((test_set.num_lps, 300), dtype=torch.float32, device=dev)
+        logits = torch.empty((test_set.num_lps, 200), dtype=torch.float32, device=dev)
+        lpb.lp_batch_features(hw.h, feats, stream)
+        net.forward(feats, logits, stream)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            net.forward(feats, logits, stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms = f0.elapsed_time(f1) / args.steps
+        mlp_flops = 2.0 * test_set.num_lps * (300 * 512 + 512 * 512 + 512 * 200)
+        hw.close()
+        net.close()
+        opt = rc["status"] == 0
+        rel = np.abs(rw["obj"][opt] - rc["obj"][opt]) / np.maximum(1.0, np.abs(rc["obj"][opt]))
+        nt_ = test_set.num_lps
+        warm = {
+            "workload": f"shared200x100_test{nt_}",
+            "value": nt_ * ws * args.steps / (e_warm * 1e-3), "unit": "LPs/s", "ms_per_step": e_warm / args.steps,
+            "cold_fp64": {"value": nt_ * ws * args.steps / (e_cold * 1e-3), "ms_per_step": e_cold / args.steps},
+            "speedup_over_cold_fp64": e_cold / e_warm,
+            "certified_fraction": pw["num_warm_certified"] / nt_,
+            "restricted_solves_per_lp": pw["num_warm_rounds"] / nt_,
+            "status_mismatches_vs_cold": int(np.sum(rw["status"] != rc["status"])),
+            "max_rel_obj_err_vs_cold": float(rel.max()) if rel.size else 0.0,
+            "training": {"lps": tinfo["train_lps"], "steps": tinfo["steps"], "seconds": train_s,
+                         "first_loss": tinfo["first_loss"], "last_loss": tinfo["last_loss"],
+                         "what": "cold FP64 solve of the training LPs + features/labels + Adam steps, all on the GPU"},
+            "network_forward": {"ms": fwd_ms, "achieved_tflops": mlp_flops / (fwd_ms * 1e-3) / 1e12,
+                                "peak_tflops": BF16_PEAK_TFLOPS,
+                                "frac": mlp_flops / (fwd_ms * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
+                                "note": "BF16 mma.sync GEMMs; 300->512->512->200 over the test set"},
+            "timing": "CUDA events on the solve's stream around K whole warm solves "
+                      "(features, network, restricted solves, cold FP64 re-solve)",
+        }
+        del feats, logits
+
     # ---- end to end through the C ABI with host buffers ----------------
     e2e = None
     if not args.no_e2e:
@@ -412,6 +486,7 @@ def run_ours(args):
             "roofline": roofline,
             "fp64_plain": fp64,
             "hyperbox": hyperbox,
+            "warm_start": warm,
             "clocks": clocks,
             "gpu_launches": args.steps * launches,
             "e2e": e2e,

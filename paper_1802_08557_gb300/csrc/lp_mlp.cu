@@ -31,7 +31,8 @@
 
 namespace lpb {
 
-constexpr int kPadK = 32;  // K dimensions are padded to this multiple
+constexpr int kPadK = 32;        // K dimensions are padded to this multiple
+constexpr int kInferRows = 16384;  // rows of activations held for inference chunks
 
 inline int pad_to(int v, int q) { return (v + q - 1) / q * q; }
 
@@ -288,7 +289,7 @@ struct MlpLayer {
 };
 
 struct MlpModel {
-    int n_in, h1, h2, n_out, max_batch, bpad;
+    int n_in, h1, h2, n_out, max_batch, train_batch, bpad;
     MlpLayer L[3];
     float *mean, *inv_std;
     // activations (batch capacity bpad rows)
@@ -575,8 +576,11 @@ lpb_err lp_mlp_create(lp_mlp** out, int32_t n_in, int32_t n_h1, int32_t n_h2, in
     cudaGetDevice(&net->device);
     lpb::MlpModel& m = net->m;
     m.n_in = n_in; m.h1 = n_h1; m.h2 = n_h2; m.n_out = n_out;
-    m.max_batch = max_batch;
-    m.bpad = lpb::pad_to(max_batch, lpb::kPadK);
+    // activations for at least kInferRows rows, so that inference runs in
+    // large chunks (whole-GPU GEMMs) even when training batches are small
+    m.max_batch = std::max<int>(max_batch, lpb::kInferRows);
+    m.train_batch = max_batch;
+    m.bpad = lpb::pad_to(m.max_batch, lpb::kPadK);
     cudaError_t e = lpb::mlp_alloc(&m);
     if (e) {
         lpb::mlp_free(&m);
@@ -663,7 +667,7 @@ lpb_err lp_mlp_train_step(lp_mlp* net, const float* x, const float* y, int32_t b
                           double* loss, void* stream) {
     lpb::api_clear_error();
     if (!net || !x || !y) return api_fail(LPB_EINVAL, "net, x or y is NULL");
-    if (batch < 1 || batch > net->m.max_batch) return api_fail(LPB_EINVAL, "batch must be in [1, max_batch]");
+    if (batch < 1 || batch > net->m.train_batch) return api_fail(LPB_EINVAL, "batch must be in [1, max_batch]");
     if (!(lr > 0.0f) || !(pos_weight > 0.0f)) return api_fail(LPB_EINVAL, "lr and pos_weight must be > 0");
     Dev guard(net->device);
     if (!on_device(x, net->device) || !on_device(y, net->device))
@@ -684,7 +688,7 @@ lpb_err lp_mlp_gradients(lp_mlp* net, const float* x, const float* y, int32_t ba
                          double* loss, void* stream) {
     lpb::api_clear_error();
     if (!net || !x || !y || !grads) return api_fail(LPB_EINVAL, "net, x, y or grads is NULL");
-    if (batch < 1 || batch > net->m.max_batch) return api_fail(LPB_EINVAL, "batch must be in [1, max_batch]");
+    if (batch < 1 || batch > net->m.train_batch) return api_fail(LPB_EINVAL, "batch must be in [1, max_batch]");
     if (!(pos_weight > 0.0f)) return api_fail(LPB_EINVAL, "pos_weight must be > 0");
     Dev guard(net->device);
     if (!on_device(x, net->device) || !on_device(y, net->device))
