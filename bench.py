@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-hyperbox", action="store_true", help="skip the hyperbox LP (Eq. 7) measurement")
     p.add_argument("--no-warm", action="store_true", help="skip the learned warm-start measurement")
+    p.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch measurement")
+    p.add_argument("--uneven-lps", type=int, default=20_000, help="LPs of the uneven-batch measurement")
     p.add_argument("--warm-train", type=int, default=1_000_000, help="self-solved LPs the network is trained on")
     p.add_argument("--warm-test", type=int, default=100_000, help="test LPs of the warm-start measurement")
     p.add_argument("--hyperbox-dirs", type=int, default=1 << 22, help="directions of the hyperbox measurement")
@@ -356,6 +358,50 @@ def run_ours(args):
         }
         del dL, dlo, dhi, dobj
 
+    # ---- uneven batch: m, n log-uniform in [10, 500], 2e4 LPs ----------------
+    uneven = None
+    if not args.no_uneven:
+        ub = W.uneven_dense(args.uneven_lps, start=rank * args.uneven_lps)
+        um, un = ub.m.astype(np.float64), ub.n.astype(np.float64)
+
+        def ev_time(fn):
+            for _ in range(max(3, args.warmup)):
+                fn()
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            a0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            return max_over_ranks(a0.elapsed_time(a1)) / args.steps
+
+        uneven = {"workload": f"uneven10to500_{ub.num_lps}", "unit": "LPs/s"}
+        for label, prec in (("fp64", lpb.LP_PREC_FP64), ("fp32r", lpb.LP_PREC_FP32_REFINE)):
+            hu = lpb.BatchSolver(ub, opts=lpb.lpb_default_opts(precision=prec), stream=stream)
+            ms_default = ev_time(lambda: lpb.lp_batch_solve(hu.h, stream))
+            ru = hu.results()
+            lpb.lp_batch_autotune(hu.h, rounds=1, stream=stream)
+            ms_tuned = ev_time(lambda: lpb.lp_batch_solve(hu.h, stream))
+            ms_graph = ev_time(lambda: lpb.lp_batch_solve_graph(hu.h, stream))
+            rt = hu.results()
+            groups = lpb.lp_batch_groups(hu.h)
+            hu.close()
+            best = min(ms_tuned, ms_graph)
+            fl = 2.0 * float(np.sum(rt["iters"] * (um + 1.0) * (un + 1.0)))
+            uneven[label] = {
+                "value": ub.num_lps * ws / (best * 1e-3), "ms_default_plan": ms_default, "ms_autotuned": ms_tuned,
+                "ms_graph": ms_graph, "groups": len(groups),
+                "persistent_groups": sum(1 for g in groups if g["persistent"] and g["kind"] != 2),
+                "streamed_lps": sum(g["count"] for g in groups if g["kind"] == 2),
+                "results_unchanged_by_tuning": bool(all(np.array_equal(ru[k], rt[k]) for k in ("status", "obj", "x"))),
+                "achieved_gflops": fl / (best * 1e-3) / 1e9, "fp64_peak_gflops": FP64_PEAK_GFLOPS,
+            }
+        uneven["value"] = max(uneven["fp64"]["value"], uneven["fp32r"]["value"])
+        uneven["timing"] = "CUDA events on the solve's stream around K whole solves (default plan, autotuned plan, graph replay)"
+        del ub
+
     # ---- learned warm start on the shared-A family (200 x 100) ----------------
     warm = None
     if not args.no_warm:
@@ -487,6 +533,7 @@ def run_ours(args):
             "fp64_plain": fp64,
             "hyperbox": hyperbox,
             "warm_start": warm,
+            "uneven": uneven,
             "clocks": clocks,
             "gpu_launches": args.steps * launches,
             "e2e": e2e,

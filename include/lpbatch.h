@@ -181,6 +181,41 @@ typedef struct {
  * outcome of the last solve: this waits for that solve). */
 lpb_err lp_batch_plan_info(lp_batch *h, lp_batch_plan *plan);
 
+/* The same solve as lp_batch_solve, captured once into a CUDA graph (on an
+ * internal stream, the first time it is called) and replayed on `stream`
+ * afterwards: one graph launch instead of the memsets, event records and
+ * kernel launches of every solve.  Stage timing does not apply to it.
+ * lp_batch_autotune drops the captured graph (the launch forms change). */
+lpb_err lp_batch_solve_graph(lp_batch *h, void *stream);
+
+/* Launch-form tuner.  For every launch group of the plan (LPs of one kernel,
+ * thread count and shared-memory size), time the group alone on `stream` with
+ * every candidate thread count (FP64: 64, 128, 256, 512; mixed precision: 64,
+ * 128, 256) in both forms -- one CTA per LP, or persistent CTAs over an atomic
+ * work queue with the LPs in descending order of work (groups that need the
+ * whole 227 KB of a CTA's shared memory: one CTA per LP only) -- `rounds` times each,
+ * and keep the fastest.  No counterpart in the paper.  Results of a solve do
+ * not depend on these choices.  The trial launches overwrite the outputs, so
+ * call lp_batch_solve again before lp_batch_results.  Waits for the GPU. */
+lpb_err lp_batch_autotune(lp_batch *h, int32_t rounds, void *stream);
+
+/* One launch group of the plan: index 0 .. lp_batch_plan.num_groups-1 (the
+ * FP64 re-solve queue of the mixed path is not listed). */
+typedef struct {
+    int32_t kind;        /* 0 mixed precision, 1 FP64 shared-memory resident, 2 FP64 streamed */
+    int32_t count;       /* LPs in the group                                  */
+    int32_t threads;     /* threads per CTA                                   */
+    int32_t persistent;  /* 1: persistent CTAs over a work queue              */
+    int64_t smem_bytes;  /* dynamic shared memory per CTA                     */
+    float tuned_ms;      /* group time of the chosen form (-1: not tuned)     */
+    int32_t reserved;
+} lp_batch_group;
+lpb_err lp_batch_group_info(lp_batch *h, int32_t index, lp_batch_group *out);
+/* Set a group's form by hand (threads a multiple of 32, at least 64 for mixed
+ * precision, at most 512; persistent 0 or 1, and 0 for groups that need more
+ * than 226 KB of shared memory).  Streamed groups are fixed. */
+lpb_err lp_batch_set_group_form(lp_batch *h, int32_t index, int32_t threads, int32_t persistent);
+
 /* Device timing of the stages of lp_batch_solve, off by default.  enable != 0
  * creates CUDA events (timing-capable) that every later solve records on the
  * caller's stream; enable == 0 waits for the last solve and frees them.  No

@@ -89,6 +89,10 @@ struct Group {
     int32_t count;
     int32_t threads;
     size_t smem;
+    int32_t gi = 0;          // index into the per-group device counters
+    int32_t persistent = 0;  // 1: persistent CTAs over an atomic work queue
+    int32_t ctas = 0;        // CTAs of the persistent form
+    float tuned_ms = -1.0f;  // time of the chosen form (lp_batch_autotune), -1: not tuned
 };
 
 // Bound of Step 1's tie window in key units: ceil(tau * 2^54 * (1 + 2^-30)) + 4
@@ -184,6 +188,12 @@ struct lp_batch {
     int32_t* warm_q = nullptr;     // LPs for the cold FP64 solve
     int32_t* warm_stats = nullptr; // [0] queue length, [1] certified, [2] rounds, [3] queue counter
     bool last_warm = false;
+    // per launch group: LP count and work counter of the persistent form
+    int32_t* group_len = nullptr;
+    int32_t* group_counter = nullptr;
+    // captured solve (lp_batch_solve_graph)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
 };
 
 namespace {
@@ -214,6 +224,82 @@ void release(lp_batch* h, cudaStream_t s) {
     h->ev_fork = nullptr;
     for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
     h->tev.clear();
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
+}
+
+// One launch group on stream ls: kind 0 mixed precision, 1 FP64 resident;
+// one CTA per LP, or persistent CTAs over the group's work queue.
+cudaError_t launch_group(lp_batch* h, int kind, const Group& g, cudaStream_t ls) {
+    const int32_t* order = h->d_order + g.offset;
+    if (kind == 0) {
+        if (g.persistent)
+            return lpb::launch_mixed_queue(h->d, h->tol, h->mp, order, h->group_len + g.gi, h->group_counter + g.gi,
+                                           g.ctas, g.threads, g.smem, h->fb_queue, h->fb_len, h->num_mixed, h->diag, ls);
+        return lpb::launch_mixed(h->d, h->tol, h->mp, order, g.count, g.threads, g.smem, h->fb_queue, h->fb_len,
+                                 h->num_mixed, h->diag, ls);
+    }
+    if (g.persistent)
+        return lpb::launch_fp64_resident_queue(h->d, h->tol, order, h->group_len + g.gi, g.count, h->num_lps,
+                                               h->group_counter + g.gi, h->diag, g.ctas, g.threads, g.smem, ls);
+    return lpb::launch_fp64_resident(h->d, h->tol, order, g.count, g.threads, g.smem, h->diag, ls);
+}
+
+// Everything a solve enqueues on stream s: counters reset, launch groups forked
+// onto the internal streams (largest first, round robin) and joined back, the
+// FP64 re-solve of uncertified LPs; with `timing`, the stage events.
+lpb_err enqueue_solve(lp_batch* h, cudaStream_t s, bool timing) {
+    cudaError_t err = cudaMemsetAsync(h->diag, 0, 8 * sizeof(int32_t), s);
+    if (err != cudaSuccess) return cuda_fail(err, "diagnostic reset");
+    if (h->num_mixed > 0 && (err = cudaMemsetAsync(h->fb_len, 0, sizeof(int32_t), s)))
+        return cuda_fail(err, "fallback queue reset");
+    struct Job { int kind; const Group* g; int64_t count; };  // kind 0 mixed, 1 resident, 2 streamed
+    std::vector<Job> jobs;
+    for (const Group& g : h->mixed_groups) jobs.push_back({0, &g, g.count});
+    for (const Group& g : h->groups) jobs.push_back({1, &g, g.count});
+    if (h->num_streamed > 0) jobs.push_back({2, nullptr, h->num_streamed});
+    std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& b) { return a.count > b.count; });
+    cudaEvent_t* tev = (!timing || h->tev.empty()) ? nullptr : &h->tev[3 * (size_t)(h->timed_solves % kTimingRing)];
+    if (tev && (err = cudaEventRecord(tev[0], s))) return cuda_fail(err, "timing");
+    if ((err = cudaEventRecord(h->ev_fork, s))) return cuda_fail(err, "fork");
+    bool used[kLanes] = {};
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        const int lane = (int)(i % kLanes);
+        cudaStream_t ls = h->lanes[lane];
+        if (!used[lane]) {
+            if ((err = cudaStreamWaitEvent(ls, h->ev_fork, 0))) return cuda_fail(err, "fork wait");
+            used[lane] = true;
+        }
+        const Job& j = jobs[i];
+        if (j.kind == 2)
+            err = lpb::launch_fp64_streamed(h->d, h->tol, h->d_order + h->streamed_offset, h->num_streamed,
+                                            h->streamed_slots, h->workspace, h->slot_bytes, h->counter, h->diag, ls);
+        else
+            err = launch_group(h, j.kind, *j.g, ls);
+        if (err != cudaSuccess) return cuda_fail(err, "solver launch");
+    }
+    for (int lane = 0; lane < kLanes; ++lane) {
+        if (!used[lane]) continue;
+        if ((err = cudaEventRecord(h->ev_join[lane], h->lanes[lane])) ||
+            (err = cudaStreamWaitEvent(s, h->ev_join[lane], 0)))
+            return cuda_fail(err, "join");
+    }
+    if (tev && (err = cudaEventRecord(tev[1], s))) return cuda_fail(err, "timing");
+    if (h->num_mixed > 0) {
+        err = lpb::launch_fp64_resident_queue(h->d, h->tol, h->fb_queue, h->fb_len, h->num_mixed, h->num_lps,
+                                              h->fb_counter, h->diag, h->fb_ctas, h->fb_threads, h->fb_smem, s);
+        if (err != cudaSuccess) return cuda_fail(err, "fallback launch");
+    }
+    if (tev) {
+        if ((err = cudaEventRecord(tev[2], s))) return cuda_fail(err, "timing");
+        ++h->timed_solves;
+    }
+    h->last_stream = s;
+    h->solved = true;
+    h->last_warm = false;
+    return LPB_OK;
 }
 
 }  // namespace
@@ -392,6 +478,18 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         buckets[{threads, smem}].push_back(k);
         h->max_smem = std::max(h->max_smem, smem);
     }
+    // Longest work first within every list (LPT): the tail of a launch is
+    // made of small LPs.  Work estimate: (m+1)(n+k+1) per pivot, O(m+n) pivots.
+    auto lpt = [&](std::vector<int32_t>& v) {
+        std::stable_sort(v.begin(), v.end(), [&](int32_t a, int32_t b) {
+            const double wa = (double)(hm[a] + 1) * (hn[a] + hk[a] + 1) * (hm[a] + hn[a]);
+            const double wb = (double)(hm[b] + 1) * (hn[b] + hk[b] + 1) * (hm[b] + hn[b]);
+            return wa > wb;
+        });
+    };
+    for (auto& kv : buckets) lpt(kv.second);
+    for (auto& kv : mixed_buckets) lpt(kv.second);
+    lpt(streamed);
     std::vector<int32_t> order;
     order.reserve(num_lps);
     for (auto& kv : buckets) {
@@ -412,6 +510,18 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         order.insert(order.end(), kv.second.begin(), kv.second.end());
         h->mixed_groups.push_back(g);
         h->num_mixed += g.count;
+    }
+    {
+        // per-group device counters of the persistent form
+        std::vector<int32_t> lens;
+        for (Group& g : h->groups) { g.gi = (int32_t)lens.size(); lens.push_back(g.count); }
+        for (Group& g : h->mixed_groups) { g.gi = (int32_t)lens.size(); lens.push_back(g.count); }
+        if (!lens.empty()) {
+            if ((err = alloc(h, &h->group_len, lens.size(), s)) || (err = alloc(h, &h->group_counter, lens.size(), s)) ||
+                (err = cudaMemcpyAsync(h->group_len, lens.data(), lens.size() * 4, cudaMemcpyHostToDevice, s)) ||
+                (err = cudaStreamSynchronize(s)))
+                return bail_cuda(err, "group counters");
+        }
     }
     h->streamed_offset = (int64_t)order.size();
     h->num_streamed = (int32_t)streamed.size();
@@ -464,64 +574,162 @@ lpb_err lp_batch_solve(lp_batch* h, void* stream) {
     g_last_error.clear();
     if (!h) return fail(LPB_EINVAL, "handle is NULL");
     DeviceGuard guard(h->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t err = cudaMemsetAsync(h->diag, 0, 8 * sizeof(int32_t), s);
-    if (err != cudaSuccess) return cuda_fail(err, "diagnostic reset");
-    if (h->num_mixed > 0 && (err = cudaMemsetAsync(h->fb_len, 0, sizeof(int32_t), s)))
-        return cuda_fail(err, "fallback queue reset");
+    return enqueue_solve(h, static_cast<cudaStream_t>(stream), true);
+}
 
-    // Fork: every launch group on an internal stream (largest first, round
-    // robin), all after the work already queued on the caller's stream.
-    struct Job { int kind; const Group* g; int64_t count; };  // kind 0 mixed, 1 resident, 2 streamed
-    std::vector<Job> jobs;
-    for (const Group& g : h->mixed_groups) jobs.push_back({0, &g, g.count});
-    for (const Group& g : h->groups) jobs.push_back({1, &g, g.count});
-    if (h->num_streamed > 0) jobs.push_back({2, nullptr, h->num_streamed});
-    std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& b) { return a.count > b.count; });
-    cudaEvent_t* tev = h->tev.empty() ? nullptr : &h->tev[3 * (size_t)(h->timed_solves % kTimingRing)];
-    if (tev && (err = cudaEventRecord(tev[0], s))) return cuda_fail(err, "timing");
-    if ((err = cudaEventRecord(h->ev_fork, s))) return cuda_fail(err, "fork");
-    bool used[kLanes] = {};
-    for (size_t i = 0; i < jobs.size(); ++i) {
-        const int lane = (int)(i % kLanes);
-        cudaStream_t ls = h->lanes[lane];
-        if (!used[lane]) {
-            if ((err = cudaStreamWaitEvent(ls, h->ev_fork, 0))) return cuda_fail(err, "fork wait");
-            used[lane] = true;
+lpb_err lp_batch_solve_graph(lp_batch* h, void* stream) {
+    g_last_error.clear();
+    if (!h) return fail(LPB_EINVAL, "handle is NULL");
+    DeviceGuard guard(h->device);
+    cudaError_t err;
+    if (!h->graph_exec) {
+        if (!h->cap_stream && (err = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)))
+            return cuda_fail(err, "capture stream");
+        if ((err = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)))
+            return cuda_fail(err, "begin capture");
+        const lpb_err r = enqueue_solve(h, h->cap_stream, false);
+        cudaGraph_t graph = nullptr;
+        err = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (r != LPB_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
         }
-        const Job& j = jobs[i];
-        if (j.kind == 0)
-            err = lpb::launch_mixed(h->d, h->tol, h->mp, h->d_order + j.g->offset, j.g->count, j.g->threads,
-                                    j.g->smem, h->fb_queue, h->fb_len, h->num_mixed, h->diag, ls);
-        else if (j.kind == 1)
-            err = lpb::launch_fp64_resident(h->d, h->tol, h->d_order + j.g->offset, j.g->count, j.g->threads,
-                                            j.g->smem, h->diag, ls);
-        else
-            err = lpb::launch_fp64_streamed(h->d, h->tol, h->d_order + h->streamed_offset, h->num_streamed,
-                                            h->streamed_slots, h->workspace, h->slot_bytes, h->counter, h->diag, ls);
-        if (err != cudaSuccess) return cuda_fail(err, "solver launch");
+        if (err != cudaSuccess) return cuda_fail(err, "end capture");
+        err = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (err != cudaSuccess) {
+            h->graph_exec = nullptr;
+            return cuda_fail(err, "graph instantiation");
+        }
     }
-    // Join back onto the caller's stream.
-    for (int lane = 0; lane < kLanes; ++lane) {
-        if (!used[lane]) continue;
-        if ((err = cudaEventRecord(h->ev_join[lane], h->lanes[lane])) ||
-            (err = cudaStreamWaitEvent(s, h->ev_join[lane], 0)))
-            return cuda_fail(err, "join");
-    }
-    if (tev && (err = cudaEventRecord(tev[1], s))) return cuda_fail(err, "timing");
-    // LPs the mixed-precision kernel did not certify: FP64 re-solve.
-    if (h->num_mixed > 0) {
-        err = lpb::launch_fp64_resident_queue(h->d, h->tol, h->fb_queue, h->fb_len, h->num_mixed, h->num_lps,
-                                              h->fb_counter, h->diag, h->fb_ctas, h->fb_threads, h->fb_smem, s);
-        if (err != cudaSuccess) return cuda_fail(err, "fallback launch");
-    }
-    if (tev) {
-        if ((err = cudaEventRecord(tev[2], s))) return cuda_fail(err, "timing");
-        ++h->timed_solves;
-    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((err = cudaGraphLaunch(h->graph_exec, s))) return cuda_fail(err, "graph launch");
     h->last_stream = s;
     h->solved = true;
     h->last_warm = false;
+    return LPB_OK;
+}
+
+lpb_err lp_batch_autotune(lp_batch* h, int32_t rounds, void* stream) {
+    g_last_error.clear();
+    if (!h) return fail(LPB_EINVAL, "handle is NULL");
+    if (rounds < 1 || rounds > 100) return fail(LPB_EINVAL, "rounds must be in [1, 100]");
+    DeviceGuard guard(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int sms = 0;
+    cudaError_t err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device))) return cuda_fail(err, "device query");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((err = cudaEventCreate(&e0)) || (err = cudaEventCreate(&e1))) return cuda_fail(err, "tuning events");
+    auto time_group = [&](int kind, Group& g, float& best) -> cudaError_t {
+        float t_min = 1e30f;
+        for (int r = 0; r < rounds; ++r) {
+            cudaError_t e;
+            if ((e = cudaMemsetAsync(h->diag, 0, 32, s))) return e;
+            if (kind == 0 && (e = cudaMemsetAsync(h->fb_len, 0, 4, s))) return e;
+            if ((e = cudaEventRecord(e0, s)) || (e = launch_group(h, kind, g, s)) || (e = cudaEventRecord(e1, s)) ||
+                (e = cudaEventSynchronize(e1)))
+                return e;
+            float ms = 0.0f;
+            if ((e = cudaEventElapsedTime(&ms, e0, e1))) return e;
+            t_min = std::min(t_min, ms);
+        }
+        best = t_min;
+        return cudaSuccess;
+    };
+    auto tune = [&](int kind, std::vector<Group>& gs, std::initializer_list<int> cand) -> cudaError_t {
+        for (Group& g : gs) {
+            Group best_g = g;
+            float best = 1e30f;
+            // the queue kernels keep a word of static shared memory: the
+            // largest groups run one CTA per LP only
+            const int max_form = g.smem <= lpb::kMaxSmemPerBlock - 1024 ? 1 : 0;
+            for (int persistent = 0; persistent <= max_form; ++persistent)
+                for (int threads : cand) {
+                    Group t = g;
+                    t.threads = threads;
+                    t.persistent = persistent;
+                    if (persistent) {
+                        const int per_sm = kind == 0 ? lpb::mixed_queue_ctas_per_sm(threads, t.smem)
+                                                     : lpb::fp64_resident_queue_ctas_per_sm(threads, t.smem);
+                        t.ctas = (int32_t)std::min<int64_t>((int64_t)sms * per_sm, t.count);
+                    }
+                    float ms = 0.0f;
+                    cudaError_t e = time_group(kind, t, ms);
+                    if (e != cudaSuccess) return e;
+                    if (ms < best) { best = ms; best_g = t; }
+                }
+            best_g.tuned_ms = best;
+            g = best_g;
+        }
+        return cudaSuccess;
+    };
+    err = tune(1, h->groups, {64, 128, 256, 512});
+    if (!err) err = tune(0, h->mixed_groups, {64, 128, 256});
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err) return cuda_fail(err, "autotune");
+    if (h->graph_exec) {  // the captured solve has the old launch forms
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
+    h->solved = false;  // the trial launches left partial outputs
+    return LPB_OK;
+}
+
+lpb_err lp_batch_set_group_form(lp_batch* h, int32_t index, int32_t threads, int32_t persistent) {
+    g_last_error.clear();
+    if (!h) return fail(LPB_EINVAL, "handle is NULL");
+    const int32_t nr = (int32_t)h->groups.size(), nm = (int32_t)h->mixed_groups.size();
+    if (index < 0 || index >= nr + nm) return fail(LPB_EINVAL, "group index out of range (or a streamed group)");
+    const int kind = index < nr ? 1 : 0;
+    if (threads < (kind == 0 ? 64 : 32) || threads > lpb::kMaxThreads || threads % 32)
+        return fail(LPB_EINVAL, "threads must be a multiple of 32 within the kernel's range");
+    if (persistent != 0 && persistent != 1) return fail(LPB_EINVAL, "persistent must be 0 or 1");
+    DeviceGuard guard(h->device);
+    Group& g = index < nr ? h->groups[index] : h->mixed_groups[index - nr];
+    if (persistent && g.smem > lpb::kMaxSmemPerBlock - 1024)
+        return fail(LPB_EINVAL, "this group's shared memory leaves no room for the persistent form");
+    g.threads = threads;
+    g.persistent = persistent;
+    g.tuned_ms = -1.0f;
+    if (persistent) {
+        int sms = 0;
+        cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        if (err) return cuda_fail(err, "device query");
+        const int per_sm = kind == 0 ? lpb::mixed_queue_ctas_per_sm(threads, g.smem)
+                                     : lpb::fp64_resident_queue_ctas_per_sm(threads, g.smem);
+        g.ctas = (int32_t)std::min<int64_t>((int64_t)sms * per_sm, g.count);
+    }
+    if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
+    return LPB_OK;
+}
+
+lpb_err lp_batch_group_info(lp_batch* h, int32_t index, lp_batch_group* out) {
+    if (!h || !out) return fail(LPB_EINVAL, "handle or out is NULL");
+    const int32_t nr = (int32_t)h->groups.size(), nm = (int32_t)h->mixed_groups.size();
+    const int32_t total = nr + nm + (h->num_streamed > 0 ? 1 : 0);
+    if (index < 0 || index >= total) return fail(LPB_EINVAL, "group index out of range");
+    std::memset(out, 0, sizeof *out);
+    if (index < nr + nm) {
+        const Group& g = index < nr ? h->groups[index] : h->mixed_groups[index - nr];
+        out->kind = index < nr ? 1 : 0;
+        out->count = g.count;
+        out->threads = g.threads;
+        out->persistent = g.persistent;
+        out->smem_bytes = (int64_t)g.smem;
+        out->tuned_ms = g.tuned_ms;
+    } else {
+        out->kind = 2;
+        out->count = h->num_streamed;
+        out->threads = lpb::kStreamedThreads;
+        out->persistent = 1;
+        out->smem_bytes = 0;
+        out->tuned_ms = -1.0f;
+    }
     return LPB_OK;
 }
 

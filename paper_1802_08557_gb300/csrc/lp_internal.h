@@ -185,6 +185,14 @@ int fp64_resident_queue_ctas_per_sm(int threads, size_t smem);
 
 // Checks (lp_api.cu helpers in lp_prepare.cu): counts non-finite values of
 // A, b, c into *bad and the rows with b_i < 0 of every LP into k[].
+// Persistent form of the mixed-precision kernel: CTAs take order[idx] for idx
+// from an atomic counter (zeroed here) until *count.
+cudaError_t launch_mixed_queue(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
+                               const int32_t* order, const int32_t* count, int32_t* counter, int ctas, int threads,
+                               size_t smem, int32_t* fb_queue, int32_t* fb_len, int32_t fb_cap, int32_t* diag,
+                               cudaStream_t stream);
+int mixed_queue_ctas_per_sm(int threads, size_t smem);
+
 // Learned warm start (lp_warm.cu): features [num_lps x (m+n)] = (b, c) as
 // FP32; the restricted-LP solve and FP64 check of each LP from the network's
 // logits (uncertified LPs appended to fb_queue); labels [num_lps x m] = 1 where

@@ -671,6 +671,29 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
     mixed_solve(g, B, tol, mp, order[blockIdx.x], smem + SmallLayout::total, fb_queue, fb_len, fb_cap, diag);
 }
 
+// Persistent CTAs over a list: LP order[idx] for idx taken from an atomic
+// counter (0 at launch) until *count is reached.
+__global__ void __launch_bounds__(kMaxThreads, 2)
+mixed_queue_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, const int32_t* __restrict__ order,
+                   const int32_t* __restrict__ count, int32_t* __restrict__ counter, int32_t* __restrict__ fb_queue,
+                   int32_t* __restrict__ fb_len, const int32_t fb_cap, int32_t* __restrict__ diag)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int next;
+    const int n_items = *count;
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int idx = next;
+        __syncthreads();
+        if (idx >= n_items) break;
+        BlockGroup g(reinterpret_cast<long long*>(smem + SmallLayout::red64),
+                     reinterpret_cast<unsigned*>(smem + SmallLayout::red32));
+        mixed_solve(g, B, tol, mp, order[idx], smem + SmallLayout::total, fb_queue, fb_len, fb_cap, diag);
+        __syncthreads();
+    }
+}
+
 // One warp per LP (blockDim = 32): for small tableaux, where a whole CTA per
 // LP mostly waits at barriers.
 __global__ void __launch_bounds__(32, 32)
@@ -689,6 +712,9 @@ cudaError_t mixed_kernel_prepare() {
     cudaError_t err = cudaFuncSetAttribute(mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(kMaxSmemPerBlock - 1024));
     if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(mixed_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kMaxSmemPerBlock - 1024));
+    if (err != cudaSuccess) return err;
     return cudaFuncSetAttribute(mixed_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(kMaxSmemPerBlock - 1024));
 }
@@ -701,6 +727,24 @@ cudaError_t launch_mixed(const DeviceBatch& B, const Tolerances& tol, const Mixe
         mixed_warp_kernel<<<count, 32, smem, stream>>>(B, tol, mp, order, fb_queue, fb_len, fb_cap, diag);
     else
         mixed_kernel<<<count, threads, smem, stream>>>(B, tol, mp, order, fb_queue, fb_len, fb_cap, diag);
+    return cudaGetLastError();
+}
+
+int mixed_queue_ctas_per_sm(int threads, size_t smem) {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mixed_queue_kernel, threads, smem) != cudaSuccess)
+        return 1;
+    return blocks > 0 ? blocks : 1;
+}
+
+cudaError_t launch_mixed_queue(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
+                               const int32_t* order, const int32_t* count, int32_t* counter, int ctas, int threads,
+                               size_t smem, int32_t* fb_queue, int32_t* fb_len, int32_t fb_cap, int32_t* diag,
+                               cudaStream_t stream) {
+    cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
+    if (err != cudaSuccess) return err;
+    mixed_queue_kernel<<<ctas, threads, smem, stream>>>(B, tol, mp, order, count, counter, fb_queue, fb_len, fb_cap,
+                                                         diag);
     return cudaGetLastError();
 }
 

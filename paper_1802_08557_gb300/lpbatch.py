@@ -29,7 +29,8 @@ EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_r
             "lpb_strerror", "lpb_last_error", "lp_solve_uniform_noalloc", "lp_hyperbox_solve",
             "lp_mlp_create", "lp_mlp_num_params", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_set_scaling",
             "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients", "lp_mlp_destroy", "lp_batch_solve_warm",
-            "lp_batch_features", "lp_batch_active_labels")
+            "lp_batch_features", "lp_batch_active_labels", "lp_batch_solve_graph", "lp_batch_autotune",
+            "lp_batch_group_info", "lp_batch_set_group_form")
 
 
 class LPBatchOpts(ctypes.Structure):
@@ -42,6 +43,18 @@ class LPBatchOpts(ctypes.Structure):
         ("tau", ctypes.c_double),
         ("block_threads", ctypes.c_int32),
         ("schedule", ctypes.c_int32),
+    ]
+
+
+class LPBatchGroup(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("count", ctypes.c_int32),
+        ("threads", ctypes.c_int32),
+        ("persistent", ctypes.c_int32),
+        ("smem_bytes", ctypes.c_int64),
+        ("tuned_ms", ctypes.c_float),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -116,6 +129,14 @@ def load(path: str | None = None):
         L.lp_mlp_gradients.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, _vp, ctypes.POINTER(ctypes.c_double),
                                        _vp]
         L.lp_mlp_destroy.argtypes = [_vp]
+        L.lp_batch_solve_graph.argtypes = [_vp, _vp]
+        L.lp_batch_solve_graph.restype = ctypes.c_int
+        L.lp_batch_autotune.argtypes = [_vp, _i32, _vp]
+        L.lp_batch_autotune.restype = ctypes.c_int
+        L.lp_batch_group_info.argtypes = [_vp, _i32, ctypes.POINTER(LPBatchGroup)]
+        L.lp_batch_group_info.restype = ctypes.c_int
+        L.lp_batch_set_group_form.argtypes = [_vp, _i32, _i32, _i32]
+        L.lp_batch_set_group_form.restype = ctypes.c_int
         L.lp_batch_solve_warm.argtypes = [_vp, _vp, ctypes.c_float, _vp]
         L.lp_batch_solve_warm.restype = ctypes.c_int
         L.lp_batch_features.argtypes = [_vp, _vp, _vp]
@@ -311,6 +332,30 @@ def lp_solve_uniform_noalloc(num_lps, m, n, A, b, c, status, iters, obj, x, y=No
                                            _addr(status), _addr(iters), _addr(obj), _addr(x), _addr(y),
                                            ctypes.byref(opts) if opts is not None else None,
                                            _stream_handle(stream))
+
+
+def lp_batch_solve_graph(h, stream=None):
+    _check(load().lp_batch_solve_graph(h, _stream_handle(stream)), "lp_batch_solve_graph")
+
+
+def lp_batch_autotune(h, rounds: int = 2, stream=None):
+    _check(load().lp_batch_autotune(h, rounds, _stream_handle(stream)), "lp_batch_autotune")
+
+
+def lp_batch_groups(h) -> list:
+    """The plan's launch groups as dicts (see include/lpbatch.h)."""
+    out = []
+    n = lp_batch_plan_info(h)["num_groups"]
+    for i in range(n):
+        g = LPBatchGroup()
+        if load().lp_batch_group_info(h, i, ctypes.byref(g)) != LPB_OK:
+            break
+        out.append({name: getattr(g, name) for name, _ in LPBatchGroup._fields_ if name != "reserved"})
+    return out
+
+
+def lp_batch_set_group_form(h, index: int, threads: int, persistent: bool):
+    _check(load().lp_batch_set_group_form(h, index, threads, 1 if persistent else 0), "lp_batch_set_group_form")
 
 
 def lp_batch_solve_warm(h, net, threshold: float = 0.2, stream=None):

@@ -1,0 +1,101 @@
+"""Launch forms of uneven batches: one CTA per LP or persistent CTAs over a
+work queue (longest work first), thread counts picked by the autotuner, and
+the solve captured in a CUDA graph.  None of these may change a single bit of
+the results (each LP's arithmetic is the same whatever runs it)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_1802_08557_gb300 import lpbatch as lpb
+from paper_1802_08557_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("status", "iters", "obj", "x", "y")
+
+
+def _same(a, b):
+    for k in KEYS:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def _batches():
+    return {
+        "uneven_fp64": (W.uneven_dense(400, lo=8, hi=120, start=3), lpb.LP_PREC_FP64),
+        "dense_mixed": (W.mixed_sign_dense(1500, 30, 30, start=5), lpb.LP_PREC_FP32_REFINE),
+        "uneven_mixed": (W.uneven_dense(300, lo=8, hi=90, start=9), lpb.LP_PREC_FP32_REFINE),
+    }
+
+
+@pytest.mark.parametrize("name", ["uneven_fp64", "dense_mixed", "uneven_mixed"])
+def test_forced_forms_give_identical_results(name):
+    batch, prec = _batches()[name]
+    s = lpb.BatchSolver(batch, opts=lpb.lpb_default_opts(precision=prec))
+    try:
+        s.solve()
+        ref = s.results()
+        groups = lpb.lp_batch_groups(s.h)
+        assert groups and sum(g["count"] for g in groups) == batch.num_lps
+        for persistent in (True, False):
+            for threads in (64, 256):
+                for i, g in enumerate(groups):
+                    if g["kind"] in (0, 1) and (not persistent or g["smem_bytes"] <= 226 * 1024):
+                        lpb.lp_batch_set_group_form(s.h, i, threads, persistent)
+                s.solve()
+                _same(s.results(), ref)
+                assert s.plan_info()["internal_errors"] == 0
+                assert all(g["persistent"] == int(persistent) for g in lpb.lp_batch_groups(s.h)
+                           if g["kind"] != 2 and g["smem_bytes"] <= 226 * 1024)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("name", ["uneven_fp64", "dense_mixed"])
+def test_autotune_keeps_results(name):
+    batch, prec = _batches()[name]
+    s = lpb.BatchSolver(batch, opts=lpb.lpb_default_opts(precision=prec))
+    try:
+        s.solve()
+        ref = s.results()
+        lpb.lp_batch_autotune(s.h, rounds=1)
+        with pytest.raises(lpb.LPBError):
+            s.results()  # the trial launches left partial outputs: solve first
+        s.solve()
+        _same(s.results(), ref)
+        tuned = [g for g in lpb.lp_batch_groups(s.h) if g["kind"] != 2]
+        assert tuned and all(g["tuned_ms"] >= 0.0 for g in tuned)
+    finally:
+        s.close()
+
+
+def test_graph_solve_replays_the_plain_solve():
+    batch, prec = _batches()["dense_mixed"]
+    s = lpb.BatchSolver(batch, opts=lpb.lpb_default_opts(precision=prec))
+    try:
+        s.solve()
+        ref = s.results()
+        for _ in range(3):
+            lpb.lp_batch_solve_graph(s.h)
+            _same(s.results(), ref)
+        assert s.plan_info()["num_fallback"] >= 0
+        # a changed form drops the graph; the next graph solve recaptures it
+        lpb.lp_batch_set_group_form(s.h, 0, 128, True)
+        lpb.lp_batch_solve_graph(s.h)
+        _same(s.results(), ref)
+    finally:
+        s.close()
+
+
+def test_lpt_order_and_errors():
+    batch = W.uneven_dense(200, lo=8, hi=150, start=11)
+    s = lpb.BatchSolver(batch)
+    try:
+        with pytest.raises(lpb.LPBError):
+            lpb.lp_batch_set_group_form(s.h, 0, 48, False)   # not a multiple of 32
+        with pytest.raises(lpb.LPBError):
+            lpb.lp_batch_set_group_form(s.h, 10_000, 64, False)
+        with pytest.raises(lpb.LPBError):
+            lpb.lp_batch_autotune(s.h, rounds=0)
+    finally:
+        s.close()
