@@ -405,7 +405,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
         for (int i0 = 0; i0 < m; i0 += nt) {
             const int i = i0 + tid;
             const int v = (i < m) ? row_var[i] : -1;
-            if (i < m && v >= n) spos[v - n] = -(i + 1);
+            if (i < m && v >= n && v < nm) spos[v - n] = -(i + 1);
             const bool st = (i < m) && (v < n);
             int tot;
             const int pos = s + g.prefix_count(st, tot);
@@ -610,6 +610,125 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
         }
         g.sync();
         ok = conv && bad == 0 && s_cd > mp.cert_tol * fmax(1.0, dmax) * cmax;
+    }
+
+    // ---- infeasible: Farkas certificate from the phase-I basis ---------------
+    // y_c = reduced cost of slack c in the phase-I row (0 when basic) is the
+    // multiplier vector of phase I's dual: y >= 0, A^T y >= 0, b^T y = -w* < 0,
+    // and y_i <= 1 on the negated rows.  It is refined in FP64 so that y^T B
+    // equals phase I's costs on the basis (0 for structurals and slacks; y_i = 1
+    // on a row whose artificial is basic), then checked: y >= 0, A^T y >= 0 to
+    // rounding, and gamma = -b^T y with gamma / max(y on negated rows) above
+    // 1e-6 max(1, max|b|).  That quotient bounds the phase-I optimum from below
+    // (sum of artificials >= gamma / max y_neg for every x >= 0), so the FP64
+    // rule (infeasible when the phase-I optimum exceeds 1e-9 max(1, max|b|))
+    // reaches the same status.  Otherwise the LP goes to the FP64 re-solve.
+    bool farkas = false;
+    if (status == kInfeasible && k > 0) {
+        int sf = 0;
+        for (int j = 1 + tid; j <= Cvar; j += nt) {
+            const int v = tb.col_var[j];
+            if (v >= n && v < nm) spos[v - n] = j;
+        }
+        for (int i0 = 0; i0 < m; i0 += nt) {
+            const int i = i0 + tid;
+            const int v = (i < m) ? row_var[i] : -1;
+            if (i < m && v >= n && v < nm) spos[v - n] = -(i + 1);
+            const bool st = (i < m) && (v < n);
+            int tot;
+            const int pos = sf + g.prefix_count(st, tot);
+            if (st) slist[pos] = i;
+            sf += tot;
+        }
+        unsigned badpos = 0, dummy;
+        for (int c = tid; c < m; c += nt) {
+            const int p = spos[c];
+            badpos += (p == 0 || p > Cvar || -p - 1 >= m) ? 1u : 0u;
+        }
+        g.count_min(badpos, 0u, badpos, dummy);
+        if (badpos == 0) {
+            const float* Tw = T + (m + 1) * LD;
+            for (int c = tid; c < m; c += nt) {
+                const int p = spos[c];
+                yv[c] = (p > 0) ? (double)Tw[p] : 0.0;
+            }
+            g.sync();
+            for (int it = 0; it < 4; ++it) {
+                // residual of y^T B = c_B (phase-I costs), one entry per tableau row
+                for (int t = tid; t < sf; t += nt) {
+                    const int v = row_var[slist[t]];
+                    double r = 0.0;
+#pragma unroll 4
+                    for (int c = 0; c < m; ++c) r = __fma_rn(-yv[c], A[(size_t)c * n + v], r);
+                    res[slist[t]] = r;
+                }
+                for (int i = tid; i < m; i += nt) {
+                    const int v = row_var[i];
+                    if (v >= n && v < nm) res[i] = -yv[v - n];
+                    else if (v >= nm) res[i] = __dsub_rn(yv[neg[v - nm]], 1.0);
+                }
+                g.sync();
+                for (int c = tid; c < m; c += nt) {
+                    const int p = spos[c];
+                    double d;
+                    if (p > 0) {
+                        float acc = 0.0f;
+#pragma unroll 4
+                        for (int i = 0; i < m; ++i) acc = __fmaf_rn(__double2float_rn(res[i]), T[i * LD + p], acc);
+                        d = (double)acc;
+                    } else {
+                        d = res[-p - 1];
+                    }
+                    yv[c] = __dadd_rn(yv[c], d);
+                }
+                g.sync();
+            }
+            // checks: y >= 0 (tiny negatives clamped), A^T y >= 0 to rounding
+            unsigned bad = 0;
+            for (int c = tid; c < m; c += nt) {
+                const double yc = yv[c];
+                bad += (yc < -1e-9) ? 1u : 0u;
+                if (yc < 0.0) yv[c] = 0.0;
+            }
+            g.count_min(bad, 0u, bad, dummy);
+            for (int j = tid; j < n; j += nt) {
+                double gj = 0.0, sc = 0.0;
+#pragma unroll 4
+                for (int c = 0; c < m; ++c) {
+                    const double a = A[(size_t)c * n + j];
+                    gj = __fma_rn(yv[c], a, gj);
+                    sc = __fma_rn(yv[c], fabs(a), sc);
+                }
+                bad += (gj < -1e-12 * sc) ? 1u : 0u;
+            }
+            double yneg = 0.0;
+            for (int t = tid; t < k; t += nt) yneg = fmax(yneg, yv[neg[t]]);
+            const double ymax_neg = block_absmax(g, yneg);
+            g.count_min(bad, 0u, bad, dummy);
+            __shared__ double s_gamma;
+            if (warp == 0) {
+                double part = 0.0;
+                for (int c = lane; c < m; c += 32) part = __fma_rn(-bv[c], yv[c], part);
+                for (int o = 16; o > 0; o >>= 1) part = __dadd_rn(part, __shfl_xor_sync(kFull, part, o));
+                if (lane == 0) s_gamma = part;
+            }
+            g.sync();
+            farkas = bad == 0 && ymax_neg > 0.0 && s_gamma > 1e-6 * bmax * ymax_neg;
+        }
+    }
+    if (farkas) {
+        double* __restrict__ x = B.x + B.x_off[lp];
+        for (int j = tid; j < n; j += nt) x[j] = 0.0;
+        if (B.y) {
+            double* __restrict__ y = B.y + B.y_off[lp];
+            for (int c = tid; c < m; c += nt) y[c] = yv[c];
+        }
+        if (tid == 0) {
+            B.status[lp] = kInfeasible;
+            B.iters[lp] = iters;
+            B.obj[lp] = 0.0;
+        }
+        return;
     }
 
     if (!ok) {

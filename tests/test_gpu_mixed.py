@@ -31,6 +31,16 @@ def check_mixed(batch, max_fallback_frac=1.0, cert_mask=None):
     xo, yo = batch.x_offsets(), batch.y_offsets()
     for k in range(batch.num_lps):
         assert g["status"][k] == r["status"][k], f"LP {k}: status {g['status'][k]} vs oracle {r['status'][k]}"
+        if r["status"][k] == 1:
+            # infeasible: y is a Farkas certificate (y >= 0, A^T y >= 0, b^T y < 0)
+            A, b, c = batch.lp(k)
+            y = g["y"][yo[k]:yo[k] + A.shape[0]]
+            # (tolerances as in the oracle's own certificate pins)
+            scale = max(1.0, np.abs(A).max(), np.abs(b).max(), np.abs(c).max())
+            ys = max(1.0, float(np.abs(y).max()))
+            assert y.min() >= -1e-7 * ys, f"LP {k}: Farkas y has negative entries"
+            assert np.all(A.T @ y >= -1e-7 * scale * ys), f"LP {k}: A^T y < 0"
+            assert float(b @ y) < 0.0, f"LP {k}: b^T y >= 0"
         if r["status"][k] != 0:
             continue
         A, b, c = batch.lp(k)
