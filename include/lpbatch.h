@@ -87,7 +87,10 @@ typedef struct {
 } lp_batch_opts;
 
 /* Kernel choice.  AUTO: shared-memory-resident tableau when it fits in one
- * CTA, global workspace otherwise.  STREAMED: global workspace for every LP. */
+ * CTA; else split by rows over the shared memory of a thread-block cluster of
+ * 2-16 CTAs (the smallest that holds it; all CTAs take the same decisions, so
+ * the results are those of the one-CTA kernel); else a global workspace.
+ * STREAMED: global workspace for every LP. */
 enum { LPB_SCHED_AUTO = 0, LPB_SCHED_STREAMED = 1 };
 
 typedef struct lp_batch lp_batch;   /* opaque; owned by the library */
@@ -173,6 +176,8 @@ typedef struct {
     int32_t num_warm_certified;/* last lp_batch_solve_warm: LPs certified from the
                                   network's proposal (the rest: num_fallback)     */
     int32_t num_warm_rounds;   /* last lp_batch_solve_warm: restricted LPs solved    */
+    int32_t num_cluster;       /* LPs solved on a thread-block cluster (tableau split
+                                  over the CTAs' shared memory)                   */
     int64_t max_smem_bytes;    /* largest shared-memory footprint of a launch        */
     int64_t workspace_bytes;   /* global workspace of the streamed LPs               */
 } lp_batch_plan;
@@ -202,13 +207,14 @@ lpb_err lp_batch_autotune(lp_batch *h, int32_t rounds, void *stream);
 /* One launch group of the plan: index 0 .. lp_batch_plan.num_groups-1 (the
  * FP64 re-solve queue of the mixed path is not listed). */
 typedef struct {
-    int32_t kind;        /* 0 mixed precision, 1 FP64 shared-memory resident, 2 FP64 streamed */
+    int32_t kind;        /* 0 mixed precision, 1 FP64 shared-memory resident, 2 FP64 streamed,
+                            3 FP64 on a thread-block cluster                  */
     int32_t count;       /* LPs in the group                                  */
     int32_t threads;     /* threads per CTA                                   */
     int32_t persistent;  /* 1: persistent CTAs over a work queue              */
     int64_t smem_bytes;  /* dynamic shared memory per CTA                     */
     float tuned_ms;      /* group time of the chosen form (-1: not tuned)     */
-    int32_t reserved;
+    int32_t cluster_ctas;/* kind 3: CTAs per cluster (else 0)                 */
 } lp_batch_group;
 lpb_err lp_batch_group_info(lp_batch *h, int32_t index, lp_batch_group *out);
 /* Set a group's form by hand (threads a multiple of 32, at least 64 for mixed

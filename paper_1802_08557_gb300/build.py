@@ -32,6 +32,7 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcom
 # the L1/shared-memory split), and L1 gives that data no reuse anyway.
 PER_FILE = {
     "lp_fp64_simplex.cu": ["--fmad=false", "-Xptxas", "-dlcm=cg"],
+    "lp_cluster.cu": ["--fmad=false"],
 }
 
 

@@ -191,6 +191,15 @@ struct lp_batch {
     // per launch group: LP count and work counter of the persistent form
     int32_t* group_len = nullptr;
     int32_t* group_counter = nullptr;
+    // LPs on thread-block clusters: one group per cluster size
+    struct ClusterGroup {
+        int64_t offset;
+        int32_t count, C, clusters, gi;
+        size_t smem;
+    };
+    std::vector<ClusterGroup> cluster_groups;
+    int32_t* cluster_counter = nullptr;
+    int32_t num_cluster = 0;
     // captured solve (lp_batch_solve_graph)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -260,6 +269,8 @@ lpb_err enqueue_solve(lp_batch* h, cudaStream_t s, bool timing) {
     for (const Group& g : h->mixed_groups) jobs.push_back({0, &g, g.count});
     for (const Group& g : h->groups) jobs.push_back({1, &g, g.count});
     if (h->num_streamed > 0) jobs.push_back({2, nullptr, h->num_streamed});
+    for (size_t ci = 0; ci < h->cluster_groups.size(); ++ci)
+        jobs.push_back({3, reinterpret_cast<const Group*>(ci), h->cluster_groups[ci].count});
     std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& b) { return a.count > b.count; });
     cudaEvent_t* tev = (!timing || h->tev.empty()) ? nullptr : &h->tev[3 * (size_t)(h->timed_solves % kTimingRing)];
     if (tev && (err = cudaEventRecord(tev[0], s))) return cuda_fail(err, "timing");
@@ -273,11 +284,16 @@ lpb_err enqueue_solve(lp_batch* h, cudaStream_t s, bool timing) {
             used[lane] = true;
         }
         const Job& j = jobs[i];
-        if (j.kind == 2)
+        if (j.kind == 2) {
             err = lpb::launch_fp64_streamed(h->d, h->tol, h->d_order + h->streamed_offset, h->num_streamed,
                                             h->streamed_slots, h->workspace, h->slot_bytes, h->counter, h->diag, ls);
-        else
+        } else if (j.kind == 3) {
+            const lp_batch::ClusterGroup& cg = h->cluster_groups[reinterpret_cast<size_t>(j.g)];
+            err = lpb::launch_fp64_cluster(h->d, h->tol, h->d_order + cg.offset, cg.count, cg.C, cg.clusters, cg.smem,
+                                           h->cluster_counter + cg.gi, h->diag, ls);
+        } else {
             err = launch_group(h, j.kind, *j.g, ls);
+        }
         if (err != cudaSuccess) return cuda_fail(err, "solver launch");
     }
     for (int lane = 0; lane < kLanes; ++lane) {
@@ -448,6 +464,7 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     // the others go to the streamed kernel (global workspace slots).
     std::map<std::pair<int, size_t>, std::vector<int32_t>> buckets, mixed_buckets;
     std::vector<int32_t> streamed;
+    std::map<int, std::vector<int32_t>> cluster_buckets;  // cluster size -> LPs
     const size_t queue_smem_cap = lpb::kMaxSmemPerBlock - 1024;
     h->uniform_m = hm[0];
     h->uniform_n = hn[0];
@@ -467,6 +484,16 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
             h->fb_smem = std::max(h->fb_smem, need);
             h->fb_threads = std::max(h->fb_threads, pick_threads(hm[k], hn[k], hk[k], 0));  // FP64 kernel's own choice
             continue;
+        }
+        if (need > lpb::kMaxSmemPerBlock && o.schedule == LPB_SCHED_AUTO) {
+            // the smallest cluster whose CTAs hold the tableau's rows
+            int C = 0;
+            for (int c = 2; c <= lpb::kMaxClusterCtas && !C; ++c)
+                if (lpb::cluster_smem_bytes(hm[k], hn[k], hk[k], c) <= lpb::kMaxSmemPerBlock - 1024) C = c;
+            if (C) {
+                cluster_buckets[C].push_back(k);
+                continue;
+            }
         }
         if (need > lpb::kMaxSmemPerBlock || o.schedule == LPB_SCHED_STREAMED) {
             streamed.push_back(k);
@@ -523,6 +550,38 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
                 return bail_cuda(err, "group counters");
         }
     }
+    // cluster groups (a cluster shape that cannot be placed goes to the streamed kernel)
+    for (auto& kv : cluster_buckets) {
+        const int C = kv.first;
+        lpt(kv.second);
+        size_t smem = 0;
+        for (int32_t k : kv.second) smem = std::max(smem, lpb::cluster_smem_bytes(hm[k], hn[k], hk[k], C));
+        smem = (smem + 1023) / 1024 * 1024;
+        int active = 0;
+        if ((err = lpb::cluster_kernel_prepare()) == cudaSuccess) active = lpb::cluster_max_active(C, smem);
+        cudaGetLastError();
+        if (active <= 0) {
+            for (int32_t k : kv.second) {
+                streamed.push_back(k);
+                h->slot_bytes = std::max(h->slot_bytes, lpb::streamed_slot_bytes(hm[k], hn[k], hk[k]));
+            }
+            continue;
+        }
+        lp_batch::ClusterGroup g;
+        g.offset = (int64_t)order.size();
+        g.count = (int32_t)kv.second.size();
+        g.C = C;
+        g.clusters = std::min<int32_t>(g.count, active);
+        g.gi = (int32_t)h->cluster_groups.size();
+        g.smem = smem;
+        order.insert(order.end(), kv.second.begin(), kv.second.end());
+        h->cluster_groups.push_back(g);
+        h->num_cluster += g.count;
+    }
+    if (!h->cluster_groups.empty() &&
+        (err = alloc(h, &h->cluster_counter, h->cluster_groups.size(), s)))
+        return bail_cuda(err, "cluster counters");
+    lpt(streamed);
     h->streamed_offset = (int64_t)order.size();
     h->num_streamed = (int32_t)streamed.size();
     order.insert(order.end(), streamed.begin(), streamed.end());
@@ -711,9 +770,21 @@ lpb_err lp_batch_set_group_form(lp_batch* h, int32_t index, int32_t threads, int
 lpb_err lp_batch_group_info(lp_batch* h, int32_t index, lp_batch_group* out) {
     if (!h || !out) return fail(LPB_EINVAL, "handle or out is NULL");
     const int32_t nr = (int32_t)h->groups.size(), nm = (int32_t)h->mixed_groups.size();
-    const int32_t total = nr + nm + (h->num_streamed > 0 ? 1 : 0);
+    const int32_t nc = (int32_t)h->cluster_groups.size();
+    const int32_t total = nr + nm + nc + (h->num_streamed > 0 ? 1 : 0);
     if (index < 0 || index >= total) return fail(LPB_EINVAL, "group index out of range");
     std::memset(out, 0, sizeof *out);
+    if (index >= nr + nm && index < nr + nm + nc) {
+        const lp_batch::ClusterGroup& g = h->cluster_groups[index - nr - nm];
+        out->kind = 3;
+        out->count = g.count;
+        out->threads = 512;
+        out->persistent = 1;
+        out->smem_bytes = (int64_t)g.smem;
+        out->tuned_ms = -1.0f;
+        out->cluster_ctas = g.C;
+        return LPB_OK;
+    }
     if (index < nr + nm) {
         const Group& g = index < nr ? h->groups[index] : h->mixed_groups[index - nr];
         out->kind = index < nr ? 1 : 0;
@@ -888,9 +959,10 @@ lpb_err lp_batch_stage_times(lp_batch* h, float* stage_ms, int32_t* num_solves) 
 
 lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
     if (!h || !plan) return fail(LPB_EINVAL, "handle or plan is NULL");
-    plan->num_groups = (int32_t)(h->groups.size() + h->mixed_groups.size()) + (h->num_streamed > 0 ? 1 : 0) +
-                       (h->num_mixed > 0 ? 1 : 0);
-    plan->num_resident = h->num_lps - h->num_streamed;
+    plan->num_groups = (int32_t)(h->groups.size() + h->mixed_groups.size() + h->cluster_groups.size()) +
+                       (h->num_streamed > 0 ? 1 : 0) + (h->num_mixed > 0 ? 1 : 0);
+    plan->num_resident = h->num_lps - h->num_streamed - h->num_cluster;
+    plan->num_cluster = h->num_cluster;
     plan->num_mixed = h->num_mixed;
     plan->num_fallback = 0;
     plan->num_warm_certified = 0;

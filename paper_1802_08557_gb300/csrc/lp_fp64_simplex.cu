@@ -190,16 +190,28 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
 
     for (int j = tid; j <= Cvar; j += nt)
         tb.col_var[j] = (j == 0) ? -1 : (j <= n ? j - 1 : n + neg[j - 1 - n]);
-    for (int i = warp; i < m; i += nw) {
-        const bool isneg = row_var[i] >= nm;
-        const double* Ai = A + (size_t)i * n;
-        double* Ti = T + (size_t)i * LD;
-        for (int j = lane; j <= Cvar; j += 32) {
-            double v;
-            if (j == 0) v = bv[i];
-            else if (j <= n) v = Ai[j - 1];
-            else v = (neg[j - 1 - n] == i) ? 1.0 : 0.0;
-            Ti[j] = isneg ? -v : v;
+    {
+        // A into rows 0..m-1, columns 1..n: one flat pass with several
+        // independent loads in flight per thread; then b and the slack columns
+        const int64_t cnt = (int64_t)m * n;
+        int i = tid / n, j = tid - i * n;
+        const int di = nt / n, dj = nt - di * n;
+#pragma unroll 4
+        for (int64_t idx = tid; idx < cnt; idx += nt) {
+            const double v = A[idx];
+            T[(size_t)i * LD + 1 + j] = (row_var[i] >= nm) ? -v : v;
+            i += di;
+            j += dj;
+            if (j >= n) { j -= n; ++i; }
+        }
+        for (int r = warp; r < m; r += nw) {
+            const bool isneg = row_var[r] >= nm;
+            double* Tr = T + (size_t)r * LD;
+            for (int t = lane; t <= k; t += 32) {
+                const int jj = (t == 0) ? 0 : n + t;
+                const double v = (t == 0) ? bv[r] : ((neg[t - 1] == r) ? 1.0 : 0.0);
+                Tr[jj] = isneg ? -v : v;
+            }
         }
     }
     {

@@ -185,6 +185,41 @@ int fp64_resident_queue_ctas_per_sm(int threads, size_t smem);
 
 // Checks (lp_api.cu helpers in lp_prepare.cu): counts non-finite values of
 // A, b, c into *bad and the rows with b_i < 0 of every LP into k[].
+// FP64 simplex of one LP on a thread-block cluster of C CTAs (lp_cluster.cu):
+// rows split over the CTAs' shared memory, rp rows each; row labels, column
+// labels and exchange slots in every CTA.
+struct ClusterLayout {
+    int rp, LD;
+    size_t row_var, neg, xch, col_var, T, prow, ob, colE, rkey, total;
+};
+
+__host__ __device__ inline ClusterLayout cluster_layout(int m, int n, int k, int C) {
+    ClusterLayout L;
+    const int R = m + 1 + (k > 0 ? 1 : 0);
+    L.rp = (R + C - 1) / C;
+    L.LD = (n + k + 1) | 1;
+    size_t o = SmallLayout::total;
+    L.row_var = o; o += align16((size_t)(m + 2) * 4);
+    L.neg = o;     o += align16((size_t)m * 4);
+    L.xch = o;     o += 64;
+    L.col_var = o; o += align16((size_t)L.LD * 4);
+    L.T = o;       o += align16((size_t)L.rp * L.LD * 8);
+    L.prow = o;    o += align16((size_t)L.LD * 8);
+    L.ob = o;      o += align16((size_t)L.LD * 8);
+    L.colE = o;    o += align16((size_t)L.rp * 8);
+    L.rkey = o;    o += align16((size_t)L.rp * 8);
+    L.total = o;
+    return L;
+}
+
+constexpr int kMaxClusterCtas = 16;
+size_t cluster_smem_bytes(int m, int n, int k, int C);
+cudaError_t cluster_kernel_prepare();
+int cluster_max_active(int C, size_t smem);
+cudaError_t launch_fp64_cluster(const DeviceBatch& B, const Tolerances& tol, const int32_t* order, int32_t count,
+                                int C, int clusters, size_t smem, int32_t* counter, int32_t* diag,
+                                cudaStream_t stream);
+
 // Persistent form of the mixed-precision kernel: CTAs take order[idx] for idx
 // from an atomic counter (zeroed here) until *count.
 cudaError_t launch_mixed_queue(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,

@@ -54,7 +54,7 @@ class LPBatchGroup(ctypes.Structure):
         ("persistent", ctypes.c_int32),
         ("smem_bytes", ctypes.c_int64),
         ("tuned_ms", ctypes.c_float),
-        ("reserved", ctypes.c_int32),
+        ("cluster_ctas", ctypes.c_int32),
     ]
 
 
@@ -72,6 +72,7 @@ class LPBatchPlan(ctypes.Structure):
         ("internal_error_detail", ctypes.c_int32 * 5),
         ("num_warm_certified", ctypes.c_int32),
         ("num_warm_rounds", ctypes.c_int32),
+        ("num_cluster", ctypes.c_int32),
         ("max_smem_bytes", ctypes.c_int64),
         ("workspace_bytes", ctypes.c_int64),
     ]
@@ -350,7 +351,7 @@ def lp_batch_groups(h) -> list:
         g = LPBatchGroup()
         if load().lp_batch_group_info(h, i, ctypes.byref(g)) != LPB_OK:
             break
-        out.append({name: getattr(g, name) for name, _ in LPBatchGroup._fields_ if name != "reserved"})
+        out.append({name: getattr(g, name) for name, _ in LPBatchGroup._fields_})
     return out
 
 
