@@ -11,14 +11,17 @@
 // every CTA and updated identically.  One pivot:
 //   A. every CTA copies the objective row from its owner (DSMEM) and runs
 //      Step 1 on the copy (identical data -> identical entering column e);
-//   B. Step 2: each CTA's minimum ratio over its rows -> exchange slot,
-//      cluster barrier 1, minimum over the slots; each CTA's lowest row within
-//      the tie window and its pivot element -> slot, barrier 2, minimum row;
-//   C. the owner of the pivot row divides it by the pivot element into the
-//      tableau and into its pivot-row buffer; labels swapped in every copy;
-//      barrier 3;
-//   D. every CTA copies the pivot row from the owner's buffer and updates its
-//      own rows (and retires an artificial column); barrier 4.
+//   B. Step 2, screened as in the one-CTA kernel: FP32 ratio keys of each
+//      CTA's rows -> exchange slot, cluster barrier 1, cluster minimum and
+//      window; each CTA counts its candidates, computes their exact ratios,
+//      and normalizes its lowest candidate row into its pivot-row buffer
+//      (speculatively) -> slot, barrier 2.  One candidate in the cluster (the
+//      common case) is the exact answer and its buffer is ready; several take
+//      the exact rule (one more exchange) and, if the buffered row is not the
+//      chosen one, its owner normalizes again behind one more barrier;
+//   C. every CTA copies the pivot row from the owner's buffer and updates its
+//      own rows (and retires an artificial column); barrier 3.
+// So a pivot costs three cluster barriers in the common case.
 // Exchange slots alternate between pivots, so a slot is only rewritten after
 // every reader has passed a later barrier.  Every branch depends on replicated
 // values or on values read after a barrier, so all CTAs of a cluster take the
@@ -49,11 +52,15 @@ __device__ __forceinline__ double tie_thr(double v, double tau) {
 
 // Exchange slots in shared memory (two of each, alternating).
 struct Xch {
-    long long k64[2];
-    unsigned u32[2];
-    int pad[2];
-    double d[2];
+    long long fmin[2];  // Step 2: this CTA's minimum screened ratio key
+    long long rmin[2];  // Step 2: minimum exact ratio key over this CTA's candidates
+    unsigned cnt[2];    // Step 2: candidates in this CTA
+    unsigned sel[2];    // lowest candidate row (Step 2) / selected column (drive-out)
+    unsigned sel2[2];   // Step 2, several candidates: lowest row within the exact window
+    unsigned pad[2];
+    double pe[2];       // pivot element of `sel`
 };
+static_assert(sizeof(Xch) <= kClusterXchBytes, "exchange slots exceed their shared-memory region");
 
 __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int C, const int q,
                                                 const DeviceBatch& B, const Tolerances& tol, const int lp,
@@ -114,14 +121,19 @@ __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int
         const double* Ab = A + (size_t)r_lo * n;
         int lr = (n > 0) ? tid / n : 0, j = tid - lr * n;
         const int dl = nt / n, dj = nt - dl * n;
-#pragma unroll 4
         for (int64_t idx = tid; idx < cnt; idx += nt) {
-            const double v = Ab[idx];
-            T[(size_t)lr * LD + 1 + j] = (row_var[r_lo + lr] >= nm) ? -v : v;
+            cp_async8(T + (size_t)lr * LD + 1 + j, Ab + idx);
             lr += dl;
             j += dj;
             if (j >= n) { j -= n; ++lr; }
         }
+        cp_async_wait_all();
+        __syncthreads();
+        if (k > 0)  // negated rows (b_i < 0)
+            for (int64_t idx = tid; idx < cnt; idx += nt) {
+                const int l2 = (int)(idx / n), j2 = (int)(idx - (int64_t)l2 * n);
+                if (row_var[r_lo + l2] >= nm) T[(size_t)l2 * LD + 1 + j2] = -T[(size_t)l2 * LD + 1 + j2];
+            }
         for (int lr2 = 0; lr2 < rows_a; ++lr2) {
             const int r = r_lo + lr2;
             const bool isneg = row_var[r] >= nm;
@@ -157,25 +169,28 @@ __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int
     const int max_iters = tol.max_iters > 0 ? tol.max_iters : 50 * (m + n);
     int iters = 0, status = -1, phase = (k > 0) ? 1 : 2, yrow = m, xs = 0;
 
-    // Pivot on row l, column e over rows < Ract (C and D above); pe is the
-    // pivot element.  Returns the label of the leaving variable.
-    auto pivot = [&](int l, int e, double pe, int Ract) -> int {
+    // Pivot on row l, column e over rows < Ract.  With `ready`, the owner of
+    // row l has already written the normalized row into its buffer; otherwise
+    // it normalizes now and a barrier publishes the buffer.  Returns the label
+    // of the leaving variable.
+    auto pivot = [&](int l, int e, int Ract, bool ready) -> int {
         const int Cact = Cvar + 1;
         const int ql = l / rp;
         if (q == ql) {
             double* Tl = T + (size_t)(l - r_lo) * LD;
-            for (int j = tid; j < Cact; j += nt) {
-                const double v = __ddiv_rn((j == e) ? 1.0 : Tl[j], pe);
-                Tl[j] = v;
-                prow[j] = v;
+            if (!ready) {
+                const double pe = colE[l - r_lo];
+                for (int j = tid; j < Cact; j += nt) prow[j] = __ddiv_rn((j == e) ? 1.0 : Tl[j], pe);
+                __syncthreads();
             }
+            for (int j = tid; j < Cact; j += nt) Tl[j] = prow[j];
         }
         if (tid == 0) {
             const int ev = col_var[e];
             col_var[e] = row_var[l];
             row_var[l] = ev;
         }
-        cl.sync();  // 3: pivot row ready
+        if (!ready) cl.sync();  // the pivot row is published
         const double* src = cl.map_shared_rank(prow, ql);
         for (int j = tid; j < Cact; j += nt) ob[j] = src[j];
         __syncthreads();
@@ -200,7 +215,7 @@ __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int
             --Cvar;
             __syncthreads();
         }
-        cl.sync();  // 4: every row updated
+        cl.sync();  // every row updated
         return left;
     };
 
@@ -236,15 +251,10 @@ __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int
                         if (col_var[j] < nm && abskey(Ti[j]) > key_eps_piv)
                             sel = min(sel, ((unsigned)col_var[j] << 16) | (unsigned)j);
                     sel = red.min_u32(sel);
-                    if (tid == 0) {
-                        xch->u32[xs] = sel;
-                        xch->d[xs] = (sel != 0xffffffffu) ? Ti[sel & 0xffffu] : 0.0;
-                    }
+                    if (tid == 0) xch->sel[xs] = sel;
                 }
                 cl.sync();
-                const Xch* xo = cl.map_shared_rank(xch, qi);
-                const unsigned sel = xo->u32[xs];
-                const double pe = xo->d[xs];
+                const unsigned sel = cl.map_shared_rank(xch, qi)->sel[xs];
                 xs ^= 1;
                 if (sel == 0xffffffffu) continue;  // redundant row
                 if (iters >= max_iters) { status = kIterLimit; break; }
@@ -252,7 +262,7 @@ __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int
                 for (int lr = tid; lr < nrow; lr += nt)
                     if (r_lo + lr < m + 1) colE[lr] = T[(size_t)lr * LD + e];
                 __syncthreads();
-                pivot(i, e, pe, m + 1);
+                pivot(i, e, m + 1, false);
                 ++iters;
             }
             phase = 2;
@@ -271,53 +281,123 @@ __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int
             status = kNumerical;
             break;
         }
-        // ---- B: Step 2 over this CTA's rows, then over the cluster -------
-        long long rloc = LLONG_MAX;
+        // ---- B: Step 2.  FP32 screen of this CTA's rows (rows whose operands
+        // leave [2^-100, 2^100] are always candidates), cluster minimum, window
+        // max(2^-12, 8 tau) relative + max(2^-20, 8 tau) absolute (wider than
+        // every FP32 rounding error); one candidate in the cluster is the exact
+        // answer, several get the exact rule on their exact ratios.
+        int floc = INT_MAX;
         for (int lr = tid; lr < nrow; lr += nt) {
             const int r = r_lo + lr;
             if (r >= Ract) continue;
             const double t = T[(size_t)lr * LD + e];
             colE[lr] = t;
+            long long code = LLONG_MAX;  // not eligible
+            if (r < m && okey(t) > key_eps_piv) {
+                const double beta = T[(size_t)lr * LD];
+                const int et = dexp(t), eb = dexp(beta);
+                const bool safe = et >= -100 && et <= 100 && (abskey(beta) == 0 || (eb >= -100 && eb <= 100));
+                if (safe) {
+                    const int fk = fkey(__fdividef(__double2float_rn(beta), __double2float_rn(t)));
+                    code = fk;
+                    floc = min(floc, fk);
+                } else {
+                    code = LLONG_MIN;
+                }
+            }
+            rkey[lr] = code;
+        }
+        floc = red.min_i32(floc);
+        if (tid == 0) xch->fmin[xs] = floc;
+        cl.sync();  // 1
+        int fmin = INT_MAX;
+        for (int qq = 0; qq < C; ++qq) fmin = min(fmin, (int)cl.map_shared_rank(xch, qq)->fmin[xs]);
+        long long fwin = LLONG_MIN;
+        if (fmin != INT_MAX) {
+            const float fm = fval(fmin);
+            fwin = fkey(fm + __fmaf_rn(tol.ratio_rel, fabsf(fm), tol.ratio_abs));
+        }
+        unsigned lcnt = 0, lsel = 0xffffffffu;
+        for (int lr = tid; lr < nrow; lr += nt) {
+            const long long code = rkey[lr];
+            if (r_lo + lr < m && (code == LLONG_MIN || (code != LLONG_MAX && code <= fwin))) {
+                ++lcnt;
+                lsel = min(lsel, (unsigned)(r_lo + lr));
+            }
+        }
+        red.count_min(lcnt, lsel, lcnt, lsel);
+        // exact ratio keys of this CTA's candidates (every other row: none),
+        // so that rkey no longer holds screen keys in any CTA
+        long long rloc = LLONG_MAX;
+        for (int lr = tid; lr < nrow; lr += nt) {
+            const long long code = rkey[lr];
             long long rk = LLONG_MAX;
-            if (r < m && okey(t) > key_eps_piv) rk = okey(__ddiv_rn(T[(size_t)lr * LD], t));
+            if (r_lo + lr < m && (code == LLONG_MIN || (code != LLONG_MAX && code <= fwin)))
+                rk = okey(__ddiv_rn(T[(size_t)lr * LD], colE[lr]));
             rkey[lr] = rk;
             rloc = min(rloc, rk);
         }
-        rloc = red.min_i64(rloc);
-        if (tid == 0) xch->k64[xs] = rloc;
-        cl.sync();  // 1
+        if (lcnt > 0) rloc = red.min_i64(rloc);
+        // speculative: the lowest candidate row, normalized, into the buffer
+        if (lcnt > 0) {
+            const int lr = (int)lsel - r_lo;
+            const double pe = colE[lr];
+            const double* Tl = T + (size_t)lr * LD;
+            for (int j = tid; j <= Cvar; j += nt) prow[j] = __ddiv_rn((j == e) ? 1.0 : Tl[j], pe);
+        }
+        if (tid == 0) {
+            xch->cnt[xs] = lcnt;
+            xch->sel[xs] = lsel;
+            xch->rmin[xs] = rloc;
+            xch->pe[xs] = (lcnt > 0) ? colE[lsel - r_lo] : 0.0;
+        }
+        cl.sync();  // 2
+        unsigned total = 0, l = 0xffffffffu;
+        double pe = 0.0;
         long long rmin = LLONG_MAX;
-        for (int qq = 0; qq < C; ++qq) rmin = min(rmin, cl.map_shared_rank(xch, qq)->k64[xs]);
-        if (rmin == LLONG_MAX) {
+        for (int qq = 0; qq < C; ++qq) {
+            const Xch* xo = cl.map_shared_rank(xch, qq);
+            const unsigned c = xo->cnt[xs];
+            total += c;
+            if (c > 0 && xo->sel[xs] < l) { l = xo->sel[xs]; pe = xo->pe[xs]; }
+            rmin = min(rmin, xo->rmin[xs]);
+        }
+        bool ready = true;
+        if (total == 0) {
+            xs ^= 1;
             status = (phase == 2) ? kUnbounded : kNumerical;
             break;
         }
-        const long long rthr = okey(tie_thr(kval(rmin), tol.tau));
-        unsigned lsel = 0xffffffffu;
-        for (int lr = tid; lr < nrow; lr += nt)
-            if (r_lo + lr < m && rkey[lr] <= rthr) lsel = min(lsel, (unsigned)(r_lo + lr));
-        lsel = red.min_u32(lsel);
-        if (tid == 0) {
-            xch->u32[xs] = lsel;
-            xch->d[xs] = (lsel != 0xffffffffu) ? colE[lsel - r_lo] : 0.0;
-        }
-        cl.sync();  // 2
-        unsigned l = 0xffffffffu;
-        double pe = 0.0;
-        for (int qq = 0; qq < C; ++qq) {
-            const Xch* xo = cl.map_shared_rank(xch, qq);
-            const unsigned v = xo->u32[xs];
-            if (v < l) { l = v; pe = xo->d[xs]; }
+        if (total > 1) {
+            // exact rule over the candidates: lowest row within the tie window
+            // of the minimum exact ratio
+            const long long rthr = okey(tie_thr(kval(rmin), tol.tau));
+            unsigned s2 = 0xffffffffu;
+            for (int lr = tid; lr < nrow; lr += nt)
+                if (r_lo + lr < m && rkey[lr] <= rthr) s2 = min(s2, (unsigned)(r_lo + lr));
+            s2 = red.min_u32(s2);
+            if (tid == 0) xch->sel2[xs] = s2;
+            cl.sync();
+            l = 0xffffffffu;
+            for (int qq = 0; qq < C; ++qq) l = min(l, cl.map_shared_rank(xch, qq)->sel2[xs]);
+            // the owner's buffer holds its lowest candidate: ready if that is l
+            ready = false;
+            if (l < (unsigned)m) {
+                const Xch* xo = cl.map_shared_rank(xch, (int)l / rp);
+                ready = xo->cnt[xs] > 0 && xo->sel[xs] == l;
+                pe = ready ? xo->pe[xs] : 0.0;
+            }
         }
         xs ^= 1;
         if (l >= (unsigned)m) {
-            if (tid == 0 && q == 0) record_internal_error(diag, 2, lp, (int)l, 0, iters, phase, e);
+            if (tid == 0 && q == 0) record_internal_error(diag, 2, lp, (int)l, (int)total, iters, phase, e);
             status = kNumerical;
             break;
         }
+        if (!ready) pe = cl.map_shared_rank(colE, (int)l / rp)[l - ((int)l / rp) * rp];
         if (abskey(pe) >= 0x7FF0000000000000LL) { status = kNumerical; break; }
         if (iters >= max_iters) { status = kIterLimit; break; }
-        pivot((int)l, e, pe, Ract);
+        pivot((int)l, e, Ract, ready);
         ++iters;
     }
 

@@ -57,6 +57,14 @@ __device__ __forceinline__ float fval(int k) { return __int_as_float(k ^ ((k >> 
 // Unbiased binary exponent of a double from its bits (-1023 for 0 and subnormals).
 __device__ __forceinline__ int dexp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF) - 1023; }
 
+// Asynchronous 8-byte copy global -> shared (no register staging, so a thread
+// can have many in flight); cp_async_wait_all waits for this thread's copies.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Block-wide reductions over per-warp `redux` results.  Each call writes
 // one slot per warp, waits at a barrier, reads every slot, and waits at a
 // second barrier before returning, so no later write can overtake a read of

@@ -196,13 +196,31 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         const int64_t cnt = (int64_t)m * n;
         int i = tid / n, j = tid - i * n;
         const int di = nt / n, dj = nt - di * n;
+        if (!kStreamed) {
+            // shared-memory tableau: asynchronous copies, all in flight at once,
+            // then the negated rows in place
+            for (int64_t idx = tid; idx < cnt; idx += nt) {
+                cp_async8(T + (size_t)i * LD + 1 + j, A + idx);
+                i += di;
+                j += dj;
+                if (j >= n) { j -= n; ++i; }
+            }
+            cp_async_wait_all();
+            __syncthreads();
+            if (k > 0)
+                for (int64_t idx = tid; idx < cnt; idx += nt) {
+                    const int i2 = (int)(idx / n), j2 = (int)(idx - (int64_t)i2 * n);
+                    if (row_var[i2] >= nm) T[(size_t)i2 * LD + 1 + j2] = -T[(size_t)i2 * LD + 1 + j2];
+                }
+        } else {
 #pragma unroll 4
-        for (int64_t idx = tid; idx < cnt; idx += nt) {
-            const double v = A[idx];
-            T[(size_t)i * LD + 1 + j] = (row_var[i] >= nm) ? -v : v;
-            i += di;
-            j += dj;
-            if (j >= n) { j -= n; ++i; }
+            for (int64_t idx = tid; idx < cnt; idx += nt) {
+                const double v = A[idx];
+                T[(size_t)i * LD + 1 + j] = (row_var[i] >= nm) ? -v : v;
+                i += di;
+                j += dj;
+                if (j >= n) { j -= n; ++i; }
+            }
         }
         for (int r = warp; r < m; r += nw) {
             const bool isneg = row_var[r] >= nm;

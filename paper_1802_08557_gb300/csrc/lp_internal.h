@@ -193,6 +193,8 @@ struct ClusterLayout {
     size_t row_var, neg, xch, col_var, T, prow, ob, colE, rkey, total;
 };
 
+constexpr size_t kClusterXchBytes = 128;  // exchange slots of one CTA (lp_cluster.cu)
+
 __host__ __device__ inline ClusterLayout cluster_layout(int m, int n, int k, int C) {
     ClusterLayout L;
     const int R = m + 1 + (k > 0 ? 1 : 0);
@@ -201,7 +203,7 @@ __host__ __device__ inline ClusterLayout cluster_layout(int m, int n, int k, int
     size_t o = SmallLayout::total;
     L.row_var = o; o += align16((size_t)(m + 2) * 4);
     L.neg = o;     o += align16((size_t)m * 4);
-    L.xch = o;     o += 64;
+    L.xch = o;     o += kClusterXchBytes;
     L.col_var = o; o += align16((size_t)L.LD * 4);
     L.T = o;       o += align16((size_t)L.rp * L.LD * 8);
     L.prow = o;    o += align16((size_t)L.LD * 8);
