@@ -310,14 +310,16 @@ def run_ours(args):
     else:
         # FP32 tableau pivots: (m+1)(n+1) FMAs each on the FP32 pipe
         achieved = 2.0 * fmas / (kernel_ms * 1e-3) / 1e9
-        roofline = {"bound": "alu", "kernel": "mixed_kernel", "achieved": achieved,
+        mixed_threads = {g["threads"] for g in lpb.lp_batch_groups(h) if g["kind"] == 0}
+        mixed_name = "mixed_warp_kernel" if mixed_threads == {32} else "mixed_kernel"
+        roofline = {"bound": "alu", "kernel": mixed_name, "achieved": achieved,
                     "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP32_PEAK_GFLOPS,
                     "traffic": None, "kernel_ms": kernel_ms, "fallback_ms": fallback_ms,
                     "peak_note": "FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz",
                     "work": "sum over LPs of reported pivots x (m+1)(n+1) FMAs (FP32 pivots of certified LPs; "
                             "the FP64 re-solve's pivots stand in for those of uncertified LPs; FP64 certificate "
                             "work not counted)",
-                    "timing": "CUDA events around the solve's launch groups (all mixed_kernel launches, "
+                    "timing": f"CUDA events around the solve's launch groups (all {mixed_name} launches, "
                               "fork to join), mean of the timed steps"}
 
     # ---- hyperbox LPs (Section 4.4, Eq. 7): support function of one box ----

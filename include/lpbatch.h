@@ -195,8 +195,8 @@ lpb_err lp_batch_solve_graph(lp_batch *h, void *stream);
 
 /* Launch-form tuner.  For every launch group of the plan (LPs of one kernel,
  * thread count and shared-memory size), time the group alone on `stream` with
- * every candidate thread count (FP64: 64, 128, 256, 512; mixed precision: 64,
- * 128, 256) in both forms -- one CTA per LP, or persistent CTAs over an atomic
+ * every candidate thread count (FP64: 32, 64, 128, 256, 512; mixed precision:
+ * 32, 64, 128, 256) in both forms -- one CTA per LP, or persistent CTAs over an atomic
  * work queue with the LPs in descending order of work (groups that need the
  * whole 227 KB of a CTA's shared memory: one CTA per LP only) -- `rounds` times each,
  * and keep the fastest.  No counterpart in the paper.  Results of a solve do
@@ -212,14 +212,15 @@ typedef struct {
     int32_t count;       /* LPs in the group                                  */
     int32_t threads;     /* threads per CTA                                   */
     int32_t persistent;  /* 1: persistent CTAs over a work queue              */
-    int64_t smem_bytes;  /* dynamic shared memory per CTA                     */
+    int64_t smem_bytes;  /* dynamic shared memory per CTA of the current form */
     float tuned_ms;      /* group time of the chosen form (-1: not tuned)     */
     int32_t cluster_ctas;/* kind 3: CTAs per cluster (else 0)                 */
 } lp_batch_group;
 lpb_err lp_batch_group_info(lp_batch *h, int32_t index, lp_batch_group *out);
-/* Set a group's form by hand (threads a multiple of 32, at least 64 for mixed
- * precision, at most 512; persistent 0 or 1, and 0 for groups that need more
- * than 226 KB of shared memory).  Streamed groups are fixed. */
+/* Set a group's form by hand (threads a multiple of 32, at most 512; for a
+ * mixed-precision group 32 without persistent selects one warp per LP;
+ * persistent 0 or 1, and 0 for groups that need more than 226 KB of shared
+ * memory).  Streamed groups are fixed. */
 lpb_err lp_batch_set_group_form(lp_batch *h, int32_t index, int32_t threads, int32_t persistent);
 
 /* Device timing of the stages of lp_batch_solve, off by default.  enable != 0

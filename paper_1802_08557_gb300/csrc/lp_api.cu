@@ -88,7 +88,8 @@ struct Group {
     int64_t offset;  // into the order array
     int32_t count;
     int32_t threads;
-    size_t smem;
+    size_t smem;             // shared memory of the block forms
+    size_t smem_warp = 0;    // mixed groups: of the one-warp form (no block reduction scratch)
     int32_t gi = 0;          // index into the per-group device counters
     int32_t persistent = 0;  // 1: persistent CTAs over an atomic work queue
     int32_t ctas = 0;        // CTAs of the persistent form
@@ -116,22 +117,22 @@ constexpr int64_t kMaxWorkspaceBytes = int64_t(16) << 30;
 int pick_threads(int m, int n, int k, int requested) {
     if (requested > 0) return std::min(std::max(32, (requested + 31) / 32 * 32), lpb::kMaxThreads);
     const int64_t e = (int64_t)(m + 1 + (k > 0)) * (n + k + 1);
-    if (e <= 128) return 32;
-    if (e <= 1024) return 64;
+    // measured best on GB300 (mixed-sign dense m x m, m = 20..100)
+    if (e <= 1024) return 32;
+    if (e <= 3072) return 64;
     if (e <= 8192) return 128;
     if (e <= 32768) return 256;
     return 512;
 }
 
 // Threads per CTA of the mixed-precision kernel; 0 requested = from the
-// tableau size (measured best: 64 for 50x50 tableaux, more for larger ones).
-// A request that rounds to 32 selects the one-warp-per-LP variant (no block
-// barriers; measured slower on 50x50: shared memory caps the LPs per SM, so
-// one warp each leaves fewer warps in flight).
+// tableau size.  32 selects the one-warp-per-LP variant (no block barriers):
+// measured best up to 70x70 tableaux (50x50: 16.3 ms per 1e5 LPs against
+// 19.7 ms at 64 threads), 128 best at 100x100.
 int mixed_threads(int m, int n, int k, int requested) {
     if (requested > 0) return pick_threads(m, n, k, requested);
     const int64_t e = (int64_t)(m + 1 + (k > 0)) * (n + k + 1);
-    if (e <= 8192) return 64;
+    if (e <= 8192) return 32;
     if (e <= 32768) return 128;
     return 256;
 }
@@ -247,8 +248,8 @@ cudaError_t launch_group(lp_batch* h, int kind, const Group& g, cudaStream_t ls)
         if (g.persistent)
             return lpb::launch_mixed_queue(h->d, h->tol, h->mp, order, h->group_len + g.gi, h->group_counter + g.gi,
                                            g.ctas, g.threads, g.smem, h->fb_queue, h->fb_len, h->num_mixed, h->diag, ls);
-        return lpb::launch_mixed(h->d, h->tol, h->mp, order, g.count, g.threads, g.smem, h->fb_queue, h->fb_len,
-                                 h->num_mixed, h->diag, ls);
+        return lpb::launch_mixed(h->d, h->tol, h->mp, order, g.count, g.threads, g.threads == 32 ? g.smem_warp : g.smem,
+                                 h->fb_queue, h->fb_len, h->num_mixed, h->diag, ls);
     }
     if (g.persistent)
         return lpb::launch_fp64_resident_queue(h->d, h->tol, order, h->group_len + g.gi, g.count, h->num_lps,
@@ -477,9 +478,7 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         if (o.precision == LP_PREC_FP32_REFINE && o.schedule == LPB_SCHED_AUTO && need <= queue_smem_cap) {
             // FP32 tableau + FP64 certificate; the FP64 fallback runs resident.
             const int threads = mixed_threads(hm[k], hn[k], hk[k], o.block_threads);
-            const size_t mbytes = threads == 32 ? lpb::mixed_layout(hm[k], hn[k], hk[k]).total
-                                                : lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]);
-            const size_t msmem = (mbytes + 1023) / 1024 * 1024;
+            const size_t msmem = (lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]) + 1023) / 1024 * 1024;
             mixed_buckets[{threads, msmem}].push_back(k);
             h->fb_smem = std::max(h->fb_smem, need);
             h->fb_threads = std::max(h->fb_threads, pick_threads(hm[k], hn[k], hk[k], 0));  // FP64 kernel's own choice
@@ -534,6 +533,8 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         g.count = (int32_t)kv.second.size();
         g.threads = kv.first.first;
         g.smem = kv.first.second;
+        for (int32_t k : kv.second)
+            g.smem_warp = std::max(g.smem_warp, (lpb::mixed_layout(hm[k], hn[k], hk[k]).total + 1023) / 1024 * 1024);
         order.insert(order.end(), kv.second.begin(), kv.second.end());
         h->mixed_groups.push_back(g);
         h->num_mixed += g.count;
@@ -723,8 +724,8 @@ lpb_err lp_batch_autotune(lp_batch* h, int32_t rounds, void* stream) {
         }
         return cudaSuccess;
     };
-    err = tune(1, h->groups, {64, 128, 256, 512});
-    if (!err) err = tune(0, h->mixed_groups, {64, 128, 256});
+    err = tune(1, h->groups, {32, 64, 128, 256, 512});
+    if (!err) err = tune(0, h->mixed_groups, {32, 64, 128, 256});
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err) return cuda_fail(err, "autotune");
@@ -742,7 +743,7 @@ lpb_err lp_batch_set_group_form(lp_batch* h, int32_t index, int32_t threads, int
     const int32_t nr = (int32_t)h->groups.size(), nm = (int32_t)h->mixed_groups.size();
     if (index < 0 || index >= nr + nm) return fail(LPB_EINVAL, "group index out of range (or a streamed group)");
     const int kind = index < nr ? 1 : 0;
-    if (threads < (kind == 0 ? 64 : 32) || threads > lpb::kMaxThreads || threads % 32)
+    if (threads < 32 || threads > lpb::kMaxThreads || threads % 32)
         return fail(LPB_EINVAL, "threads must be a multiple of 32 within the kernel's range");
     if (persistent != 0 && persistent != 1) return fail(LPB_EINVAL, "persistent must be 0 or 1");
     DeviceGuard guard(h->device);
@@ -791,7 +792,7 @@ lpb_err lp_batch_group_info(lp_batch* h, int32_t index, lp_batch_group* out) {
         out->count = g.count;
         out->threads = g.threads;
         out->persistent = g.persistent;
-        out->smem_bytes = (int64_t)g.smem;
+        out->smem_bytes = (int64_t)(index >= nr && g.threads == 32 && !g.persistent ? g.smem_warp : g.smem);
         out->tuned_ms = g.tuned_ms;
     } else {
         out->kind = 2;

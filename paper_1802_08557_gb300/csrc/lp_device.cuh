@@ -54,6 +54,22 @@ __device__ __forceinline__ int fkey(float f) {
 }
 __device__ __forceinline__ float fval(int k) { return __int_as_float(k ^ ((k >> 31) & INT_MAX)); }
 
+// |v| as a float by integer operations only (no FP64-pipe conversion, which
+// GB300 issues at the FP64 rate): the double's exponent rebiased and its
+// significand truncated to 24 bits, so for |v| in [2^-126, 2^128) the result
+// is below |v| by less than 2^-23 relative; 0 gives 0, smaller magnitudes
+// give at most 7 * 2^-149, larger ones the largest finite float.
+__device__ __forceinline__ float f64_abs_to_f32_trunc(double v) {
+    const int hi = __double2hiint(v) & 0x7fffffff;
+    const unsigned lo = (unsigned)__double2loint(v);
+    const int t = min(max(hi - (896 << 20), 0), 0x0FEFFFFF);
+    return __uint_as_float(__funnelshift_l(lo, (unsigned)t, 3));
+}
+// v as a float, the same truncation with v's sign.
+__device__ __forceinline__ float f64_to_f32_trunc(double v) {
+    return __uint_as_float(__float_as_uint(f64_abs_to_f32_trunc(v)) | ((unsigned)__double2hiint(v) & 0x80000000u));
+}
+
 // Unbiased binary exponent of a double from its bits (-1023 for 0 and subnormals).
 __device__ __forceinline__ int dexp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF) - 1023; }
 

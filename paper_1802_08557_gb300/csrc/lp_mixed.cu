@@ -37,6 +37,12 @@ __device__ __forceinline__ long long pack_key(int hi, unsigned lo) {
     return (long long)(((unsigned long long)(unsigned)hi << 32) | (unsigned long long)lo);
 }
 
+// Rows per batch of the pivot update (all loads of a batch issued before its
+// stores).  Measured on 50x50 LPs: deeper batches, deeper unrolling of the
+// loops that read A, or a larger register budget for the one-warp kernel
+// were all slower (larger code, same latency-bound issue rate).
+constexpr int kPivotBatch = 4;
+
 struct Tab32 {
     float* T;
     float* colE;
@@ -75,8 +81,9 @@ __device__ __forceinline__ QuadMap quad_map(int tid, int nt, int Cact) {
 //           gives fma(-t_ie, 1/PE, 0) = -t_ie/PE there (the leaving variable's
 //           column);
 //  phase B: t_rj = fma(-t_re, r_j, t_rj) for r != l over quads of 4 columns
-//           (16-byte loads and stores; LD is a multiple of 4), 4 rows per
-//           batch with every load of a batch issued before its stores.
+//           (16-byte loads and stores; LD is a multiple of 4), kPivotBatch
+//           rows per batch with every load of a batch issued before its
+//           stores.
 //  Columns of the last quad beyond Cact are padding: updated, never read.
 template <class G>
 __device__ __forceinline__ int pivot32(G& g, Tab32& tb, int Ract, int Cact, int l, int e, const QuadMap& qm) {
@@ -98,29 +105,27 @@ __device__ __forceinline__ int pivot32(G& g, Tab32& tb, int Ract, int Cact, int 
     const int left = tb.col_var[e];
     const int nq = (Cact + 3) >> 2;
     const int qstep = qm.qstep, r0 = qm.r0, rg = qm.rg;
+    constexpr int kB = kPivotBatch;
     for (int q = qm.q0; q < nq; q += qstep) {
         const float4 p = *reinterpret_cast<const float4*>(Tl + 4 * q);
         float* base = T + 4 * q;
         int r = r0;
-        for (; r + 3 * rg < Ract; r += 4 * rg) {
-            float4* a0 = reinterpret_cast<float4*>(base + r * LD);
-            float4* a1 = reinterpret_cast<float4*>(base + (r + rg) * LD);
-            float4* a2 = reinterpret_cast<float4*>(base + (r + 2 * rg) * LD);
-            float4* a3 = reinterpret_cast<float4*>(base + (r + 3 * rg) * LD);
-            float4 v0 = *a0, v1 = *a1, v2 = *a2, v3 = *a3;
-            const float c0 = -colE[r], c1 = -colE[r + rg], c2 = -colE[r + 2 * rg], c3 = -colE[r + 3 * rg];
-            v0.x = __fmaf_rn(c0, p.x, v0.x); v0.y = __fmaf_rn(c0, p.y, v0.y);
-            v0.z = __fmaf_rn(c0, p.z, v0.z); v0.w = __fmaf_rn(c0, p.w, v0.w);
-            v1.x = __fmaf_rn(c1, p.x, v1.x); v1.y = __fmaf_rn(c1, p.y, v1.y);
-            v1.z = __fmaf_rn(c1, p.z, v1.z); v1.w = __fmaf_rn(c1, p.w, v1.w);
-            v2.x = __fmaf_rn(c2, p.x, v2.x); v2.y = __fmaf_rn(c2, p.y, v2.y);
-            v2.z = __fmaf_rn(c2, p.z, v2.z); v2.w = __fmaf_rn(c2, p.w, v2.w);
-            v3.x = __fmaf_rn(c3, p.x, v3.x); v3.y = __fmaf_rn(c3, p.y, v3.y);
-            v3.z = __fmaf_rn(c3, p.z, v3.z); v3.w = __fmaf_rn(c3, p.w, v3.w);
-            if (r != l) *a0 = v0;
-            if (r + rg != l) *a1 = v1;
-            if (r + 2 * rg != l) *a2 = v2;
-            if (r + 3 * rg != l) *a3 = v3;
+        for (; r + (kB - 1) * rg < Ract; r += kB * rg) {
+            float4 v[kB];
+            float c[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                v[u] = *reinterpret_cast<const float4*>(base + (r + u * rg) * LD);
+                c[u] = -colE[r + u * rg];
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                v[u].x = __fmaf_rn(c[u], p.x, v[u].x); v[u].y = __fmaf_rn(c[u], p.y, v[u].y);
+                v[u].z = __fmaf_rn(c[u], p.z, v[u].z); v[u].w = __fmaf_rn(c[u], p.w, v[u].w);
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u)
+                if (r + u * rg != l) *reinterpret_cast<float4*>(base + (r + u * rg) * LD) = v[u];
         }
         for (; r < Ract; r += rg) {
             float4* a0 = reinterpret_cast<float4*>(base + r * LD);
@@ -177,6 +182,8 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
     double* yv = reinterpret_cast<double*>(big + L0.yv);
     double* dv = reinterpret_cast<double*>(big + L0.dv);
     double* res = reinterpret_cast<double*>(big + L0.res);
+    float* zf = reinterpret_cast<float*>(big + L0.zf);  // FP32 copy of the vector being refined
+    float* rf = reinterpret_cast<float*>(big + L0.rf);  // FP32 copy of its residual
     int* row_var = reinterpret_cast<int*>(big + L0.row_var);
     int* neg = reinterpret_cast<int*>(big + L0.neg);
     int* spos = reinterpret_cast<int*>(big + L0.spos);
@@ -436,35 +443,42 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
     // sum |B_c,i| |z_i| (backward error) and that correction moved no
     // component by more than fwd_tol of max(|z_i|, 1e-8 max|z|) (forward
     // error: an ill-conditioned basis stalls and is left to the FP64 re-solve).
-    // The tolerance tests run in FP32 (converting costs no FP64-pipe time).
+    // The tolerance tests run in FP32 on magnitudes: |a| of A by integer
+    // operations (f64_abs_to_f32_trunc; A is range-checked), z and r through
+    // their FP32 copies zf, rf, converted once where they are written.
     const float conv_tol32 = (float)mp.conv_tol, fwd_tol32 = (float)mp.fwd_tol;
     auto refine = [&](double* z, int rhs_var, bool& conv) {
         conv = false;
         double zloc = 0.0;
-        for (int i = tid; i < m; i += nt) zloc = (abskey(z[i]) > abskey(zloc)) ? z[i] : zloc;
-        const float zfloor = 1e-8f * __double2float_ru(block_absmax(g, zloc));
+        for (int i = tid; i < m; i += nt) {
+            zloc = (abskey(z[i]) > abskey(zloc)) ? z[i] : zloc;
+            zf[i] = fabs32(__double2float_rn(z[i]));
+        }
+        const float zfloor = 1e-8f * __double2float_ru(block_absmax(g, zloc));  // barrier: zf complete
         for (int it = 0; it <= mp.max_refine; ++it) {
             unsigned bad = 0;
             for (int c = tid; c < m; c += nt) {
                 double r;
                 if (rhs_var < 0) r = bv[c];
                 else r = (rhs_var < n) ? -A[(size_t)c * n + rhs_var] : ((rhs_var - n == c) ? -1.0 : 0.0);
-                float mag = fabs32(__double2float_rn(r));
+                float mag = f64_abs_to_f32_trunc(r);  // b, A or 1: range-checked
                 const double* Ac = A + (size_t)c * n;
 #pragma unroll 4
                 for (int t = 0; t < s; ++t) {
                     const int i = slist[t];
                     const double a = Ac[row_var[i]];
                     r = __fma_rn(-a, z[i], r);
-                    mag = __fmaf_rn(fabs32(__double2float_rn(a)), fabs32(__double2float_rn(z[i])), mag);
+                    mag = __fmaf_rn(f64_abs_to_f32_trunc(a), zf[i], mag);
                 }
                 const int p = spos[c];
                 if (p < 0) {
                     r = __dsub_rn(r, z[-p - 1]);
-                    mag = __fadd_rn(mag, fabs32(__double2float_rn(z[-p - 1])));
+                    mag = __fadd_rn(mag, zf[-p - 1]);
                 }
                 res[c] = r;
-                bad += (!(fabs32(__double2float_rn(r)) <= conv_tol32 * mag) || isinf(mag)) ? 1u : 0u;
+                const float r32 = __double2float_rn(r);
+                rf[c] = r32;
+                bad += (!(fabs32(r32) <= conv_tol32 * mag) || isinf(mag)) ? 1u : 0u;
             }
             g.sync();
             unsigned fwdbad = 0;
@@ -473,15 +487,16 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
 #pragma unroll 4
                 for (int c = 0; c < m; ++c) {
                     const int p = spos[c];
-                    if (p > 0) acc = __fmaf_rn(T[i * LD + p], __double2float_rn(res[c]), acc);
+                    if (p > 0) acc = __fmaf_rn(T[i * LD + p], rf[c], acc);
                 }
                 const int v = row_var[i];
                 // the correction: B^-1 r (FP32), plus r_c exactly for a basic slack
                 const double d = (v >= n) ? __dadd_rn((double)acc, res[v - n]) : (double)acc;
                 const double znew = __dadd_rn(z[i], d);
                 z[i] = znew;
-                fwdbad += (!(fabs32(__double2float_rn(d)) <= fwd_tol32 * fmaxf(fabs32(__double2float_rn(znew)), zfloor)))
-                              ? 1u : 0u;
+                const float zn32 = fabs32(__double2float_rn(znew));
+                zf[i] = zn32;
+                fwdbad += (!(fabs32(__double2float_rn(d)) <= fwd_tol32 * fmaxf(zn32, zfloor))) ? 1u : 0u;
             }
             unsigned tot, dummy;
             g.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
@@ -507,8 +522,11 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
         g.sync();
         bool conv = false;
         double yloc = 0.0;
-        for (int c = tid; c < m; c += nt) yloc = (abskey(yv[c]) > abskey(yloc)) ? yv[c] : yloc;
-        const float yfloor = 1e-8f * __double2float_ru(block_absmax(g, yloc));
+        for (int c = tid; c < m; c += nt) {
+            yloc = (abskey(yv[c]) > abskey(yloc)) ? yv[c] : yloc;
+            zf[c] = __double2float_rn(yv[c]);  // y in FP32 (signed: the dual screen uses it)
+        }
+        const float yfloor = 1e-8f * __double2float_ru(block_absmax(g, yloc));  // barrier: zf complete
         for (int it = 0; it <= mp.max_refine; ++it) {
             // rho_i = c_(v_i) - y^T col(v_i) for each basic variable (by tableau row)
             unsigned bad = 0;
@@ -516,20 +534,23 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
                 const int i = slist[t];
                 const int v = row_var[i];
                 double r = cv[v];
-                float mag = fabs32(__double2float_rn(r));
+                float mag = f64_abs_to_f32_trunc(r);
 #pragma unroll 4
                 for (int c = 0; c < m; ++c) {
                     const double a = A[(size_t)c * n + v];
                     r = __fma_rn(-yv[c], a, r);
-                    mag = __fmaf_rn(fabs32(__double2float_rn(a)), fabs32(__double2float_rn(yv[c])), mag);
+                    mag = __fmaf_rn(f64_abs_to_f32_trunc(a), fabs32(zf[c]), mag);
                 }
                 res[i] = r;
-                bad += (!(fabs32(__double2float_rn(r)) <= conv_tol32 * mag) || isinf(mag)) ? 1u : 0u;
+                const float r32 = __double2float_rn(r);
+                rf[i] = r32;
+                bad += (!(fabs32(r32) <= conv_tol32 * mag) || isinf(mag)) ? 1u : 0u;
             }
             for (int i = tid; i < m; i += nt) {
                 const int v = row_var[i];
                 if (v >= n) {
                     res[i] = -yv[v - n];
+                    rf[i] = -zf[v - n];
                     bad += (abskey(yv[v - n]) != 0) ? 1u : 0u;
                 }
             }
@@ -541,38 +562,42 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
                 if (p > 0) {
                     float acc = 0.0f;
 #pragma unroll 4
-                    for (int i = 0; i < m; ++i) acc = __fmaf_rn(__double2float_rn(res[i]), T[i * LD + p], acc);
+                    for (int i = 0; i < m; ++i) acc = __fmaf_rn(rf[i], T[i * LD + p], acc);
                     d = (double)acc;
                 } else {
                     d = res[-p - 1];
                 }
                 const double ynew = __dadd_rn(yv[c], d);
                 yv[c] = ynew;
-                fwdbad += (!(fabs32(__double2float_rn(d)) <= fwd_tol32 * fmaxf(fabs32(__double2float_rn(ynew)), yfloor)))
-                              ? 1u : 0u;
+                const float yn32 = __double2float_rn(ynew);
+                zf[c] = yn32;
+                fwdbad += (!(fabs32(__double2float_rn(d)) <= fwd_tol32 * fmaxf(fabs32(yn32), yfloor))) ? 1u : 0u;
             }
             unsigned tot, dummy;
             g.count_min(bad + (fwdbad << 16), 0u, tot, dummy);
             if (tot == 0) { conv = true; break; }
         }
         // dual feasibility: y >= -tol and A^T y - c >= -tol on non-basic
-        // structurals; each reduced cost is screened in FP32 with an error
-        // bound and computed in FP64 only when the screen cannot decide
+        // structurals; each reduced cost is screened in FP32 (y from zf,
+        // rounded; a truncated by f64_to_f32_trunc, < 2^-23 relative) with an
+        // error bound and computed in FP64 only when the screen cannot decide
         unsigned bad = 0, dummy;
         for (int c = tid; c < m; c += nt) bad += (yv[c] < -tol_d) ? 1u : 0u;
         for (int j = 1 + tid; j <= Cvar; j += nt) {
             const int v = tb.col_var[j];
             if (v < n) {
-                float d32 = -__double2float_rn(cv[v]);
+                float d32 = -f64_to_f32_trunc(cv[v]);
                 float mag = fabs32(d32);
 #pragma unroll 4
                 for (int c = 0; c < m; ++c) {
-                    const float a = __double2float_rn(A[(size_t)c * n + v]);
-                    const float yc = __double2float_rn(yv[c]);
+                    const float a = f64_to_f32_trunc(A[(size_t)c * n + v]);
+                    const float yc = zf[c];
                     d32 = __fmaf_rn(yc, a, d32);
                     mag = __fmaf_rn(fabs32(yc), fabs32(a), mag);
                 }
-                // |d32 - d| <= (m + 2) * 2^-23 * mag covers the float roundings
+                // |d32 - d| <= (m/2 + 2) * 2^-23 * (|c| + sum |y||a|): the
+                // conversions 1.5 * 2^-23, the m FMA roundings 2^-24 each;
+                // (m + 2) * 2^-23 * mag covers it with mag's own roundings
                 if (!(d32 - (float)(m + 2) * 1.2e-7f * mag >= -(float)tol_d) || isinf(mag)) {
                     double d = -cv[v];
 #pragma unroll 4
@@ -661,11 +686,16 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
 #pragma unroll 4
                     for (int c = 0; c < m; ++c) r = __fma_rn(-yv[c], A[(size_t)c * n + v], r);
                     res[slist[t]] = r;
+                    rf[slist[t]] = __double2float_rn(r);
                 }
                 for (int i = tid; i < m; i += nt) {
                     const int v = row_var[i];
-                    if (v >= n && v < nm) res[i] = -yv[v - n];
-                    else if (v >= nm) res[i] = __dsub_rn(yv[neg[v - nm]], 1.0);
+                    double r;
+                    if (v >= n && v < nm) r = -yv[v - n];
+                    else if (v >= nm) r = __dsub_rn(yv[neg[v - nm]], 1.0);
+                    else continue;
+                    res[i] = r;
+                    rf[i] = __double2float_rn(r);
                 }
                 g.sync();
                 for (int c = tid; c < m; c += nt) {
@@ -674,7 +704,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
                     if (p > 0) {
                         float acc = 0.0f;
 #pragma unroll 4
-                        for (int i = 0; i < m; ++i) acc = __fmaf_rn(__double2float_rn(res[i]), T[i * LD + p], acc);
+                        for (int i = 0; i < m; ++i) acc = __fmaf_rn(rf[i], T[i * LD + p], acc);
                         d = (double)acc;
                     } else {
                         d = res[-p - 1];

@@ -67,7 +67,9 @@ def check_mixed(batch, max_fallback_frac=1.0, cert_mask=None):
 
 def test_mixed_dense50x50_phase1():
     batch = W.mixed_sign_dense(3000, 50, 50, start=777)
-    g, r = check_mixed(batch, max_fallback_frac=0.25)
+    # about 1.2% are re-solved in FP64 (ill-conditioned bases, phase-I
+    # degeneracy); a certificate that stopped converging would exceed 5%
+    g, r = check_mixed(batch, max_fallback_frac=0.05)
     assert set(np.unique(g["status"])) == {0, 1, 2}
 
 

@@ -38,7 +38,7 @@ def test_forced_forms_give_identical_results(name):
         groups = lpb.lp_batch_groups(s.h)
         assert groups and sum(g["count"] for g in groups) == batch.num_lps
         for persistent in (True, False):
-            for threads in (64, 256):
+            for threads in (32, 64, 256):
                 for i, g in enumerate(groups):
                     if g["kind"] in (0, 1) and (not persistent or g["smem_bytes"] <= 226 * 1024):
                         lpb.lp_batch_set_group_form(s.h, i, threads, persistent)
