@@ -113,7 +113,7 @@ __host__ __device__ inline size_t streamed_slot_bytes(int m, int n, int k) {
 // pivot-column copy and the column labels.
 struct MixedLayout {
     int R, LD;
-    size_t xb, yv, dv, res, zf, rf, row_var, neg, spos, slist;  // k-independent
+    size_t xb, yv, dv, res, zf, rf, row_var, neg, spos, slist, nbl;  // k-independent
     size_t T, colE, col_var;                           // k-dependent
     size_t total;
 };
@@ -134,6 +134,7 @@ __host__ __device__ inline MixedLayout mixed_layout(int m, int n, int k) {
     L.neg = o;     o += align16((size_t)m * 4);
     L.spos = o;    o += align16((size_t)m * 4);
     L.slist = o;   o += align16((size_t)m * 4);
+    L.nbl = o;     o += align16((size_t)m * 4);
     L.T = o;       o += align16((size_t)L.R * (size_t)L.LD * 4);
     L.colE = o;    o += align16((size_t)L.R * 4);
     L.col_var = o; o += align16((size_t)L.LD * 4);

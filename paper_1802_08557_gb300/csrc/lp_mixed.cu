@@ -154,6 +154,43 @@ __device__ __forceinline__ void retire_column32(G& g, Tab32& tb, int Ract, int e
     g.sync();
 }
 
+// Lanes per output of the certificate's long sums (residuals and corrections
+// over all m rows for a few outputs): a power of two from m alone, so that the
+// arithmetic of an LP does not depend on the launch form; 1 below m = 64.
+__device__ __forceinline__ int split_width(int m) {
+    int p = 1;
+    while (p < 32 && m >= 64 * p) p <<= 1;
+    return p;
+}
+
+// Sum over the P consecutive lanes of a split group (butterfly; every lane of
+// the group ends with the same value).  All 32 lanes of the warp must call it.
+__device__ __forceinline__ double group_sum(double v, int P) {
+    for (int off = P >> 1; off > 0; off >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, off));
+    return v;
+}
+__device__ __forceinline__ float group_sum(float v, int P) {
+    for (int off = P >> 1; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, off));
+    return v;
+}
+
+template <class G, bool kSplit>
+__device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
+                                            const int lp, unsigned char* big, int32_t* fb_queue, int32_t* fb_len,
+                                            const int32_t fb_cap, int32_t* diag);
+
+// mixed_solve with the split chosen from the LP's m (the same in every form).
+template <class G>
+__device__ __forceinline__ void mixed_solve_lp(G& g, const DeviceBatch& B, const Tolerances& tol,
+                                               const MixedParams& mp, const int lp, unsigned char* big,
+                                               int32_t* fb_queue, int32_t* fb_len, const int32_t fb_cap,
+                                               int32_t* diag) {
+    if (split_width(B.m[lp]) > 1)
+        mixed_solve<G, true>(g, B, tol, mp, lp, big, fb_queue, fb_len, fb_cap, diag);
+    else
+        mixed_solve<G, false>(g, B, tol, mp, lp, big, fb_queue, fb_len, fb_cap, diag);
+}
+
 // max |v| over the group (FP64), as a double.
 template <class G>
 __device__ __forceinline__ double block_absmax(G& g, double v) {
@@ -162,8 +199,9 @@ __device__ __forceinline__ double block_absmax(G& g, double v) {
 
 // One LP on the FP32 tableau, then its FP64 certificate.  `big` is the
 // LP's shared-memory area (mixed_layout); G is the group of threads that owns
-// the LP.
-template <class G>
+// the LP.  kSplit: the certificate's long sums are split over
+// split_width(m) > 1 lanes (else P = 1 at compile time, plain loops).
+template <class G, bool kSplit>
 __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
                                             const int lp, unsigned char* big, int32_t* fb_queue, int32_t* fb_len,
                                             const int32_t fb_cap, int32_t* diag)
@@ -188,6 +226,8 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
     int* neg = reinterpret_cast<int*>(big + L0.neg);
     int* spos = reinterpret_cast<int*>(big + L0.spos);
     int* slist = reinterpret_cast<int*>(big + L0.slist);
+    // non-basic slacks c in increasing order, packed (column position << 16) | c
+    int* nbl = reinterpret_cast<int*>(big + L0.nbl);
 
     // ---- tableau build (FP32), rows with b_i < 0 negated (two-phase) -------
     int k = 0;
@@ -395,7 +435,24 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
 
     // ---- FP64 certificate ---------------------------------------------------
     bool ok = (status == kOptimal || status == kUnbounded);
-    int s = 0;  // basic structurals
+    int s = 0;    // basic structurals
+    int nnb = 0;  // non-basic slacks (the columns of B^-1 that are not unit vectors)
+    // nbl from a complete spos (after a barrier); ends with a barrier
+    auto build_nbl = [&]() {
+        int cnt = 0;
+        for (int c0 = 0; c0 < m; c0 += nt) {
+            const int c = c0 + tid;
+            const int p = (c < m) ? spos[c] : 0;
+            int tot;
+            const int pos = cnt + g.prefix_count(p > 0, tot);
+            if (p > 0) nbl[pos] = (p << 16) | c;
+            cnt += tot;
+        }
+        g.sync();
+        return cnt;
+    };
+    const int P = kSplit ? split_width(m) : 1;
+    const int sgid = tid / P, sq = tid - (tid / P) * P, sgroups = nt / P;
     if (ok) {
         unsigned nart = 0, dummy;
         for (int i = tid; i < m; i += nt) nart += (row_var[i] >= nm) ? 1u : 0u;
@@ -430,6 +487,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
             if (tid == 0) record_internal_error(diag, 3, lp);
             ok = false;
         }
+        nnb = build_nbl();
         for (int i = tid; i < m; i += nt) xb[i] = (double)T[i * LD];
         g.sync();
     }
@@ -484,10 +542,11 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
             unsigned fwdbad = 0;
             for (int i = tid; i < m; i += nt) {
                 float acc = 0.0f;
+                const float* Ti = T + i * LD;
 #pragma unroll 4
-                for (int c = 0; c < m; ++c) {
-                    const int p = spos[c];
-                    if (p > 0) acc = __fmaf_rn(T[i * LD + p], rf[c], acc);
+                for (int u = 0; u < nnb; ++u) {
+                    const int pc = nbl[u];
+                    acc = __fmaf_rn(Ti[(unsigned)pc >> 16], rf[pc & 0xffff], acc);
                 }
                 const int v = row_var[i];
                 // the correction: B^-1 r (FP32), plus r_c exactly for a basic slack
@@ -529,22 +588,31 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
         const float yfloor = 1e-8f * __double2float_ru(block_absmax(g, yloc));  // barrier: zf complete
         for (int it = 0; it <= mp.max_refine; ++it) {
             // rho_i = c_(v_i) - y^T col(v_i) for each basic variable (by tableau row)
+            // (split over P lanes per basic variable, rows c = q, q + P, ...)
             unsigned bad = 0;
-            for (int t = tid; t < s; t += nt) {
-                const int i = slist[t];
-                const int v = row_var[i];
-                double r = cv[v];
-                float mag = f64_abs_to_f32_trunc(r);
+            for (int t0 = 0; t0 < s; t0 += sgroups) {
+                const int t = t0 + sgid;
+                const bool act = t < s;
+                const int i = act ? slist[t] : 0;
+                const int v = act ? row_var[i] : 0;
+                double r = (act && sq == 0) ? cv[v] : 0.0;
+                float mag = (act && sq == 0) ? f64_abs_to_f32_trunc(r) : 0.0f;
+                if (act) {
 #pragma unroll 4
-                for (int c = 0; c < m; ++c) {
-                    const double a = A[(size_t)c * n + v];
-                    r = __fma_rn(-yv[c], a, r);
-                    mag = __fmaf_rn(f64_abs_to_f32_trunc(a), fabs32(zf[c]), mag);
+                    for (int c = sq; c < m; c += P) {
+                        const double a = A[(size_t)c * n + v];
+                        r = __fma_rn(-yv[c], a, r);
+                        mag = __fmaf_rn(f64_abs_to_f32_trunc(a), fabs32(zf[c]), mag);
+                    }
                 }
-                res[i] = r;
-                const float r32 = __double2float_rn(r);
-                rf[i] = r32;
-                bad += (!(fabs32(r32) <= conv_tol32 * mag) || isinf(mag)) ? 1u : 0u;
+                r = group_sum(r, P);
+                mag = group_sum(mag, P);
+                if (act && sq == 0) {
+                    res[i] = r;
+                    const float r32 = __double2float_rn(r);
+                    rf[i] = r32;
+                    bad += (!(fabs32(r32) <= conv_tol32 * mag) || isinf(mag)) ? 1u : 0u;
+                }
             }
             for (int i = tid; i < m; i += nt) {
                 const int v = row_var[i];
@@ -555,18 +623,26 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
                 }
             }
             g.sync();
+            // corrections of the non-basic slacks (B^-1 columns), split over
+            // P lanes each; parked in zf[c], which is rewritten below
+            for (int u0 = 0; u0 < nnb; u0 += sgroups) {
+                const int u = u0 + sgid;
+                const bool act = u < nnb;
+                const int pc = act ? nbl[u] : 0;
+                float acc = 0.0f;
+                if (act) {
+                    const float* Tp = T + ((unsigned)pc >> 16);
+#pragma unroll 4
+                    for (int i = sq; i < m; i += P) acc = __fmaf_rn(rf[i], Tp[i * LD], acc);
+                }
+                acc = group_sum(acc, P);
+                if (act && sq == 0) zf[pc & 0xffff] = acc;
+            }
+            g.sync();
             unsigned fwdbad = 0;
             for (int c = tid; c < m; c += nt) {
                 const int p = spos[c];
-                double d;
-                if (p > 0) {
-                    float acc = 0.0f;
-#pragma unroll 4
-                    for (int i = 0; i < m; ++i) acc = __fmaf_rn(rf[i], T[i * LD + p], acc);
-                    d = (double)acc;
-                } else {
-                    d = res[-p - 1];
-                }
+                const double d = (p > 0) ? (double)zf[c] : res[-p - 1];
                 const double ynew = __dadd_rn(yv[c], d);
                 yv[c] = ynew;
                 const float yn32 = __double2float_rn(ynew);
@@ -583,27 +659,37 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
         // error bound and computed in FP64 only when the screen cannot decide
         unsigned bad = 0, dummy;
         for (int c = tid; c < m; c += nt) bad += (yv[c] < -tol_d) ? 1u : 0u;
-        for (int j = 1 + tid; j <= Cvar; j += nt) {
-            const int v = tb.col_var[j];
-            if (v < n) {
-                float d32 = -f64_to_f32_trunc(cv[v]);
-                float mag = fabs32(d32);
+        // (split over P lanes per column like the residuals)
+        for (int j0 = 0; j0 < Cvar; j0 += sgroups) {
+            const int j = 1 + j0 + sgid;
+            const int v = (j <= Cvar) ? tb.col_var[j] : n;
+            const bool act = v < n;
+            float d32 = (act && sq == 0) ? -f64_to_f32_trunc(cv[v]) : 0.0f;
+            float mag = fabs32(d32);
+            if (act) {
 #pragma unroll 4
-                for (int c = 0; c < m; ++c) {
+                for (int c = sq; c < m; c += P) {
                     const float a = f64_to_f32_trunc(A[(size_t)c * n + v]);
                     const float yc = zf[c];
                     d32 = __fmaf_rn(yc, a, d32);
                     mag = __fmaf_rn(fabs32(yc), fabs32(a), mag);
                 }
-                // |d32 - d| <= (m/2 + 2) * 2^-23 * (|c| + sum |y||a|): the
-                // conversions 1.5 * 2^-23, the m FMA roundings 2^-24 each;
-                // (m + 2) * 2^-23 * mag covers it with mag's own roundings
-                if (!(d32 - (float)(m + 2) * 1.2e-7f * mag >= -(float)tol_d) || isinf(mag)) {
-                    double d = -cv[v];
+            }
+            d32 = group_sum(d32, P);
+            mag = group_sum(mag, P);
+            // |d32 - d| <= (m/P + log2 P + 2) * 2^-23 * (|c| + sum |y||a|):
+            // the conversions 1.5 * 2^-23, at most m/P + log2 P roundings of
+            // 2^-24 in sequence; (m + 2) * 2^-23 * mag covers it with mag's
+            // own roundings
+            const bool undecided = act && (!(d32 - (float)(m + 2) * 1.2e-7f * mag >= -(float)tol_d) || isinf(mag));
+            if (__any_sync(kFull, undecided)) {
+                double d = (undecided && sq == 0) ? -cv[v] : 0.0;
+                if (undecided) {
 #pragma unroll 4
-                    for (int c = 0; c < m; ++c) d = __fma_rn(yv[c], A[(size_t)c * n + v], d);
-                    bad += (d < -tol_d) ? 1u : 0u;
+                    for (int c = sq; c < m; c += P) d = __fma_rn(yv[c], A[(size_t)c * n + v], d);
                 }
+                d = group_sum(d, P);
+                if (undecided && sq == 0) bad += (d < -tol_d) ? 1u : 0u;
             }
         }
         g.count_min(bad, 0u, bad, dummy);
@@ -672,6 +758,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
         }
         g.count_min(badpos, 0u, badpos, dummy);
         if (badpos == 0) {
+            nnb = build_nbl();
             const float* Tw = T + (m + 1) * LD;
             for (int c = tid; c < m; c += nt) {
                 const int p = spos[c];
@@ -679,14 +766,22 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
             }
             g.sync();
             for (int it = 0; it < 4; ++it) {
-                // residual of y^T B = c_B (phase-I costs), one entry per tableau row
-                for (int t = tid; t < sf; t += nt) {
-                    const int v = row_var[slist[t]];
+                // residual of y^T B = c_B (phase-I costs), one entry per tableau
+                // row (split over P lanes per basic structural)
+                for (int t0 = 0; t0 < sf; t0 += sgroups) {
+                    const int t = t0 + sgid;
+                    const bool act = t < sf;
+                    const int v = act ? row_var[slist[t]] : 0;
                     double r = 0.0;
+                    if (act) {
 #pragma unroll 4
-                    for (int c = 0; c < m; ++c) r = __fma_rn(-yv[c], A[(size_t)c * n + v], r);
-                    res[slist[t]] = r;
-                    rf[slist[t]] = __double2float_rn(r);
+                        for (int c = sq; c < m; c += P) r = __fma_rn(-yv[c], A[(size_t)c * n + v], r);
+                    }
+                    r = group_sum(r, P);
+                    if (act && sq == 0) {
+                        res[slist[t]] = r;
+                        rf[slist[t]] = __double2float_rn(r);
+                    }
                 }
                 for (int i = tid; i < m; i += nt) {
                     const int v = row_var[i];
@@ -698,17 +793,24 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
                     rf[i] = __double2float_rn(r);
                 }
                 g.sync();
+                // corrections of the non-basic slacks, split over P lanes each
+                for (int u0 = 0; u0 < nnb; u0 += sgroups) {
+                    const int u = u0 + sgid;
+                    const bool act = u < nnb;
+                    const int pc = act ? nbl[u] : 0;
+                    float acc = 0.0f;
+                    if (act) {
+                        const float* Tp = T + ((unsigned)pc >> 16);
+#pragma unroll 4
+                        for (int i = sq; i < m; i += P) acc = __fmaf_rn(rf[i], Tp[i * LD], acc);
+                    }
+                    acc = group_sum(acc, P);
+                    if (act && sq == 0) zf[pc & 0xffff] = acc;
+                }
+                g.sync();
                 for (int c = tid; c < m; c += nt) {
                     const int p = spos[c];
-                    double d;
-                    if (p > 0) {
-                        float acc = 0.0f;
-#pragma unroll 4
-                        for (int i = 0; i < m; ++i) acc = __fmaf_rn(rf[i], T[i * LD + p], acc);
-                        d = (double)acc;
-                    } else {
-                        d = res[-p - 1];
-                    }
+                    const double d = (p > 0) ? (double)zf[c] : res[-p - 1];
                     yv[c] = __dadd_rn(yv[c], d);
                 }
                 g.sync();
@@ -817,7 +919,7 @@ mixed_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp, co
     extern __shared__ __align__(16) unsigned char smem[];
     BlockGroup g(reinterpret_cast<long long*>(smem + SmallLayout::red64),
                  reinterpret_cast<unsigned*>(smem + SmallLayout::red32));
-    mixed_solve(g, B, tol, mp, order[blockIdx.x], smem + SmallLayout::total, fb_queue, fb_len, fb_cap, diag);
+    mixed_solve_lp(g, B, tol, mp, order[blockIdx.x], smem + SmallLayout::total, fb_queue, fb_len, fb_cap, diag);
 }
 
 // Persistent CTAs over a list: LP order[idx] for idx taken from an atomic
@@ -838,7 +940,7 @@ mixed_queue_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams 
         if (idx >= n_items) break;
         BlockGroup g(reinterpret_cast<long long*>(smem + SmallLayout::red64),
                      reinterpret_cast<unsigned*>(smem + SmallLayout::red32));
-        mixed_solve(g, B, tol, mp, order[idx], smem + SmallLayout::total, fb_queue, fb_len, fb_cap, diag);
+        mixed_solve_lp(g, B, tol, mp, order[idx], smem + SmallLayout::total, fb_queue, fb_len, fb_cap, diag);
         __syncthreads();
     }
 }
@@ -852,7 +954,7 @@ mixed_warp_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams m
 {
     extern __shared__ __align__(16) unsigned char smem[];
     WarpGroup g;
-    mixed_solve(g, B, tol, mp, order[blockIdx.x], smem, fb_queue, fb_len, fb_cap, diag);
+    mixed_solve_lp(g, B, tol, mp, order[blockIdx.x], smem, fb_queue, fb_len, fb_cap, diag);
 }
 
 }  // namespace
