@@ -38,9 +38,10 @@ __device__ __forceinline__ long long pack_key(int hi, unsigned lo) {
 }
 
 // Rows per batch of the pivot update (all loads of a batch issued before its
-// stores).  Measured on 50x50 LPs: deeper batches, deeper unrolling of the
-// loops that read A, or a larger register budget for the one-warp kernel
-// were all slower (larger code, same latency-bound issue rate).
+// stores).  Measured on 50x50 LPs: deeper batches, two quads per thread and
+// step, deeper unrolling of the loops that read A, or a larger register budget
+// for the one-warp kernel were all slower (larger code or spills, same
+// latency-bound issue rate).
 constexpr int kPivotBatch = 4;
 
 struct Tab32 {
@@ -229,6 +230,14 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
     // non-basic slacks c in increasing order, packed (column position << 16) | c
     int* nbl = reinterpret_cast<int*>(big + L0.nbl);
 
+    {
+        // every 128-byte line of this LP's A requested into L2 at once, so the
+        // build's loads below find it there instead of each waiting on HBM
+        const char* a0 = reinterpret_cast<const char*>(A);
+        const size_t bytes = (size_t)m * (size_t)n * 8;
+        for (size_t off = (size_t)tid * 128; off < bytes; off += (size_t)nt * 128)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a0 + off));
+    }
     // ---- tableau build (FP32), rows with b_i < 0 negated (two-phase) -------
     int k = 0;
     for (int i0 = 0; i0 < m; i0 += nt) {
