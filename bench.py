@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-hyperbox", action="store_true", help="skip the hyperbox LP (Eq. 7) measurement")
     p.add_argument("--no-warm", action="store_true", help="skip the learned warm-start measurement")
     p.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch measurement")
+    p.add_argument("--no-support", action="store_true", help="skip the support-function measurement")
+    p.add_argument("--support-dirs", type=int, default=100_000, help="directions of the support-function measurement")
     p.add_argument("--uneven-lps", type=int, default=20_000, help="LPs of the uneven-batch measurement")
     p.add_argument("--warm-train", type=int, default=1_000_000, help="self-solved LPs the network is trained on")
     p.add_argument("--warm-test", type=int, default=100_000, help="test LPs of the warm-start measurement")
@@ -360,24 +362,49 @@ def run_ours(args):
         }
         del dL, dlo, dhi, dobj
 
+    def ev_time(fn):
+        """Mean ms of K calls of fn between CUDA events on the solve's stream (after W warm-ups)."""
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        a0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(a0.elapsed_time(a1)) / args.steps
+
+    # ---- support function of one polytope: 40 halfspaces in R^10, 1e5 directions
+    support = None
+    if not args.no_support:
+        sb = W.support_function(args.support_dirs, start=rank * args.support_dirs)
+        support = {"workload": f"support40x10_dirs{sb.num_lps}", "unit": "LPs/s"}
+        res_s = {}
+        for label, prec in (("fp64", lpb.LP_PREC_FP64), ("fp32r", lpb.LP_PREC_FP32_REFINE)):
+            hs = lpb.BatchSolver(sb, opts=lpb.lpb_default_opts(precision=prec), stream=stream)
+            ms = ev_time(lambda: lpb.lp_batch_solve(hs.h, stream))
+            res_s[label] = hs.results()
+            info_s = hs.plan_info()
+            hs.close()
+            support[label] = {"value": sb.num_lps * ws / (ms * 1e-3), "ms_per_step": ms,
+                              "fp64_fallback_lps": int(info_s["num_fallback"]) if prec != lpb.LP_PREC_FP64 else 0}
+        r64s, r32s = res_s["fp64"], res_s["fp32r"]
+        opt = r64s["status"] == 0
+        rel = np.abs(r32s["obj"][opt] - r64s["obj"][opt]) / np.maximum(1.0, np.abs(r64s["obj"][opt]))
+        support["value"] = support["fp32r"]["value"]
+        support["speedup_over_fp64"] = support["fp32r"]["value"] / support["fp64"]["value"]
+        support["status_mismatches"] = int(np.sum(r32s["status"] != r64s["status"]))
+        support["max_rel_obj_err_on_optimal"] = float(rel.max()) if rel.size else 0.0
+        support["timing"] = "CUDA events on the solve's stream around K whole solves"
+        del sb, res_s
+
     # ---- uneven batch: m, n log-uniform in [10, 500], 2e4 LPs ----------------
     uneven = None
     if not args.no_uneven:
         ub = W.uneven_dense(args.uneven_lps, start=rank * args.uneven_lps)
         um, un = ub.m.astype(np.float64), ub.n.astype(np.float64)
-
-        def ev_time(fn):
-            for _ in range(max(3, args.warmup)):
-                fn()
-            torch.cuda.synchronize()
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            barrier()
-            a0.record(stream)
-            for _ in range(args.steps):
-                fn()
-            a1.record(stream)
-            torch.cuda.synchronize()
-            return max_over_ranks(a0.elapsed_time(a1)) / args.steps
 
         uneven = {"workload": f"uneven10to500_{ub.num_lps}", "unit": "LPs/s"}
         for label, prec in (("fp64", lpb.LP_PREC_FP64), ("fp32r", lpb.LP_PREC_FP32_REFINE)):
@@ -396,7 +423,7 @@ def run_ours(args):
                 "value": ub.num_lps * ws / (best * 1e-3), "ms_default_plan": ms_default, "ms_autotuned": ms_tuned,
                 "ms_graph": ms_graph, "groups": len(groups),
                 "persistent_groups": sum(1 for g in groups if g["persistent"] and g["kind"] != 2),
-                "streamed_lps": sum(g["count"] for g in groups if g["kind"] == 2),
+                "streamed_lps": sum(g["count"] for g in groups if g["kind"] in (2, 4)),
                 "results_unchanged_by_tuning": bool(all(np.array_equal(ru[k], rt[k]) for k in ("status", "obj", "x"))),
                 "achieved_gflops": fl / (best * 1e-3) / 1e9, "fp64_peak_gflops": FP64_PEAK_GFLOPS,
             }
@@ -535,6 +562,7 @@ def run_ours(args):
             "fp64_plain": fp64,
             "hyperbox": hyperbox,
             "warm_start": warm,
+            "support_function": support,
             "uneven": uneven,
             "clocks": clocks,
             "gpu_launches": args.steps * launches,

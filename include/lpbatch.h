@@ -90,7 +90,11 @@ typedef struct {
  * CTA; else split by rows over the shared memory of a thread-block cluster of
  * 2-16 CTAs (the smallest that holds it; all CTAs take the same decisions, so
  * the results are those of the one-CTA kernel); else a global workspace.
- * STREAMED: global workspace for every LP. */
+ * With LP_PREC_FP32_REFINE the FP32 tableau is in one CTA's shared memory when
+ * it fits, else in a global workspace (no cluster form); the FP64 re-solve of
+ * an uncertified LP runs in one CTA when its FP64 tableau fits, else streamed.
+ * STREAMED: global workspace for every LP (FP32_REFINE: the FP32 tableau of
+ * every LP; results are bit-identical to AUTO's). */
 enum { LPB_SCHED_AUTO = 0, LPB_SCHED_STREAMED = 1 };
 
 typedef struct lp_batch lp_batch;   /* opaque; owned by the library */
@@ -163,7 +167,7 @@ lpb_err lp_batch_results(lp_batch *h, int32_t *status, int32_t *iters, double *o
 typedef struct {
     int32_t num_groups;        /* kernel launches per solve                         */
     int32_t num_resident;      /* LPs whose tableau stays in one CTA's shared memory */
-    int32_t num_streamed;      /* LPs whose tableau lives in a global workspace      */
+    int32_t num_streamed;      /* LPs whose tableau lives in a global workspace (FP64 or FP32) */
     int32_t num_phase1;        /* LPs with some b_i < 0                              */
     int32_t num_mixed;         /* LPs on the FP32 tableau + FP64 certificate path    */
     int32_t num_fallback;      /* of those, re-solved in FP64 by the last solve      */
@@ -179,7 +183,8 @@ typedef struct {
     int32_t num_cluster;       /* LPs solved on a thread-block cluster (tableau split
                                   over the CTAs' shared memory)                   */
     int64_t max_smem_bytes;    /* largest shared-memory footprint of a launch        */
-    int64_t workspace_bytes;   /* global workspace of the streamed LPs               */
+    int64_t workspace_bytes;   /* global workspace of the streamed LPs (and of the
+                                  streamed FP64 re-solve of large mixed LPs)      */
 } lp_batch_plan;
 
 /* Report the launch plan made by lp_batch_create (and, for num_fallback, the
@@ -205,10 +210,11 @@ lpb_err lp_batch_solve_graph(lp_batch *h, void *stream);
 lpb_err lp_batch_autotune(lp_batch *h, int32_t rounds, void *stream);
 
 /* One launch group of the plan: index 0 .. lp_batch_plan.num_groups-1 (the
- * FP64 re-solve queue of the mixed path is not listed). */
+ * FP64 re-solve launches of the mixed path are not listed). */
 typedef struct {
     int32_t kind;        /* 0 mixed precision, 1 FP64 shared-memory resident, 2 FP64 streamed,
-                            3 FP64 on a thread-block cluster                  */
+                            3 FP64 on a thread-block cluster, 4 mixed precision
+                            with the FP32 tableau in a global workspace       */
     int32_t count;       /* LPs in the group                                  */
     int32_t threads;     /* threads per CTA                                   */
     int32_t persistent;  /* 1: persistent CTAs over a work queue              */

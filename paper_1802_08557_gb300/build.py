@@ -33,6 +33,7 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcom
 PER_FILE = {
     "lp_fp64_simplex.cu": ["--fmad=false", "-Xptxas", "-dlcm=cg"],
     "lp_cluster.cu": ["--fmad=false"],
+    "lp_mixed_streamed.cu": ["-Xptxas", "-dlcm=cg"],
 }
 
 

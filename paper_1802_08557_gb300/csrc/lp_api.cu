@@ -174,6 +174,23 @@ struct lp_batch {
     cudaEvent_t ev_join[kLanes] = {};
     int fb_threads = 0, fb_ctas = 0;
     size_t fb_smem = 0;
+    int32_t num_fsmall = 0;  // mixed LPs whose FP64 re-solve fits one CTA (fb_queue's capacity)
+    // mixed precision with the FP32 tableau in a global workspace slot
+    int64_t mstream_offset = 0;
+    int32_t num_mstream = 0;
+    int32_t mstream_slots = 0;
+    size_t mslot_bytes = 0;
+    unsigned char* mworkspace = nullptr;
+    int32_t* mcounter = nullptr;
+    // FP64 streamed re-solve of uncertified mixed LPs whose FP64 tableau
+    // exceeds one CTA
+    int32_t num_fbig = 0;
+    int32_t* fbig_queue = nullptr;
+    int32_t* fbig_len = nullptr;
+    int32_t* fbig_counter = nullptr;
+    int32_t fbig_slots = 0;
+    size_t fbig_slot_bytes = 0;
+    unsigned char* fbig_workspace = nullptr;
     // optional stage timing: event triples (start, groups joined, re-solve
     // done) for the last kTimingRing solves
     std::vector<cudaEvent_t> tev;
@@ -240,6 +257,10 @@ void release(lp_batch* h, cudaStream_t s) {
     h->cap_stream = nullptr;
 }
 
+lpb::FallbackQueues fallback_queues(const lp_batch* h) {
+    return lpb::FallbackQueues{h->fb_queue, h->fb_len, h->num_fsmall, h->fbig_queue, h->fbig_len, h->num_fbig};
+}
+
 // One launch group on stream ls: kind 0 mixed precision, 1 FP64 resident;
 // one CTA per LP, or persistent CTAs over the group's work queue.
 cudaError_t launch_group(lp_batch* h, int kind, const Group& g, cudaStream_t ls) {
@@ -247,9 +268,9 @@ cudaError_t launch_group(lp_batch* h, int kind, const Group& g, cudaStream_t ls)
     if (kind == 0) {
         if (g.persistent)
             return lpb::launch_mixed_queue(h->d, h->tol, h->mp, order, h->group_len + g.gi, h->group_counter + g.gi,
-                                           g.ctas, g.threads, g.smem, h->fb_queue, h->fb_len, h->num_mixed, h->diag, ls);
+                                           g.ctas, g.threads, g.smem, fallback_queues(h), h->diag, ls);
         return lpb::launch_mixed(h->d, h->tol, h->mp, order, g.count, g.threads, g.threads == 32 ? g.smem_warp : g.smem,
-                                 h->fb_queue, h->fb_len, h->num_mixed, h->diag, ls);
+                                 fallback_queues(h), h->diag, ls);
     }
     if (g.persistent)
         return lpb::launch_fp64_resident_queue(h->d, h->tol, order, h->group_len + g.gi, g.count, h->num_lps,
@@ -263,13 +284,16 @@ cudaError_t launch_group(lp_batch* h, int kind, const Group& g, cudaStream_t ls)
 lpb_err enqueue_solve(lp_batch* h, cudaStream_t s, bool timing) {
     cudaError_t err = cudaMemsetAsync(h->diag, 0, 8 * sizeof(int32_t), s);
     if (err != cudaSuccess) return cuda_fail(err, "diagnostic reset");
-    if (h->num_mixed > 0 && (err = cudaMemsetAsync(h->fb_len, 0, sizeof(int32_t), s)))
+    if (h->num_mixed > 0 && ((err = cudaMemsetAsync(h->fb_len, 0, sizeof(int32_t), s)) ||
+                             (err = cudaMemsetAsync(h->fbig_len, 0, sizeof(int32_t), s))))
         return cuda_fail(err, "fallback queue reset");
-    struct Job { int kind; const Group* g; int64_t count; };  // kind 0 mixed, 1 resident, 2 streamed
+    // kind 0 mixed, 1 resident, 2 streamed, 3 cluster, 4 mixed streamed
+    struct Job { int kind; const Group* g; int64_t count; };
     std::vector<Job> jobs;
     for (const Group& g : h->mixed_groups) jobs.push_back({0, &g, g.count});
     for (const Group& g : h->groups) jobs.push_back({1, &g, g.count});
     if (h->num_streamed > 0) jobs.push_back({2, nullptr, h->num_streamed});
+    if (h->num_mstream > 0) jobs.push_back({4, nullptr, h->num_mstream});
     for (size_t ci = 0; ci < h->cluster_groups.size(); ++ci)
         jobs.push_back({3, reinterpret_cast<const Group*>(ci), h->cluster_groups[ci].count});
     std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& b) { return a.count > b.count; });
@@ -288,6 +312,10 @@ lpb_err enqueue_solve(lp_batch* h, cudaStream_t s, bool timing) {
         if (j.kind == 2) {
             err = lpb::launch_fp64_streamed(h->d, h->tol, h->d_order + h->streamed_offset, h->num_streamed,
                                             h->streamed_slots, h->workspace, h->slot_bytes, h->counter, h->diag, ls);
+        } else if (j.kind == 4) {
+            err = lpb::launch_mixed_streamed(h->d, h->tol, h->mp, h->d_order + h->mstream_offset, h->num_mstream,
+                                             h->mstream_slots, h->mworkspace, h->mslot_bytes, h->mcounter,
+                                             fallback_queues(h), h->diag, ls);
         } else if (j.kind == 3) {
             const lp_batch::ClusterGroup& cg = h->cluster_groups[reinterpret_cast<size_t>(j.g)];
             err = lpb::launch_fp64_cluster(h->d, h->tol, h->d_order + cg.offset, cg.count, cg.C, cg.clusters, cg.smem,
@@ -304,9 +332,14 @@ lpb_err enqueue_solve(lp_batch* h, cudaStream_t s, bool timing) {
             return cuda_fail(err, "join");
     }
     if (tev && (err = cudaEventRecord(tev[1], s))) return cuda_fail(err, "timing");
-    if (h->num_mixed > 0) {
-        err = lpb::launch_fp64_resident_queue(h->d, h->tol, h->fb_queue, h->fb_len, h->num_mixed, h->num_lps,
+    if (h->num_fsmall > 0) {
+        err = lpb::launch_fp64_resident_queue(h->d, h->tol, h->fb_queue, h->fb_len, h->num_fsmall, h->num_lps,
                                               h->fb_counter, h->diag, h->fb_ctas, h->fb_threads, h->fb_smem, s);
+        if (err != cudaSuccess) return cuda_fail(err, "fallback launch");
+    }
+    if (h->num_fbig > 0) {
+        err = lpb::launch_fp64_streamed(h->d, h->tol, h->fbig_queue, h->num_fbig, h->fbig_slots, h->fbig_workspace,
+                                        h->fbig_slot_bytes, h->fbig_counter, h->diag, s, h->fbig_len);
         if (err != cudaSuccess) return cuda_fail(err, "fallback launch");
     }
     if (tev) {
@@ -466,6 +499,7 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     std::map<std::pair<int, size_t>, std::vector<int32_t>> buckets, mixed_buckets;
     std::vector<int32_t> streamed;
     std::map<int, std::vector<int32_t>> cluster_buckets;  // cluster size -> LPs
+    std::vector<int32_t> mstream;                         // mixed precision, tableau in global memory
     const size_t queue_smem_cap = lpb::kMaxSmemPerBlock - 1024;
     h->uniform_m = hm[0];
     h->uniform_n = hn[0];
@@ -475,13 +509,28 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         if (hm[k] != h->uniform_m || hn[k] != h->uniform_n) h->uniform_m = h->uniform_n = -1;
         h->cold_smem = std::max(h->cold_smem, need);
         h->cold_threads = std::max(h->cold_threads, pick_threads(hm[k], hn[k], hk[k], 0));
-        if (o.precision == LP_PREC_FP32_REFINE && o.schedule == LPB_SCHED_AUTO && need <= queue_smem_cap) {
-            // FP32 tableau + FP64 certificate; the FP64 fallback runs resident.
-            const int threads = mixed_threads(hm[k], hn[k], hk[k], o.block_threads);
-            const size_t msmem = (lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]) + 1023) / 1024 * 1024;
-            mixed_buckets[{threads, msmem}].push_back(k);
-            h->fb_smem = std::max(h->fb_smem, need);
-            h->fb_threads = std::max(h->fb_threads, pick_threads(hm[k], hn[k], hk[k], 0));  // FP64 kernel's own choice
+        if (o.precision == LP_PREC_FP32_REFINE) {
+            // FP32 tableau + FP64 certificate: in shared memory when the FP32
+            // tableau fits one CTA (AUTO), else in a global workspace slot.
+            // The FP64 re-solve of an uncertified LP runs in one CTA when its
+            // FP64 tableau fits, else streamed.
+            if (need <= queue_smem_cap) {
+                ++h->num_fsmall;
+                h->fb_smem = std::max(h->fb_smem, need);
+                h->fb_threads = std::max(h->fb_threads, pick_threads(hm[k], hn[k], hk[k], 0));  // FP64 kernel's own
+            } else {
+                ++h->num_fbig;
+                h->fbig_slot_bytes = std::max(h->fbig_slot_bytes, lpb::streamed_slot_bytes(hm[k], hn[k], hk[k]));
+            }
+            const size_t mneed = lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]);
+            if (o.schedule == LPB_SCHED_AUTO && mneed <= queue_smem_cap) {
+                const int threads = mixed_threads(hm[k], hn[k], hk[k], o.block_threads);
+                mixed_buckets[{threads, (mneed + 1023) / 1024 * 1024}].push_back(k);
+            } else {
+                mstream.push_back(k);
+                h->mslot_bytes = std::max(h->mslot_bytes, (lpb::mixed_layout(hm[k], hn[k], hk[k]).total + 255) &
+                                                              ~size_t(255));
+            }
             continue;
         }
         if (need > lpb::kMaxSmemPerBlock && o.schedule == LPB_SCHED_AUTO) {
@@ -582,6 +631,22 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     if (!h->cluster_groups.empty() &&
         (err = alloc(h, &h->cluster_counter, h->cluster_groups.size(), s)))
         return bail_cuda(err, "cluster counters");
+    lpt(mstream);
+    h->mstream_offset = (int64_t)order.size();
+    h->num_mstream = (int32_t)mstream.size();
+    h->num_mixed += h->num_mstream;
+    order.insert(order.end(), mstream.begin(), mstream.end());
+    if (h->num_mstream > 0) {
+        int sms = 0;
+        if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device)))
+            return bail_cuda(err, "device query");
+        int64_t slots = (int64_t)sms * lpb::mixed_streamed_ctas_per_sm();
+        const int64_t cap = std::max<int64_t>(1, kMaxWorkspaceBytes / (int64_t)h->mslot_bytes);
+        slots = std::min<int64_t>({slots, (int64_t)h->num_mstream, cap});
+        h->mstream_slots = (int32_t)slots;
+        if ((err = alloc(h, &h->mworkspace, (size_t)slots * h->mslot_bytes, s)) || (err = alloc(h, &h->mcounter, 1, s)))
+            return bail_cuda(err, "mixed streamed workspace allocation");
+    }
     lpt(streamed);
     h->streamed_offset = (int64_t)order.size();
     h->num_streamed = (int32_t)streamed.size();
@@ -606,14 +671,24 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         h->mp.fwd_tol = 1e-12;
         h->mp.max_refine = 6;
         h->fb_smem = (h->fb_smem + 1023) / 1024 * 1024;
-        if ((err = alloc(h, &h->fb_queue, (size_t)h->num_mixed, s)) || (err = alloc(h, &h->fb_len, 1, s)) ||
-            (err = alloc(h, &h->fb_counter, 1, s)) || (err = cudaMemsetAsync(h->fb_len, 0, 4, s)))
+        if ((err = alloc(h, &h->fb_queue, (size_t)h->num_fsmall, s)) || (err = alloc(h, &h->fb_len, 1, s)) ||
+            (err = alloc(h, &h->fb_counter, 1, s)) || (err = cudaMemsetAsync(h->fb_len, 0, 4, s)) ||
+            (err = alloc(h, &h->fbig_queue, (size_t)h->num_fbig, s)) || (err = alloc(h, &h->fbig_len, 1, s)) ||
+            (err = alloc(h, &h->fbig_counter, 1, s)) || (err = cudaMemsetAsync(h->fbig_len, 0, 4, s)))
             return bail_cuda(err, "fallback queue allocation");
         int sms = 0;
         if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device)) ||
             (err = lpb::fp64_kernels_prepare()) || (err = lpb::mixed_kernel_prepare()))
             return bail_cuda(err, "device query");
-        h->fb_ctas = sms * lpb::fp64_resident_queue_ctas_per_sm(h->fb_threads, h->fb_smem);
+        if (h->num_fsmall > 0)
+            h->fb_ctas = sms * lpb::fp64_resident_queue_ctas_per_sm(h->fb_threads, h->fb_smem);
+        if (h->num_fbig > 0) {
+            // one slot per SM: re-solves are few, and each slot holds an FP64 tableau
+            const int64_t cap = std::max<int64_t>(1, kMaxWorkspaceBytes / (int64_t)h->fbig_slot_bytes);
+            h->fbig_slots = (int32_t)std::min<int64_t>({(int64_t)sms, (int64_t)h->num_fbig, cap});
+            if ((err = alloc(h, &h->fbig_workspace, (size_t)h->fbig_slots * h->fbig_slot_bytes, s)))
+                return bail_cuda(err, "fallback workspace allocation");
+        }
     }
     if ((err = alloc(h, &h->diag, 8, s)) || (err = cudaMemsetAsync(h->diag, 0, 32, s)))
         return bail_cuda(err, "diagnostic word allocation");
@@ -686,7 +761,8 @@ lpb_err lp_batch_autotune(lp_batch* h, int32_t rounds, void* stream) {
         for (int r = 0; r < rounds; ++r) {
             cudaError_t e;
             if ((e = cudaMemsetAsync(h->diag, 0, 32, s))) return e;
-            if (kind == 0 && (e = cudaMemsetAsync(h->fb_len, 0, 4, s))) return e;
+            if (kind == 0 && ((e = cudaMemsetAsync(h->fb_len, 0, 4, s)) || (e = cudaMemsetAsync(h->fbig_len, 0, 4, s))))
+                return e;
             if ((e = cudaEventRecord(e0, s)) || (e = launch_group(h, kind, g, s)) || (e = cudaEventRecord(e1, s)) ||
                 (e = cudaEventSynchronize(e1)))
                 return e;
@@ -772,7 +848,8 @@ lpb_err lp_batch_group_info(lp_batch* h, int32_t index, lp_batch_group* out) {
     if (!h || !out) return fail(LPB_EINVAL, "handle or out is NULL");
     const int32_t nr = (int32_t)h->groups.size(), nm = (int32_t)h->mixed_groups.size();
     const int32_t nc = (int32_t)h->cluster_groups.size();
-    const int32_t total = nr + nm + nc + (h->num_streamed > 0 ? 1 : 0);
+    const int32_t ns = h->num_streamed > 0 ? 1 : 0;
+    const int32_t total = nr + nm + nc + ns + (h->num_mstream > 0 ? 1 : 0);
     if (index < 0 || index >= total) return fail(LPB_EINVAL, "group index out of range");
     std::memset(out, 0, sizeof *out);
     if (index >= nr + nm && index < nr + nm + nc) {
@@ -794,10 +871,17 @@ lpb_err lp_batch_group_info(lp_batch* h, int32_t index, lp_batch_group* out) {
         out->persistent = g.persistent;
         out->smem_bytes = (int64_t)(index >= nr && g.threads == 32 && !g.persistent ? g.smem_warp : g.smem);
         out->tuned_ms = g.tuned_ms;
-    } else {
+    } else if (index < nr + nm + nc + ns) {
         out->kind = 2;
         out->count = h->num_streamed;
         out->threads = lpb::kStreamedThreads;
+        out->persistent = 1;
+        out->smem_bytes = 0;
+        out->tuned_ms = -1.0f;
+    } else {
+        out->kind = 4;
+        out->count = h->num_mstream;
+        out->threads = lpb::kMixedStreamedThreads;
         out->persistent = 1;
         out->smem_bytes = 0;
         out->tuned_ms = -1.0f;
@@ -961,8 +1045,9 @@ lpb_err lp_batch_stage_times(lp_batch* h, float* stage_ms, int32_t* num_solves) 
 lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
     if (!h || !plan) return fail(LPB_EINVAL, "handle or plan is NULL");
     plan->num_groups = (int32_t)(h->groups.size() + h->mixed_groups.size() + h->cluster_groups.size()) +
-                       (h->num_streamed > 0 ? 1 : 0) + (h->num_mixed > 0 ? 1 : 0);
-    plan->num_resident = h->num_lps - h->num_streamed - h->num_cluster;
+                       (h->num_streamed > 0 ? 1 : 0) + (h->num_mstream > 0 ? 1 : 0) + (h->num_fsmall > 0 ? 1 : 0) +
+                       (h->num_fbig > 0 ? 1 : 0);
+    plan->num_resident = h->num_lps - h->num_streamed - h->num_mstream - h->num_cluster;
     plan->num_cluster = h->num_cluster;
     plan->num_mixed = h->num_mixed;
     plan->num_fallback = 0;
@@ -974,16 +1059,17 @@ lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
     for (int i = 0; i < 5; ++i) plan->internal_error_detail[i] = 0;
     if (h->solved) {
         DeviceGuard guard(h->device);
-        int32_t fb = 0, dg[8] = {0, 0, -1, 0, 0, 0, 0, 0}, ws[4] = {0, 0, 0, 0};
+        int32_t fb = 0, fbig = 0, dg[8] = {0, 0, -1, 0, 0, 0, 0, 0}, ws[4] = {0, 0, 0, 0};
         cudaError_t err = cudaSuccess;
         if (h->last_warm)
             err = cudaMemcpyAsync(ws, h->warm_stats, sizeof ws, cudaMemcpyDeviceToHost, h->last_stream);
-        else if (h->num_mixed > 0)
-            err = cudaMemcpyAsync(&fb, h->fb_len, sizeof fb, cudaMemcpyDeviceToHost, h->last_stream);
+        else if (h->num_mixed > 0 &&
+                 (err = cudaMemcpyAsync(&fb, h->fb_len, sizeof fb, cudaMemcpyDeviceToHost, h->last_stream)) == cudaSuccess)
+            err = cudaMemcpyAsync(&fbig, h->fbig_len, sizeof fbig, cudaMemcpyDeviceToHost, h->last_stream);
         if (err == cudaSuccess) err = cudaMemcpyAsync(dg, h->diag, sizeof dg, cudaMemcpyDeviceToHost, h->last_stream);
         if (err == cudaSuccess) err = cudaStreamSynchronize(h->last_stream);
         if (err != cudaSuccess) return cuda_fail(err, "plan counters");
-        plan->num_fallback = h->last_warm ? ws[0] : fb;
+        plan->num_fallback = h->last_warm ? ws[0] : fb + fbig;
         plan->num_warm_certified = h->last_warm ? ws[1] : 0;
         plan->num_warm_rounds = h->last_warm ? ws[2] : 0;
         plan->internal_errors = dg[0];
@@ -991,10 +1077,12 @@ lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
         plan->internal_error_lp = dg[0] ? dg[2] : -1;
         for (int i = 0; i < 5; ++i) plan->internal_error_detail[i] = dg[0] ? dg[3 + i] : 0;
     }
-    plan->num_streamed = h->num_streamed;
+    plan->num_streamed = h->num_streamed + h->num_mstream;
     plan->num_phase1 = h->num_phase1;
     plan->max_smem_bytes = (int64_t)h->max_smem;
-    plan->workspace_bytes = (int64_t)h->streamed_slots * (int64_t)h->slot_bytes;
+    plan->workspace_bytes = (int64_t)h->streamed_slots * (int64_t)h->slot_bytes +
+                            (int64_t)h->mstream_slots * (int64_t)h->mslot_bytes +
+                            (int64_t)h->fbig_slots * (int64_t)h->fbig_slot_bytes;
     return LPB_OK;
 }
 

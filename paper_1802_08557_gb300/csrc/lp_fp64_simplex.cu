@@ -471,18 +471,19 @@ fp64_resident_queue_kernel(const DeviceBatch B, const Tolerances tol, const int3
 
 __global__ void __launch_bounds__(kStreamedThreads, 2)
 fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order,
-                     const int32_t count, unsigned char* workspace, const size_t slot_bytes,
-                     int32_t* __restrict__ counter, int32_t* __restrict__ diag)
+                     const int32_t count, const int32_t* __restrict__ count_dev, unsigned char* workspace,
+                     const size_t slot_bytes, int32_t* __restrict__ counter, int32_t* __restrict__ diag)
 {
     __shared__ __align__(16) unsigned char small[SmallLayout::total];
     __shared__ int next;
     unsigned char* big = workspace + (size_t)blockIdx.x * slot_bytes;
+    const int n_items = count_dev ? min(*count_dev, count) : count;
     for (;;) {
         if (threadIdx.x == 0) next = atomicAdd(counter, 1);
         __syncthreads();
         const int idx = next;
         __syncthreads();
-        if (idx >= count) break;
+        if (idx >= n_items) break;
         solve_one<true>(B, tol, order[idx], small, big, diag);
         __syncthreads();
     }
@@ -525,12 +526,12 @@ int fp64_streamed_ctas_per_sm() {
 
 cudaError_t launch_fp64_streamed(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
                                  int32_t count, int slots, unsigned char* workspace, size_t slot_bytes,
-                                 int32_t* counter, int32_t* diag, cudaStream_t stream) {
+                                 int32_t* counter, int32_t* diag, cudaStream_t stream, const int32_t* count_dev) {
     if (count <= 0) return cudaSuccess;
     cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
     if (err != cudaSuccess) return err;
-    fp64_streamed_kernel<<<slots, kStreamedThreads, 0, stream>>>(B, tol, order, count, workspace, slot_bytes,
-                                                                  counter, diag);
+    fp64_streamed_kernel<<<slots, kStreamedThreads, 0, stream>>>(B, tol, order, count, count_dev, workspace,
+                                                                  slot_bytes, counter, diag);
     return cudaGetLastError();
 }
 

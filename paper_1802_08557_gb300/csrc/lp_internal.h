@@ -155,15 +155,29 @@ struct MixedParams {
     int32_t max_refine;  // refinement steps per vector
 };
 
+// Where the mixed-precision kernels put the LPs they do not certify: an LP
+// whose FP64 tableau fits one CTA (resident_smem_bytes <= kMaxSmemPerBlock -
+// 1 KiB) is appended to q (length *len, capacity cap), any other to qbig (the
+// FP64 streamed re-solve).  The lengths are zeroed by the caller before the
+// first mixed launch of a solve; a null queue or a full one records internal
+// error 4 and reports the LP LP_NUMERICAL.
+struct FallbackQueues {
+    int32_t* q;
+    int32_t* len;
+    int32_t cap;
+    int32_t* qbig;
+    int32_t* lenbig;
+    int32_t capbig;
+};
+
 cudaError_t mixed_kernel_prepare();
-// One CTA per LP of order[0..count): FP32 simplex, FP64 certificate; LPs that
-// are not certified are appended to fb_queue (length *fb_len, zeroed by the
-// caller before the first mixed launch of a solve).
+// One CTA per LP of order[0..count) (one warp per LP when threads == 32):
+// FP32 simplex in shared memory, FP64 certificate; uncertified LPs to fq.
 // diag: 3 int32 (count, first code, first LP) of internal-consistency
 // failures (see record_internal_error); may be null.
 cudaError_t launch_mixed(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
                          const int32_t* order, int32_t count, int threads, size_t smem,
-                         int32_t* fb_queue, int32_t* fb_len, int32_t fb_cap, int32_t* diag, cudaStream_t stream);
+                         const FallbackQueues& fq, int32_t* diag, cudaStream_t stream);
 
 // Launchers (lp_fp64_simplex.cu).
 constexpr int kStreamedThreads = 512;
@@ -174,9 +188,12 @@ cudaError_t launch_fp64_resident(const DeviceBatch& B, const Tolerances& tol, co
 // Persistent CTAs (grid = slots) take LPs of `order` from the atomic `counter`
 // (must be 0 at launch); each CTA keeps its tableau in workspace slot
 // blockIdx.x of `slot_bytes` bytes.
+// count_dev (or null): a device-side length of `order`, read at launch and
+// capped at `count`.
 cudaError_t launch_fp64_streamed(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
                                  int32_t count, int slots, unsigned char* workspace, size_t slot_bytes,
-                                 int32_t* counter, int32_t* diag, cudaStream_t stream);
+                                 int32_t* counter, int32_t* diag, cudaStream_t stream,
+                                 const int32_t* count_dev = nullptr);
 // CTAs of the streamed kernel that fit on one SM.
 int fp64_streamed_ctas_per_sm();
 // Resident kernel over a device-side LP list (persistent CTAs, atomic
@@ -231,9 +248,21 @@ cudaError_t launch_fp64_cluster(const DeviceBatch& B, const Tolerances& tol, con
 // from an atomic counter (zeroed here) until *count.
 cudaError_t launch_mixed_queue(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
                                const int32_t* order, const int32_t* count, int32_t* counter, int ctas, int threads,
-                               size_t smem, int32_t* fb_queue, int32_t* fb_len, int32_t fb_cap, int32_t* diag,
-                               cudaStream_t stream);
+                               size_t smem, const FallbackQueues& fq, int32_t* diag, cudaStream_t stream);
 int mixed_queue_ctas_per_sm(int threads, size_t smem);
+
+// Mixed precision with the FP32 tableau in a global workspace slot
+// (lp_mixed_streamed.cu), for LPs whose FP32 tableau exceeds one CTA's shared
+// memory: persistent CTAs of kMixedStreamedThreads threads take LPs of
+// order[0..count) from `counter` (zeroed here); CTA i works in slot i of
+// `slot_bytes` bytes (at least mixed_layout(m, n, k).total of every listed LP,
+// a multiple of 256).  Results are bit-identical to the shared-memory kernels.
+constexpr int kMixedStreamedThreads = 512;
+cudaError_t launch_mixed_streamed(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
+                                  const int32_t* order, int32_t count, int slots, unsigned char* workspace,
+                                  size_t slot_bytes, int32_t* counter, const FallbackQueues& fq, int32_t* diag,
+                                  cudaStream_t stream);
+int mixed_streamed_ctas_per_sm();
 
 // Learned warm start (lp_warm.cu): features [num_lps x (m+n)] = (b, c) as
 // FP32; the restricted-LP solve and FP64 check of each LP from the network's

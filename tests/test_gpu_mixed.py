@@ -107,6 +107,71 @@ def test_mixed_extreme_scales_fall_back_correctly():
     assert g["plan"]["num_fallback"] >= int((~in_range).sum())
 
 
+def test_mixed_streamed_matches_shared_memory_bitwise():
+    """LPB_SCHED_STREAMED with FP32_REFINE puts every LP's FP32 tableau in a
+    global workspace slot (persistent 512-thread CTAs, group kind 4).  The
+    per-LP arithmetic does not depend on where the tableau lives or on the
+    thread count, so every output equals the shared-memory kernels' bit for
+    bit (the uneven batch includes m >= 64, where certificate sums are split)."""
+    for batch in (W.mixed_sign_dense(1500, 50, 50, start=99), W.uneven_dense(300, lo=8, hi=150, start=17)):
+        a = gpu_solve(batch, opts=mixed_opts())
+        s = lpb.BatchSolver(batch, opts=mixed_opts(schedule=lpb.LPB_SCHED_STREAMED))
+        try:
+            s.solve()
+            b = s.results()
+            plan = s.plan_info()
+            kinds = {g["kind"] for g in lpb.lp_batch_groups(s.h)}
+        finally:
+            s.close()
+        assert plan["internal_errors"] == 0, plan
+        assert plan["num_streamed"] == batch.num_lps and plan["num_resident"] == 0, plan
+        assert kinds == {4}, kinds
+        assert plan["num_fallback"] == a["plan"]["num_fallback"]
+        for key in ("status", "iters", "obj", "x", "y"):
+            np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+
+
+def test_mixed_large_lps_and_their_fp64_streamed_re_solve():
+    """FP32 tableaux above one CTA's shared memory run in the streamed mixed
+    kernel; LPs whose FP64 tableau exceeds one CTA and that the mixed path does
+    not certify (here: an entry outside the FP32 range) are re-solved by the
+    FP64 streamed kernel, whose answer equals the FP64 path's (cluster
+    kernel) bit for bit.  Every status equals the FP64 path's, every optimal
+    objective agrees within 1e-9."""
+    rng = np.random.default_rng(5)
+    lps, forced = [], []
+    for t in range(8):
+        # t < 4: FP32 tableau fits one CTA, FP64 does not; t >= 4: neither fits
+        m, n = (170 + 10 * t, 160 + 5 * t) if t < 4 else (250 + 10 * t, 240 + 10 * t)
+        A = rng.uniform(0.0, 1.0, (m, n))
+        b = rng.uniform(1.0, 100.0, m)
+        c = rng.uniform(0.0, 1.0, n)
+        if t % 2 == 1:
+            A[0, 0] = 2.0 ** 61  # outside the FP32 range: straight to the FP64 re-solve
+        forced.append(t % 2 == 1)
+        lps.append((A, b, c))
+    batch = W.pack("large_mixed", lps)
+    g = gpu_solve(batch, opts=mixed_opts())
+    f = gpu_solve(batch, opts=lpb.lpb_default_opts())
+    s = lpb.BatchSolver(batch, opts=mixed_opts())
+    try:
+        kinds = sorted({gg["kind"] for gg in lpb.lp_batch_groups(s.h)})
+    finally:
+        s.close()
+    assert kinds == [0, 4], kinds
+    assert g["plan"]["num_fallback"] >= sum(forced)
+    np.testing.assert_array_equal(g["status"], f["status"])
+    opt = f["status"] == 0
+    assert opt.any()
+    np.testing.assert_allclose(g["obj"][opt], f["obj"][opt], rtol=OBJ_RTOL, atol=OBJ_RTOL)
+    xo, yo = batch.x_offsets(), batch.y_offsets()
+    for k in np.nonzero(forced)[0]:
+        m, n = int(batch.m[k]), int(batch.n[k])
+        assert g["iters"][k] == f["iters"][k] and g["obj"][k] == f["obj"][k]
+        np.testing.assert_array_equal(g["x"][xo[k]:xo[k] + n], f["x"][xo[k]:xo[k] + n])
+        np.testing.assert_array_equal(g["y"][yo[k]:yo[k] + m], f["y"][yo[k]:yo[k] + m])
+
+
 @pytest.mark.slow
 def test_full_size_repeat_solves_are_identical():
     """1e5 LPs of 50 x 50: solving twice gives bitwise identical results on
