@@ -191,6 +191,10 @@ struct lp_batch {
     int32_t fbig_slots = 0;
     size_t fbig_slot_bytes = 0;
     unsigned char* fbig_workspace = nullptr;
+    // ... on thread-block clusters of fbig_C CTAs when every such LP fits one
+    // (0: on the streamed kernel)
+    int fbig_C = 0, fbig_clusters = 0;
+    size_t fbig_cluster_smem = 0;
     // optional stage timing: event triples (start, groups joined, re-solve
     // done) for the last kTimingRing solves
     std::vector<cudaEvent_t> tev;
@@ -338,8 +342,13 @@ lpb_err enqueue_solve(lp_batch* h, cudaStream_t s, bool timing) {
         if (err != cudaSuccess) return cuda_fail(err, "fallback launch");
     }
     if (h->num_fbig > 0) {
-        err = lpb::launch_fp64_streamed(h->d, h->tol, h->fbig_queue, h->num_fbig, h->fbig_slots, h->fbig_workspace,
-                                        h->fbig_slot_bytes, h->fbig_counter, h->diag, s, h->fbig_len);
+        if (h->fbig_C > 0)
+            err = lpb::launch_fp64_cluster(h->d, h->tol, h->fbig_queue, h->num_fbig, h->fbig_C, h->fbig_clusters,
+                                           h->fbig_cluster_smem, h->fbig_counter, h->diag, s, h->fbig_len);
+        else
+            err = lpb::launch_fp64_streamed(h->d, h->tol, h->fbig_queue, h->num_fbig, h->fbig_slots,
+                                            h->fbig_workspace, h->fbig_slot_bytes, h->fbig_counter, h->diag, s,
+                                            h->fbig_len);
         if (err != cudaSuccess) return cuda_fail(err, "fallback launch");
     }
     if (tev) {
@@ -500,6 +509,7 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     std::vector<int32_t> streamed;
     std::map<int, std::vector<int32_t>> cluster_buckets;  // cluster size -> LPs
     std::vector<int32_t> mstream;                         // mixed precision, tableau in global memory
+    std::vector<int32_t> fbig_lps;                        // mixed LPs whose FP64 re-solve exceeds one CTA
     const size_t queue_smem_cap = lpb::kMaxSmemPerBlock - 1024;
     h->uniform_m = hm[0];
     h->uniform_n = hn[0];
@@ -521,6 +531,7 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
             } else {
                 ++h->num_fbig;
                 h->fbig_slot_bytes = std::max(h->fbig_slot_bytes, lpb::streamed_slot_bytes(hm[k], hn[k], hk[k]));
+                fbig_lps.push_back(k);
             }
             const size_t mneed = lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]);
             if (o.schedule == LPB_SCHED_AUTO && mneed <= queue_smem_cap) {
@@ -683,11 +694,36 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         if (h->num_fsmall > 0)
             h->fb_ctas = sms * lpb::fp64_resident_queue_ctas_per_sm(h->fb_threads, h->fb_smem);
         if (h->num_fbig > 0) {
-            // one slot per SM: re-solves are few, and each slot holds an FP64 tableau
-            const int64_t cap = std::max<int64_t>(1, kMaxWorkspaceBytes / (int64_t)h->fbig_slot_bytes);
-            h->fbig_slots = (int32_t)std::min<int64_t>({(int64_t)sms, (int64_t)h->num_fbig, cap});
-            if ((err = alloc(h, &h->fbig_workspace, (size_t)h->fbig_slots * h->fbig_slot_bytes, s)))
-                return bail_cuda(err, "fallback workspace allocation");
+            // re-solve on clusters: the smallest cluster size that holds every
+            // such LP (re-solves are few, so each gets many SMs' FP64 pipes)
+            int C = 0;
+            for (int32_t k : fbig_lps) {
+                int ck = 0;
+                for (int c = 2; c <= lpb::kMaxClusterCtas && !ck; ++c)
+                    if (lpb::cluster_smem_bytes(hm[k], hn[k], hk[k], c) <= lpb::kMaxSmemPerBlock - 1024) ck = c;
+                if (!ck) { C = 0; break; }
+                C = std::max(C, ck);
+            }
+            if (C) {
+                size_t smem = 0;
+                for (int32_t k : fbig_lps) smem = std::max(smem, lpb::cluster_smem_bytes(hm[k], hn[k], hk[k], C));
+                smem = (smem + 1023) / 1024 * 1024;
+                int active = 0;
+                if (lpb::cluster_kernel_prepare() == cudaSuccess) active = lpb::cluster_max_active(C, smem);
+                cudaGetLastError();
+                if (active > 0) {
+                    h->fbig_C = C;
+                    h->fbig_clusters = std::min<int32_t>(active, h->num_fbig);
+                    h->fbig_cluster_smem = smem;
+                }
+            }
+            if (!h->fbig_C) {
+                // else streamed, one slot per SM
+                const int64_t cap = std::max<int64_t>(1, kMaxWorkspaceBytes / (int64_t)h->fbig_slot_bytes);
+                h->fbig_slots = (int32_t)std::min<int64_t>({(int64_t)sms, (int64_t)h->num_fbig, cap});
+                if ((err = alloc(h, &h->fbig_workspace, (size_t)h->fbig_slots * h->fbig_slot_bytes, s)))
+                    return bail_cuda(err, "fallback workspace allocation");
+            }
         }
     }
     if ((err = alloc(h, &h->diag, 8, s)) || (err = cudaMemsetAsync(h->diag, 0, 32, s)))

@@ -448,19 +448,20 @@ __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int
 
 __global__ void __launch_bounds__(kClusterThreads, 1)
 fp64_cluster_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order, const int32_t count,
-                    int32_t* __restrict__ counter, int32_t* __restrict__ diag)
+                    const int32_t* __restrict__ count_dev, int32_t* __restrict__ counter, int32_t* __restrict__ diag)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_next;
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int q = (int)cl.block_rank();
+    const int n_items = count_dev ? min(*count_dev, count) : count;
     for (;;) {
         if (q == 0 && threadIdx.x == 0) s_next = atomicAdd(counter, 1);
         cl.sync();
         const int idx = *cl.map_shared_rank(&s_next, 0);
         cl.sync();  // every CTA has read it (and left the previous LP's rows)
-        if (idx >= count) break;
+        if (idx >= n_items) break;
         build_and_solve(cl, C, q, B, tol, order[idx], smem, diag);
     }
 }
@@ -500,7 +501,7 @@ int cluster_max_active(int C, size_t smem) {
 
 cudaError_t launch_fp64_cluster(const DeviceBatch& B, const Tolerances& tol, const int32_t* order, int32_t count,
                                 int C, int clusters, size_t smem, int32_t* counter, int32_t* diag,
-                                cudaStream_t stream) {
+                                cudaStream_t stream, const int32_t* count_dev) {
     if (count <= 0) return cudaSuccess;
     cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
     if (err != cudaSuccess) return err;
@@ -516,7 +517,7 @@ cudaError_t launch_fp64_cluster(const DeviceBatch& B, const Tolerances& tol, con
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, fp64_cluster_kernel, B, tol, order, count, counter, diag);
+    return cudaLaunchKernelEx(&cfg, fp64_cluster_kernel, B, tol, order, count, count_dev, counter, diag);
 }
 
 }  // namespace lpb

@@ -240,9 +240,11 @@ constexpr int kMaxClusterCtas = 16;
 size_t cluster_smem_bytes(int m, int n, int k, int C);
 cudaError_t cluster_kernel_prepare();
 int cluster_max_active(int C, size_t smem);
+// count_dev (or null): a device-side length of `order`, read at launch and
+// capped at `count`.
 cudaError_t launch_fp64_cluster(const DeviceBatch& B, const Tolerances& tol, const int32_t* order, int32_t count,
                                 int C, int clusters, size_t smem, int32_t* counter, int32_t* diag,
-                                cudaStream_t stream);
+                                cudaStream_t stream, const int32_t* count_dev = nullptr);
 
 // Persistent form of the mixed-precision kernel: CTAs take order[idx] for idx
 // from an atomic counter (zeroed here) until *count.
