@@ -536,7 +536,10 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
             const size_t mneed = lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]);
             if (o.schedule == LPB_SCHED_AUTO && mneed <= queue_smem_cap) {
                 const int threads = mixed_threads(hm[k], hn[k], hk[k], o.block_threads);
-                mixed_buckets[{threads, (mneed + 1023) / 1024 * 1024}].push_back(k);
+                // shared memory rounded to 1 KiB for the one-warp form (it sets
+                // how many LPs share an SM), to 4 KiB otherwise (fewer launches)
+                const size_t gran = threads == 32 ? 1024 : 4096;
+                mixed_buckets[{threads, std::min(queue_smem_cap, (mneed + gran - 1) / gran * gran)}].push_back(k);
             } else {
                 mstream.push_back(k);
                 h->mslot_bytes = std::max(h->mslot_bytes, (lpb::mixed_layout(hm[k], hn[k], hk[k]).total + 255) &
