@@ -537,8 +537,11 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
             if (o.schedule == LPB_SCHED_AUTO && mneed <= queue_smem_cap) {
                 const int threads = mixed_threads(hm[k], hn[k], hk[k], o.block_threads);
                 // shared memory rounded to 1 KiB for the one-warp form (it sets
-                // how many LPs share an SM), to 4 KiB otherwise (fewer launches)
-                const size_t gran = threads == 32 ? 1024 : 4096;
+                // how many LPs share an SM), to 8 KiB otherwise: fewer, larger
+                // launches (uneven workload: 1 KiB 280 groups 17.3 ms, 4 KiB
+                // 123 groups 11.6 ms, 8 KiB 97 groups 11.2 ms, 16 KiB 84 groups
+                // 11.4 ms)
+                const size_t gran = threads == 32 ? 1024 : 8192;
                 mixed_buckets[{threads, std::min(queue_smem_cap, (mneed + gran - 1) / gran * gran)}].push_back(k);
             } else {
                 mstream.push_back(k);
