@@ -163,6 +163,40 @@ lpb_err lp_batch_solve(lp_batch *h, void *stream);
 lpb_err lp_batch_results(lp_batch *h, int32_t *status, int32_t *iters, double *obj,
                          double *x, double *y, int32_t ptr_kind);
 
+/* Largest `chunks` of lp_solve_host. */
+#define LPB_MAX_HOST_CHUNKS 64
+
+/*
+ * One call from host buffers to host results, with the copy of the inputs
+ * overlapped with the solve: the batch is split into `chunks` contiguous
+ * ranges of LPs (0 = 4 for 4096 LPs or more, else 1), each created and solved
+ * as its own batch on its own internal stream, so that one range's inputs are
+ * copied while the previous one solves; then every range's results are read.
+ * Section 4.3 of the paper splits a batch over CUDA streams so that copies
+ * overlap kernels; this is the same idea inside one call.
+ *
+ *  num_lps, m, n, a_off, A, a_len, b_off, b, b_len, c_off, c, c_len, opts:
+ *                 as for lp_batch_create, all in HOST memory.  Each range
+ *                 copies the smallest spans of A, b and c that hold its LPs
+ *                 (shared data is copied once per range).  The overlap needs
+ *                 page-locked (pinned) A, b, c; with pageable memory the call
+ *                 still works, with less overlap.
+ *  status, iters, obj [num_lps], x [sum of n], y [sum of m] or NULL: HOST
+ *                 buffers, filled as by lp_batch_results.
+ * Each LP's results are the same, bit for bit, as those of lp_batch_create +
+ * lp_batch_solve + lp_batch_results on the whole batch with the same opts (an
+ * LP's arithmetic does not depend on the batch it is solved in).  Synchronous:
+ * returns when the results are in the host buffers.  Errors: LPB_EINVAL for
+ * bad arguments (nothing launched) and every error of lp_batch_create /
+ * lp_batch_solve / lp_batch_results; all device memory is released on return.
+ */
+lpb_err lp_solve_host(int32_t num_lps, const int32_t *m, const int32_t *n,
+                      const int64_t *a_off, const double *A, int64_t a_len,
+                      const int64_t *b_off, const double *b, int64_t b_len,
+                      const int64_t *c_off, const double *c, int64_t c_len,
+                      const lp_batch_opts *opts, int32_t chunks,
+                      int32_t *status, int32_t *iters, double *obj, double *x, double *y);
+
 /* Launch plan of a batch (filled by lp_batch_plan_info). */
 typedef struct {
     int32_t num_groups;        /* kernel launches per solve                         */

@@ -496,11 +496,22 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         return bail_cuda(err, "input check kernel");
     std::vector<int32_t> hk(num_lps);
     unsigned long long bad = 0;
-    if ((err = cudaMemcpyAsync(hk.data(), dk, nl * 4, cudaMemcpyDeviceToHost, s)) ||
-        (err = cudaMemcpyAsync(&bad, dbad, sizeof bad, cudaMemcpyDeviceToHost, s)) ||
-        (err = cudaStreamSynchronize(s)))
-        return bail_cuda(err, "input check");
-    if (bad) return bail(LPB_EINVAL, std::to_string(bad) + " non-finite entries in A, b or c");
+    if (ptr_kind == LPB_HOST) {
+        // phase-I rows counted here while the copies and the input check run
+        // (the plan below overlaps them too); the check is read after the plan
+        for (int32_t k = 0; k < num_lps; ++k) {
+            const double* bk = b + hb[k];
+            int32_t cnt = 0;
+            for (int32_t i = 0; i < hm[k]; ++i) cnt += bk[i] < 0.0 ? 1 : 0;
+            hk[k] = cnt;
+        }
+    } else {
+        if ((err = cudaMemcpyAsync(hk.data(), dk, nl * 4, cudaMemcpyDeviceToHost, s)) ||
+            (err = cudaMemcpyAsync(&bad, dbad, sizeof bad, cudaMemcpyDeviceToHost, s)) ||
+            (err = cudaStreamSynchronize(s)))
+            return bail_cuda(err, "input check");
+        if (bad) return bail(LPB_EINVAL, std::to_string(bad) + " non-finite entries in A, b or c");
+    }
 
     // Plan: LPs whose tableau fits in one CTA's shared memory are grouped by
     // (threads per CTA, footprint rounded up to 4 KiB), one launch per group;
@@ -572,12 +583,14 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     }
     // Longest work first within every list (LPT): the tail of a launch is
     // made of small LPs.  Work estimate: (m+1)(n+k+1) per pivot, O(m+n) pivots.
+    std::vector<double> work(num_lps);
+    for (int32_t k = 0; k < num_lps; ++k)
+        work[k] = (double)(hm[k] + 1) * (hn[k] + hk[k] + 1) * (hm[k] + hn[k]);
     auto lpt = [&](std::vector<int32_t>& v) {
-        std::stable_sort(v.begin(), v.end(), [&](int32_t a, int32_t b) {
-            const double wa = (double)(hm[a] + 1) * (hn[a] + hk[a] + 1) * (hm[a] + hn[a]);
-            const double wb = (double)(hm[b] + 1) * (hn[b] + hk[b] + 1) * (hm[b] + hn[b]);
-            return wa > wb;
-        });
+        bool uniform = true;
+        for (size_t i = 1; i < v.size() && uniform; ++i) uniform = work[v[i]] == work[v[0]];
+        if (uniform) return;  // already in order
+        std::stable_sort(v.begin(), v.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
     };
     for (auto& kv : buckets) lpt(kv.second);
     for (auto& kv : mixed_buckets) lpt(kv.second);
@@ -741,8 +754,10 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
             (err = cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming)))
             return bail_cuda(err, "stream creation");
     if ((err = cudaMemcpyAsync(dorder, order.data(), nl * 4, cudaMemcpyHostToDevice, s)) ||
+        (ptr_kind == LPB_HOST && (err = cudaMemcpyAsync(&bad, dbad, sizeof bad, cudaMemcpyDeviceToHost, s))) ||
         (err = lpb::fp64_kernels_prepare()) || (err = cudaStreamSynchronize(s)))
         return bail_cuda(err, "plan upload");
+    if (bad) return bail(LPB_EINVAL, std::to_string(bad) + " non-finite entries in A, b or c");
     *out = h;
     return LPB_OK;
 }
@@ -1192,6 +1207,85 @@ lpb_err lp_batch_destroy(lp_batch* h) {
     cudaStreamSynchronize(h->last_stream);
     release(h, h->last_stream);
     delete h;
+    return LPB_OK;
+}
+
+lpb_err lp_solve_host(int32_t num_lps, const int32_t* m, const int32_t* n,
+                      const int64_t* a_off, const double* A, int64_t a_len,
+                      const int64_t* b_off, const double* b, int64_t b_len,
+                      const int64_t* c_off, const double* c, int64_t c_len,
+                      const lp_batch_opts* opts, int32_t chunks,
+                      int32_t* status, int32_t* iters, double* obj, double* x, double* y) {
+    g_last_error.clear();
+    if (num_lps < 1) return fail(LPB_EINVAL, "num_lps < 1");
+    if (!m || !n || !A || !b || !c) return fail(LPB_EINVAL, "m, n, A, b and c must be non-NULL");
+    if (!status || !iters || !obj || !x) return fail(LPB_EINVAL, "status, iters, obj and x must be non-NULL");
+    if (chunks < 0 || chunks > LPB_MAX_HOST_CHUNKS) return fail(LPB_EINVAL, "chunks must be in [0, LPB_MAX_HOST_CHUNKS]");
+    if (chunks == 0) chunks = num_lps >= 4096 ? 4 : 1;
+    chunks = std::min(chunks, num_lps);
+    // every LP's offsets (packed when NULL); each chunk passes the smallest
+    // ranges of A, b and c that hold its LPs, with offsets rebased to them
+    std::vector<int64_t> ha(num_lps), hb(num_lps), hc(num_lps);
+    int64_t pa = 0, pb = 0, pc = 0;
+    for (int32_t k = 0; k < num_lps; ++k) {
+        const int64_t mk = m[k], nk = n[k];
+        if (mk < 1 || nk < 1) return fail(LPB_EINVAL, "LP " + std::to_string(k) + ": m and n must be >= 1");
+        ha[k] = a_off ? a_off[k] : pa;
+        hb[k] = b_off ? b_off[k] : pb;
+        hc[k] = c_off ? c_off[k] : pc;
+        pa += mk * nk; pb += mk; pc += nk;
+        if (ha[k] < 0 || ha[k] + mk * nk > a_len || hb[k] < 0 || hb[k] + mk > b_len || hc[k] < 0 ||
+            hc[k] + nk > c_len)
+            return fail(LPB_EINVAL, "LP " + std::to_string(k) + ": offset out of range");
+    }
+    std::vector<cudaStream_t> streams(chunks, nullptr);
+    std::vector<lp_batch*> hs(chunks, nullptr);
+    std::vector<int32_t> k0s(chunks + 1);
+    std::vector<int64_t> xs(chunks), ys(chunks);
+    lpb_err e = LPB_OK;
+    int64_t px = 0, py = 0;
+    for (int32_t i = 0; i <= chunks; ++i) k0s[i] = (int32_t)((int64_t)num_lps * i / chunks);
+    // chunk i+1 is created (its inputs copied) while chunk i solves
+    for (int32_t i = 0; i < chunks && e == LPB_OK; ++i) {
+        const int32_t k0 = k0s[i], k1 = k0s[i + 1];
+        xs[i] = px;
+        ys[i] = py;
+        int64_t alo = INT64_MAX, ahi = 0, blo = INT64_MAX, bhi = 0, clo = INT64_MAX, chi = 0;
+        for (int32_t k = k0; k < k1; ++k) {
+            px += n[k];
+            py += m[k];
+            alo = std::min(alo, ha[k]); ahi = std::max(ahi, ha[k] + (int64_t)m[k] * n[k]);
+            blo = std::min(blo, hb[k]); bhi = std::max(bhi, hb[k] + (int64_t)m[k]);
+            clo = std::min(clo, hc[k]); chi = std::max(chi, hc[k] + (int64_t)n[k]);
+        }
+        std::vector<int64_t> sa(k1 - k0), sb(k1 - k0), sc(k1 - k0);
+        for (int32_t k = k0; k < k1; ++k) {
+            sa[k - k0] = ha[k] - alo;
+            sb[k - k0] = hb[k] - blo;
+            sc[k - k0] = hc[k] - clo;
+        }
+        cudaError_t err = cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking);
+        if (err != cudaSuccess) {
+            e = cuda_fail(err, "stream creation");
+            break;
+        }
+        e = lp_batch_create(&hs[i], k1 - k0, m + k0, n + k0, sa.data(), A + alo, ahi - alo, sb.data(), b + blo,
+                            bhi - blo, sc.data(), c + clo, chi - clo, LPB_HOST, opts, streams[i]);
+        if (e == LPB_OK) e = lp_batch_solve(hs[i], streams[i]);
+    }
+    for (int32_t i = 0; i < chunks && e == LPB_OK; ++i) {
+        const int32_t k0 = k0s[i];
+        e = lp_batch_results(hs[i], status + k0, iters + k0, obj + k0, x + xs[i], y ? y + ys[i] : nullptr, LPB_HOST);
+    }
+    const std::string msg = g_last_error;
+    for (int32_t i = 0; i < chunks; ++i) {
+        if (hs[i]) lp_batch_destroy(hs[i]);
+        if (streams[i]) {
+            cudaStreamSynchronize(streams[i]);
+            cudaStreamDestroy(streams[i]);
+        }
+    }
+    if (e != LPB_OK) return fail(e, msg);
     return LPB_OK;
 }
 

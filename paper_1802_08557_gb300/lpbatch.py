@@ -30,7 +30,7 @@ EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_r
             "lp_mlp_create", "lp_mlp_num_params", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_set_scaling",
             "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients", "lp_mlp_destroy", "lp_batch_solve_warm",
             "lp_batch_features", "lp_batch_active_labels", "lp_batch_solve_graph", "lp_batch_autotune",
-            "lp_batch_group_info", "lp_batch_set_group_form")
+            "lp_batch_group_info", "lp_batch_set_group_form", "lp_solve_host")
 
 
 class LPBatchOpts(ctypes.Structure):
@@ -138,6 +138,9 @@ def load(path: str | None = None):
         L.lp_batch_group_info.restype = ctypes.c_int
         L.lp_batch_set_group_form.argtypes = [_vp, _i32, _i32, _i32]
         L.lp_batch_set_group_form.restype = ctypes.c_int
+        L.lp_solve_host.argtypes = [_i32, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _i64, _vp, _vp, _i64,
+                                    ctypes.POINTER(LPBatchOpts), _i32, _vp, _vp, _vp, _vp, _vp]
+        L.lp_solve_host.restype = ctypes.c_int
         L.lp_batch_solve_warm.argtypes = [_vp, _vp, ctypes.c_float, _vp]
         L.lp_batch_solve_warm.restype = ctypes.c_int
         L.lp_batch_features.argtypes = [_vp, _vp, _vp]
@@ -226,6 +229,24 @@ def lp_batch_create(m, n, a_off, A, b_off, b, c_off, c, ptr_kind: int, opts: LPB
                              ctypes.byref(opts) if opts is not None else None, _stream_handle(stream))
     _check(code, "lp_batch_create")
     return h
+
+
+def lp_solve_host(m, n, a_off, A, b_off, b, c_off, c, status, iters, obj, x, y=None,
+                  opts: LPBatchOpts | None = None, chunks: int = 0):
+    """One call from host arrays (numpy or pinned CPU tensors) to host result
+    arrays, the input copies overlapped with the solve (see include/lpbatch.h)."""
+    L = load()
+    m = np.ascontiguousarray(m, np.int32)
+    n = np.ascontiguousarray(n, np.int32)
+    a_off = None if a_off is None else np.ascontiguousarray(a_off, np.int64)
+    b_off = None if b_off is None else np.ascontiguousarray(b_off, np.int64)
+    c_off = None if c_off is None else np.ascontiguousarray(c_off, np.int64)
+    lens = [int(np.prod(np.shape(v))) if isinstance(v, np.ndarray) else int(v.numel()) for v in (A, b, c)]
+    code = L.lp_solve_host(int(m.shape[0]), _addr(m), _addr(n), _addr(a_off), _addr(A), lens[0],
+                           _addr(b_off), _addr(b), lens[1], _addr(c_off), _addr(c), lens[2],
+                           ctypes.byref(opts) if opts is not None else None, int(chunks),
+                           _addr(status), _addr(iters), _addr(obj), _addr(x), _addr(y))
+    _check(code, "lp_solve_host")
 
 
 def lp_batch_solve(h, stream=None):

@@ -85,6 +85,25 @@ def test_argument_errors_before_device_work(lib):
     assert lib.lp_batch_destroy(None) == lpb.LPB_OK
 
 
+def test_solve_host_argument_errors_before_device_work(lib):
+    A, b, c = np.ones(4), np.ones(2), np.ones(2)
+    m, n = np.array([2], np.int32), np.array([2], np.int32)
+    st, it, ob, x = np.zeros(1, np.int32), np.zeros(1, np.int32), np.zeros(1), np.zeros(2)
+    P = lambda a: a.ctypes.data if a is not None else None
+
+    def call(num=1, mm=m, AA=A, a_len=4, chunks=0, xx=x):
+        return lib.lp_solve_host(num, P(mm), P(n), None, P(AA), a_len, None, P(b), 2, None, P(c), 2, None, chunks,
+                                 P(st), P(it), P(ob), P(xx), None)
+    assert call(num=0) == lpb.LPB_EINVAL
+    assert call(AA=None) == lpb.LPB_EINVAL
+    assert call(xx=None) == lpb.LPB_EINVAL
+    assert call(chunks=-1) == lpb.LPB_EINVAL
+    assert call(chunks=65) == lpb.LPB_EINVAL
+    assert call(mm=np.array([0], np.int32)) == lpb.LPB_EINVAL
+    assert call(a_len=3) == lpb.LPB_EINVAL
+    assert b"offset out of range" in lib.lpb_last_error()
+
+
 def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(lpb, "_lib", None)
     with pytest.raises(ImportError):

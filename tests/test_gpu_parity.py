@@ -274,3 +274,30 @@ def test_cluster_kernel_matches_streamed_bitwise():
     assert len(set(a["status"].tolist())) >= 2
     for key in ("status", "iters", "obj", "x", "y"):
         np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32r"])
+def test_solve_host_equals_create_solve_results(prec):
+    """lp_solve_host (host buffers in, host results out, the batch split into
+    chunks whose input copies overlap the previous chunk's solve) gives every
+    LP's results bit for bit as one create + solve + results of the whole
+    batch, for several chunk counts, pinned and pageable inputs, and a batch
+    whose LPs share one A (repeated offsets)."""
+    import torch
+    opts = lpb.lpb_default_opts(precision=lpb.LP_PREC_FP64 if prec == "fp64" else lpb.LP_PREC_FP32_REFINE)
+    for batch in (W.mixed_sign_dense(3001, 30, 20, start=123), W.support_function(2000, start=7)):
+        ref = gpu_solve(batch, opts=opts)
+        N = batch.num_lps
+        for chunks, pinned in ((0, True), (1, False), (3, True), (7, False)):
+            if pinned:
+                A, b, c = (torch.from_numpy(getattr(batch, k)).pin_memory() for k in ("A", "b", "c"))
+            else:
+                A, b, c = batch.A, batch.b, batch.c
+            st, it = np.zeros(N, np.int32), np.zeros(N, np.int32)
+            ob = np.zeros(N)
+            x = np.zeros(int(batch.n.astype(np.int64).sum()))
+            y = np.zeros(int(batch.m.astype(np.int64).sum()))
+            lpb.lp_solve_host(batch.m, batch.n, batch.a_off, A, batch.b_off, b, batch.c_off, c, st, it, ob, x, y,
+                              opts=opts, chunks=chunks)
+            for key, v in (("status", st), ("iters", it), ("obj", ob), ("x", x), ("y", y)):
+                np.testing.assert_array_equal(v, ref[key], err_msg=f"{key} chunks={chunks}")
