@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kWarmThreads) warm_features_kernel(DeviceBatch
 // Dynamic shared memory of the warm kernel.
 struct WarmLayout {
     int LD;  // tableau row stride (doubles)
-    size_t rows, inR, col_var, row_var, T, colE, xv, yv, total;
+    size_t rows, inR, col_var, row_var, T, colE, rkey, xv, yv, total;
 };
 
 __host__ __device__ inline WarmLayout warm_layout(int m, int n, int kmax) {
@@ -73,6 +73,7 @@ __host__ __device__ inline WarmLayout warm_layout(int m, int n, int kmax) {
     L.row_var = o; o += align16((size_t)kmax * 4);
     L.T = o;       o += align16((size_t)(kmax + 1) * L.LD * 8);
     L.colE = o;    o += align16((size_t)(kmax + 1) * 8);
+    L.rkey = o;    o += align16((size_t)(kmax + 1) * 8);
     L.xv = o;      o += align16((size_t)n * 8);
     L.yv = o;      o += align16((size_t)kmax * 8);
     L.total = o;
@@ -94,6 +95,8 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
     int* row_var = reinterpret_cast<int*>(smem + L.row_var);
     double* T = reinterpret_cast<double*>(smem + L.T);
     double* colE = reinterpret_cast<double*>(smem + L.colE);
+    long long* rkey = reinterpret_cast<long long*>(smem + L.rkey);  // Step 2 ratio keys
+    __shared__ double s_rinv;
     double* xv = reinterpret_cast<double*>(smem + L.xv);
     double* yv = reinterpret_cast<double*>(smem + L.yv);
     const int LD = L.LD;
@@ -158,38 +161,54 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
             esel = red.min_u32(esel);
             const int e = (int)(esel & 0xFFFFu);
             if (e < 1 || e > n) { status = 4; break; }
-            // Step 2: minimum ratio over rows with t_re > eps_piv; exact ties to the lowest row
+            // Step 2: minimum ratio over rows with t_re > eps_piv; exact ties to
+            // the lowest row (each ratio divided once, its key kept for the tie pass)
             long long rl = LLONG_MAX;
             for (int r = tid; r <= k; r += nt) {
                 const double t = T[(size_t)r * LD + e];
                 colE[r] = t;
-                if (r < k && t > a.eps_piv) rl = min(rl, okey(__ddiv_rn(T[(size_t)r * LD], t)));
+                const long long key = (r < k && t > a.eps_piv) ? okey(__ddiv_rn(T[(size_t)r * LD], t)) : LLONG_MAX;
+                rkey[r] = key;
+                rl = min(rl, key);
             }
             const long long rmin = red.min_i64(rl);
             if (rmin == LLONG_MAX) { status = 2; e_unb = e; break; }
             unsigned lsel = 0xFFFFFFFFu;
-            for (int r = tid; r < k; r += nt) {
-                const double t = colE[r];
-                if (t > a.eps_piv && okey(__ddiv_rn(T[(size_t)r * LD], t)) == rmin) lsel = min(lsel, (unsigned)r);
-            }
+            for (int r = tid; r < k; r += nt)
+                if (rkey[r] == rmin) lsel = min(lsel, (unsigned)r);
             const int l = (int)red.min_u32(lsel);
             if (l < 0 || l >= k || !(fabs(colE[l]) < 1e300)) { status = 4; break; }
             if (iters >= a.max_iters) { status = 3; break; }
-            // Step 3: pivot
-            const double pe = colE[l];
+            // Step 3: pivot row times one reciprocal (the restricted LP only
+            // proposes the rows; its optimum is checked on the full LP below),
+            // computed once and shared: a warp's FP64 instruction costs the
+            // whole warp's pipe time
+            if (tid == 0) s_rinv = __drcp_rn(colE[l]);
+            __syncthreads();
+            const double rinv = s_rinv;
             double* Tl = T + (size_t)l * LD;
-            for (int j = tid; j <= n; j += nt) Tl[j] = __ddiv_rn((j == e) ? 1.0 : Tl[j], pe);
+            for (int j = tid; j <= n; j += nt) Tl[j] = (j == e) ? rinv : __dmul_rn(Tl[j], rinv);
             if (tid == 0) {
                 const int ev = col_var[e];
                 col_var[e] = row_var[l];
                 row_var[l] = ev;
             }
             __syncthreads();
-            for (int idx = tid; idx < (k + 1) * (n + 1); idx += nt) {
-                const int r = idx / (n + 1), j = idx - r * (n + 1);
-                if (r == l) continue;
-                double* t = T + (size_t)r * LD + j;
-                *t = __fma_rn(-colE[r], Tl[j], (j == e) ? 0.0 : *t);
+            {
+                // every other row, over the (k+1) x (n+1) elements in one flat
+                // pass (no idle lanes at row ends)
+                const int W = n + 1;
+                int r = tid / W, j = tid - (tid / W) * W;
+                const int dr = nt / W, dj = nt - dr * W;
+                for (int idx = tid; idx < (k + 1) * W; idx += nt) {
+                    if (r != l) {
+                        double* t = T + (size_t)r * LD + j;
+                        *t = __fma_rn(-colE[r], Tl[j], (j == e) ? 0.0 : *t);
+                    }
+                    r += dr;
+                    j += dj;
+                    if (j >= W) { j -= W; ++r; }
+                }
             }
             __syncthreads();
             ++iters;
