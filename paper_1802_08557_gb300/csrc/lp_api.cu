@@ -612,8 +612,10 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         g.count = (int32_t)kv.second.size();
         g.threads = kv.first.first;
         g.smem = kv.first.second;
+        // the one-warp form at its exact size (128-byte units): 13.5 KB, not
+        // 14 KB, is what lets 16 CTAs of 50 x 50 LPs share an SM
         for (int32_t k : kv.second)
-            g.smem_warp = std::max(g.smem_warp, (lpb::mixed_layout(hm[k], hn[k], hk[k]).total + 1023) / 1024 * 1024);
+            g.smem_warp = std::max(g.smem_warp, (lpb::mixed_layout(hm[k], hn[k], hk[k]).total + 127) / 128 * 128);
         order.insert(order.end(), kv.second.begin(), kv.second.end());
         h->mixed_groups.push_back(g);
         h->num_mixed += g.count;

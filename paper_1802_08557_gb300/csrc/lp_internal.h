@@ -106,14 +106,15 @@ __host__ __device__ inline size_t streamed_slot_bytes(int m, int n, int k) {
 }
 
 // Shared-memory layout of the mixed-precision kernel (after SmallLayout):
-// FP64 certification vectors, their FP32 copies (zf, rf: converted once per
-// refinement step instead of once per use) and per-row arrays first
-// (k-independent), then
-// the FP32 condensed tableau (R x LD floats, LD a multiple of 4), its
-// pivot-column copy and the column labels.
+// FP64 certification vectors (x_B; y, which also holds the ray of an
+// unbounded LP; the residual), the FP32 copy zf of the vector being refined
+// (converted once per refinement step instead of once per use) and per-row
+// arrays first (k-independent), then the FP32 condensed tableau (R x LD
+// floats, LD a multiple of 4), its pivot-column copy colE (after the simplex:
+// the FP32 copy of the residual) and the column labels.
 struct MixedLayout {
     int R, LD;
-    size_t xb, yv, dv, res, zf, rf, row_var, neg, spos, slist, nbl;  // k-independent
+    size_t scal, xb, yv, res, zf, row_var, neg, spos, slist, nbl;  // k-independent
     size_t T, colE, col_var;                           // k-dependent
     size_t total;
 };
@@ -124,12 +125,11 @@ __host__ __device__ inline MixedLayout mixed_layout(int m, int n, int k) {
     L.LD = (n + k + 1 + 3) & ~3;  // 16-byte rows for the quad update
     const size_t mn = (size_t)(m > n ? m : n);
     size_t o = 0;
+    L.scal = o;    o += 32;  // broadcast scalars (objective, ray slope, Farkas gap)
     L.xb = o;      o += align16((size_t)m * 8);
     L.yv = o;      o += align16((size_t)m * 8);
-    L.dv = o;      o += align16((size_t)m * 8);
     L.res = o;     o += align16(mn * 8);
     L.zf = o;      o += align16((size_t)m * 4);
-    L.rf = o;      o += align16((size_t)m * 4);
     L.row_var = o; o += align16((size_t)m * 4);
     L.neg = o;     o += align16((size_t)m * 4);
     L.spos = o;    o += align16((size_t)m * 4);

@@ -221,12 +221,15 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
     const int lane = g.lane, warp = g.warp;
 
     const MixedLayout L0 = mixed_layout(m, n, 0);
+    double* scal = reinterpret_cast<double*>(big + L0.scal);  // values broadcast from warp 0
+    double& s_obj = scal[0];
+    double& s_cd = scal[1];
+    double& s_gamma = scal[2];
     double* xb = reinterpret_cast<double*>(big + L0.xb);
     double* yv = reinterpret_cast<double*>(big + L0.yv);
-    double* dv = reinterpret_cast<double*>(big + L0.dv);
+    double* dv = yv;  // the ray of an unbounded LP; y is only refined for optimal and infeasible ones
     double* res = reinterpret_cast<double*>(big + L0.res);
     float* zf = reinterpret_cast<float*>(big + L0.zf);  // FP32 copy of the vector being refined
-    float* rf = reinterpret_cast<float*>(big + L0.rf);  // FP32 copy of its residual
     int* row_var = reinterpret_cast<int*>(big + L0.row_var);
     int* neg = reinterpret_cast<int*>(big + L0.neg);
     int* spos = reinterpret_cast<int*>(big + L0.spos);
@@ -268,6 +271,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
     tb.row_var = row_var;
     tb.LD = L.LD;
     const int LD = L.LD;
+    float* rf = tb.colE;  // FP32 copy of the certificate's residual (colE is dead after the simplex)
     float* T = tb.T;  // the tableau is written through several pointers: no restrict
     int Cvar = n + k;
 
@@ -723,7 +727,6 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
         for (int i = tid; i < m; i += nt) bad += (dv[i] < -mp.cert_tol * fmax(1.0, dmax)) ? 1u : 0u;
         g.count_min(bad, 0u, bad, dummy);
         // objective increase along the ray (warp 0, fixed order)
-        __shared__ double s_cd;
         if (warp == 0) {
             double part = 0.0;
             for (int t = lane; t < s; t += 32) {
@@ -851,7 +854,6 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
             for (int t = tid; t < k; t += nt) yneg = fmax(yneg, yv[neg[t]]);
             const double ymax_neg = block_absmax(g, yneg);
             g.count_min(bad, 0u, bad, dummy);
-            __shared__ double s_gamma;
             if (warp == 0) {
                 double part = 0.0;
                 for (int c = lane; c < m; c += 32) part = __fma_rn(-bv[c], yv[c], part);
@@ -916,7 +918,6 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
             }
         }
     }
-    __shared__ double s_obj;
     if (warp == 0) {
         double part = 0.0;
         for (int t = lane; t < s; t += 32) {
