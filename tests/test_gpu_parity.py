@@ -301,3 +301,23 @@ def test_solve_host_equals_create_solve_results(prec):
                               opts=opts, chunks=chunks)
             for key, v in (("status", st), ("iters", it), ("obj", ob), ("x", x), ("y", y)):
                 np.testing.assert_array_equal(v, ref[key], err_msg=f"{key} chunks={chunks}")
+
+
+def test_solve_host_reports_errors_of_a_later_chunk():
+    """A non-finite entry in the last chunk: lp_solve_host returns LPB_EINVAL
+    (from that chunk's create) after solving the earlier chunks, releases
+    everything, and a later call on good data still works."""
+    batch = W.mixed_sign_dense(400, 10, 8, start=5)
+    A = batch.A.copy()
+    A[-1] = np.inf
+    N = batch.num_lps
+    st, it, ob = np.zeros(N, np.int32), np.zeros(N, np.int32), np.zeros(N)
+    x = np.zeros(int(batch.n.astype(np.int64).sum()))
+    with pytest.raises(lpb.LPBError) as e:
+        lpb.lp_solve_host(batch.m, batch.n, batch.a_off, A, batch.b_off, batch.b, batch.c_off, batch.c,
+                          st, it, ob, x, chunks=4)
+    assert e.value.code == lpb.LPB_EINVAL
+    lpb.lp_solve_host(batch.m, batch.n, batch.a_off, batch.A, batch.b_off, batch.b, batch.c_off, batch.c,
+                      st, it, ob, x, chunks=4)
+    ref = gpu_solve(batch)
+    np.testing.assert_array_equal(ob, ref["obj"])
