@@ -141,11 +141,13 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(const GemmArgs g)
                 } else if (kEpi == kEpiBias) {
                     g.C[ci] = v + g.bias[col];
                 } else if (kEpi == kEpiBiasReLU) {
+                    // (inference: no pre-activation and no transposed copy,
+                    // which only the backward pass reads)
                     v = v + g.bias[col];
-                    g.C[ci] = v;
+                    if (g.C) g.C[ci] = v;
                     const __nv_bfloat16 h = __float2bfloat16_rn(fmaxf(v, 0.0f));
                     g.hbf[(size_t)row * g.ldh + col] = h;
-                    g.hbfT[(size_t)col * g.ldt + row] = h;
+                    if (g.hbfT) g.hbfT[(size_t)col * g.ldt + row] = h;
                 } else {  // kEpiMaskGrad
                     v = (g.pre[ci] > 0.0f) ? v : 0.0f;
                     g.C[ci] = v;
@@ -164,11 +166,21 @@ cudaError_t gemm(const GemmArgs& a, cudaStream_t s) {
 }
 
 // x (FP32 [batch x n_in]) -> (x - mean) * inv_std as BF16, [batch x ld] and
-// transposed [n_in x ldT]; padding columns/rows were zeroed at allocation and
-// rows batch..ldT-1 of the transposed copy are zeroed here.
+// transposed [n_in x ldT] (xbT null: inference, no transposed copy); padding
+// columns/rows were zeroed at allocation and rows batch..ldT-1 of the
+// transposed copy are zeroed here.
 __global__ void features_kernel(const float* __restrict__ x, int batch, int n_in, const float* __restrict__ mean,
                                 const float* __restrict__ inv_std, __nv_bfloat16* __restrict__ xb, int ld,
                                 __nv_bfloat16* __restrict__ xbT, int ldT) {
+    if (!xbT) {
+        const int64_t total = (int64_t)batch * n_in;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const int r = (int)(e / n_in), c = (int)(e - (int64_t)r * n_in);
+            xb[(size_t)r * ld + c] = __float2bfloat16_rn((x[e] - mean[c]) * inv_std[c]);
+        }
+        return;
+    }
     const int64_t total = (int64_t)ldT * n_in;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / n_in), c = (int)(e - (int64_t)r * n_in);
@@ -367,20 +379,23 @@ cudaError_t mlp_refresh_bf16(MlpModel* m, cudaStream_t s) {
 cudaError_t mlp_forward(MlpModel* m, const float* x, int batch, float* logits, cudaStream_t s) {
     cudaError_t e;
     const int bT = pad_to(batch, kPadK);
+    const bool infer = logits != nullptr;  // only the BF16 activations and the logits are written
     features_kernel<<<grid_for((int64_t)bT * m->n_in), 256, 0, s>>>(x, batch, m->n_in, m->mean, m->inv_std, m->xb,
-                                                                      m->L[0].in_pad, m->xbT, bT);
+                                                                      m->L[0].in_pad, infer ? nullptr : m->xbT, bT);
     if ((e = cudaGetLastError())) return e;
     GemmArgs g{};
     // layer 1
     g.A = m->xb; g.lda = m->L[0].in_pad; g.B = m->L[0].Wb; g.ldb = m->L[0].in_pad;
-    g.M = batch; g.N = m->h1; g.K = m->L[0].in_pad; g.C = m->a1; g.ldc = m->h1; g.bias = m->L[0].b;
-    g.hbf = m->h1b; g.ldh = m->L[1].in_pad; g.hbfT = m->h1bT; g.ldt = bT;
+    g.M = batch; g.N = m->h1; g.K = m->L[0].in_pad; g.C = infer ? nullptr : m->a1; g.ldc = m->h1;
+    g.bias = m->L[0].b;
+    g.hbf = m->h1b; g.ldh = m->L[1].in_pad; g.hbfT = infer ? nullptr : m->h1bT; g.ldt = bT;
     if ((e = gemm<kEpiBiasReLU>(g, s))) return e;
     // layer 2
     g = GemmArgs{};
     g.A = m->h1b; g.lda = m->L[1].in_pad; g.B = m->L[1].Wb; g.ldb = m->L[1].in_pad;
-    g.M = batch; g.N = m->h2; g.K = m->L[1].in_pad; g.C = m->a2; g.ldc = m->h2; g.bias = m->L[1].b;
-    g.hbf = m->h2b; g.ldh = m->L[2].in_pad; g.hbfT = m->h2bT; g.ldt = bT;
+    g.M = batch; g.N = m->h2; g.K = m->L[1].in_pad; g.C = infer ? nullptr : m->a2; g.ldc = m->h2;
+    g.bias = m->L[1].b;
+    g.hbf = m->h2b; g.ldh = m->L[2].in_pad; g.hbfT = infer ? nullptr : m->h2bT; g.ldt = bT;
     if ((e = gemm<kEpiBiasReLU>(g, s))) return e;
     // layer 3
     g = GemmArgs{};
@@ -388,7 +403,7 @@ cudaError_t mlp_forward(MlpModel* m, const float* x, int batch, float* logits, c
     g.M = batch; g.N = m->n_out; g.K = m->L[2].in_pad; g.C = logits ? logits : m->z; g.ldc = m->n_out;  // logits: inference
     g.bias = m->L[2].b;
     if ((e = gemm<kEpiBias>(g, s))) return e;
-    if (bT > batch) {
+    if (!infer && bT > batch) {
         zero_cols_kernel<<<grid_for((int64_t)m->h1 * (bT - batch)), 256, 0, s>>>(m->h1bT, m->h1, bT, batch, bT);
         zero_cols_kernel<<<grid_for((int64_t)m->h2 * (bT - batch)), 256, 0, s>>>(m->h2bT, m->h2, bT, batch, bT);
         zero_cols_kernel<<<grid_for((int64_t)m->h2 * (bT - batch)), 256, 0, s>>>(m->g2bT, m->h2, bT, batch, bT);
