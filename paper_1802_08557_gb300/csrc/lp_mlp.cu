@@ -70,6 +70,31 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Epilogue of one output element (row, col) with accumulator v.
+template <int kEpi>
+__device__ __forceinline__ void epilogue(const GemmArgs& g, int row, int col, float v) {
+    const size_t ci = (size_t)row * g.ldc + col;
+    if (kEpi == kEpiStore) {
+        g.C[ci] = v;
+    } else if (kEpi == kEpiBias) {
+        g.C[ci] = v + g.bias[col];
+    } else if (kEpi == kEpiBiasReLU) {
+        // (inference: no pre-activation and no transposed copy,
+        // which only the backward pass reads)
+        v = v + g.bias[col];
+        if (g.C) g.C[ci] = v;
+        const __nv_bfloat16 h = __float2bfloat16_rn(fmaxf(v, 0.0f));
+        g.hbf[(size_t)row * g.ldh + col] = h;
+        if (g.hbfT) g.hbfT[(size_t)col * g.ldt + row] = h;
+    } else {  // kEpiMaskGrad
+        v = (g.pre[ci] > 0.0f) ? v : 0.0f;
+        g.C[ci] = v;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        g.hbf[(size_t)row * g.ldh + col] = h;
+        g.hbfT[(size_t)col * g.ldt + row] = h;
+    }
+}
+
 template <int kEpi>
 __global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(const GemmArgs g) {
     __shared__ __align__(16) __nv_bfloat16 As[kBM][kBK + 8];
@@ -133,35 +158,112 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_nt_kernel(const GemmArgs g)
             for (int r = 0; r < 4; ++r) {
                 const int row = m0 + wm + i * 16 + gq + ((r & 2) ? 8 : 0);
                 const int col = n0 + wn + j * 8 + 2 * tq + (r & 1);
-                if (row >= g.M || col >= g.N) continue;
-                float v = acc[i][j][r];
-                const size_t ci = (size_t)row * g.ldc + col;
-                if (kEpi == kEpiStore) {
-                    g.C[ci] = v;
-                } else if (kEpi == kEpiBias) {
-                    g.C[ci] = v + g.bias[col];
-                } else if (kEpi == kEpiBiasReLU) {
-                    // (inference: no pre-activation and no transposed copy,
-                    // which only the backward pass reads)
-                    v = v + g.bias[col];
-                    if (g.C) g.C[ci] = v;
-                    const __nv_bfloat16 h = __float2bfloat16_rn(fmaxf(v, 0.0f));
-                    g.hbf[(size_t)row * g.ldh + col] = h;
-                    if (g.hbfT) g.hbfT[(size_t)col * g.ldt + row] = h;
-                } else {  // kEpiMaskGrad
-                    v = (g.pre[ci] > 0.0f) ? v : 0.0f;
-                    g.C[ci] = v;
-                    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-                    g.hbf[(size_t)row * g.ldh + col] = h;
-                    g.hbfT[(size_t)col * g.ldt + row] = h;
-                }
+                if (row < g.M && col < g.N) epilogue<kEpi>(g, row, col, acc[i][j][r]);
             }
 }
 
+// The same product for large grids: 128 x 128 tiles over 8 warps (each
+// 64 x 32), operands staged by 16-byte cp.async in two stages (the next K
+// tile loads while the current one multiplies), fragments by ldmatrix.x4
+// from rows padded to 80 bytes (no bank conflicts).  Each output element
+// gets the same mma.sync sequence (K ascending in steps of 16) as in
+// gemm_nt_kernel, so the results are bit-identical.
+constexpr int kTM = 128, kTN = 128, kTK = 32, kTThreads = 256, kTLd = kTK + 8;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    const int bytes = valid ? 16 : 0;  // 0: the 16 bytes are zero-filled
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void* smem) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+template <int kEpi>
+__global__ void __launch_bounds__(kTThreads) gemm_nt_tiled_kernel(const GemmArgs g) {
+    __shared__ __align__(16) __nv_bfloat16 As[2][kTM][kTLd];
+    __shared__ __align__(16) __nv_bfloat16 Bs[2][kTN][kTLd];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+    const int gq = lane >> 2, tq = lane & 3;
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+    // one stage: 128 rows x 4 chunks of 16 bytes per operand, 2 chunks of
+    // each per thread; rows past M (N) are zero-filled from a valid address
+    auto load = [&](int st, int k0) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int idx = tid + c * kTThreads;
+            const int row = idx >> 2, col = (idx & 3) * 8;
+            const bool va = m0 + row < g.M, vb = n0 + row < g.N;
+            cp_async16(&As[st][row][col], g.A + (size_t)(va ? m0 + row : 0) * g.lda + k0 + col, va);
+            cp_async16(&Bs[st][row][col], g.B + (size_t)(vb ? n0 + row : 0) * g.ldb + k0 + col, vb);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const int nk = g.K / kTK;
+    load(0, 0);
+    for (int kt = 0; kt < nk; ++kt) {
+        const int st = kt & 1;
+        if (kt + 1 < nk) {
+            load(st ^ 1, (kt + 1) * kTK);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kTK; kk += 16) {
+            uint32_t a[4][4], b[2][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                ldmatrix_x4(a[i], &As[st][wm + i * 16 + (lane & 7) + ((lane >> 3) & 1) * 8][kk + (lane >> 4) * 8]);
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj)
+                ldmatrix_x4(b[jj], &Bs[st][wn + jj * 16 + (lane & 7) + (lane >> 4) * 8][kk + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t bj[2] = {b[j >> 1][(j & 1) * 2], b[j >> 1][(j & 1) * 2 + 1]};
+                    mma_bf16(acc[i][j], a[i], bj);
+                }
+        }
+        __syncthreads();  // this stage is reloaded two tiles later
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int row = m0 + wm + i * 16 + gq + ((r & 2) ? 8 : 0);
+                const int col = n0 + wn + j * 8 + 2 * tq + (r & 1);
+                if (row < g.M && col < g.N) epilogue<kEpi>(g, row, col, acc[i][j][r]);
+            }
+}
+
+// 128 x 128 tiles when they give at least one per SM, else 64 x 64 (small
+// products, e.g. the weight gradients of one training batch): same results.
 template <int kEpi>
 cudaError_t gemm(const GemmArgs& a, cudaStream_t s) {
-    const dim3 grid((a.N + kBN - 1) / kBN, (a.M + kBM - 1) / kBM);
-    gemm_nt_kernel<kEpi><<<grid, kGemmThreads, 0, s>>>(a);
+    const int64_t big_tiles = (int64_t)((a.N + kTN - 1) / kTN) * ((a.M + kTM - 1) / kTM);
+    if (big_tiles >= 152) {
+        const dim3 grid((a.N + kTN - 1) / kTN, (a.M + kTM - 1) / kTM);
+        gemm_nt_tiled_kernel<kEpi><<<grid, kTThreads, 0, s>>>(a);
+    } else {
+        const dim3 grid((a.N + kBN - 1) / kBN, (a.M + kBM - 1) / kBM);
+        gemm_nt_kernel<kEpi><<<grid, kGemmThreads, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -72,6 +72,31 @@ def test_forward_matches_oracle(batch):
     net.close()
 
 
+def test_large_batch_forward_tiled_kernel():
+    """Batches whose 128 x 128 tiles fill the GPU take the tiled GEMM (cp.async
+    stages, ldmatrix fragments): logits match the oracle, and bit for bit the
+    small-tile kernel's on the same rows (forwarded in pieces too small for the
+    tiled kernel; each row's result does not depend on the batch)."""
+    import torch
+    net, params = _net_with_oracle_params(SIZES, seed=5, max_batch=512)
+    batch = 6000
+    x, _ = _data(batch, SIZES, seed=17)
+    dx = _dev(x)
+    whole = torch.empty((batch, SIZES[-1]), dtype=torch.float32, device="cuda")
+    net.forward(dx, whole)
+    pieces = torch.empty_like(whole)
+    for r0 in range(0, batch, 1000):
+        net.forward(dx[r0:r0 + 1000], pieces[r0:r0 + 1000])
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(whole.cpu().numpy(), pieces.cpu().numpy())
+    want, _ = omlp.forward(params, x)
+    got = whole.cpu().numpy()
+    scale = float(np.std(want)) + 1e-6
+    assert np.max(np.abs(got - want)) <= 2e-2 * scale
+    assert np.mean(np.abs(got - want)) <= 1e-3 * scale
+    net.close()
+
+
 @pytest.mark.parametrize("batch", [64, 250])
 def test_gradients_match_oracle(batch):
     net, params = _net_with_oracle_params(SIZES, seed=7, max_batch=256)
