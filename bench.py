@@ -37,6 +37,13 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
 # HBM bandwidth of a GB300 measured with a STREAM-style copy (read + write bytes)
 HBM_PEAK_GBS = 6784.5
+# DRAM bytes per LP (read + write) from ncu captures of the kernels as they are
+# now, for the roofline's `traffic` (scaled to a launch by the LPs it solves):
+# profiles/mixed_warp_kernel__dense50x50_20k__ncu.md (k = 0 group, 15629 LPs:
+# 349.4 MB + 12.4 MB) and profiles/hyperbox_tile_kernel__dirs1M_dim28__ncu.md
+# (2^20 LPs in R^28: 234.9 MB + 7.6 MB).
+MIXED_DRAM_BYTES_PER_LP = (349.375232e6 + 12.406528e6) / 15629
+HYPERBOX_DRAM_BYTES_PER_LP_DIM28 = (234.9e6 + 7.6e6) / (1 << 20)
 # dense BF16 tensor throughput of a GB300 measured with a cuBLAS GEMM (burst)
 BF16_PEAK_TFLOPS = 1958.9
 L2_BYTES = 129 * 1024 * 1024
@@ -318,7 +325,11 @@ def run_ours(args):
         mixed_name = "mixed_warp_kernel" if mixed_threads == {32} else "mixed_kernel"
         roofline = {"bound": "alu", "kernel": mixed_name, "achieved": achieved,
                     "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP32_PEAK_GFLOPS,
-                    "traffic": None, "kernel_ms": kernel_ms, "fallback_ms": fallback_ms,
+                    "traffic": MIXED_DRAM_BYTES_PER_LP * N if mixed_name == "mixed_warp_kernel" else None,
+                    "traffic_note": "DRAM bytes per step: the ncu capture's read+write per LP (A, b, c once, "
+                                    "outputs) x the step's LPs; algorithmic bytes of the inputs alone: "
+                                    f"{in_bytes:.4g}",
+                    "kernel_ms": kernel_ms, "fallback_ms": fallback_ms,
                     "peak_note": "FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz",
                     "work": "sum over LPs of reported pivots x (m+1)(n+1) FMAs (FP32 pivots of certified LPs; "
                             "the FP64 re-solve's pivots stand in for those of uncertified LPs; FP64 certificate "
@@ -354,7 +365,8 @@ def run_ours(args):
             "ms_per_step": hb_ms,
             "roofline": {"bound": "alu", "kernel": "hyperbox_tile_kernel",
                          "achieved": flops / (hb_ms * 1e-3) / 1e9, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": flops / (hb_ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS, "traffic": None,
+                         "frac": flops / (hb_ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
+                         "traffic": HYPERBOX_DRAM_BYTES_PER_LP_DIM28 * hb_num if hb_dim == 28 else None,
                          "hbm_gbs": bytes_ / (hb_ms * 1e-3) / 1e9, "hbm_peak_gbs": HBM_PEAK_GBS,
                          "hbm_frac": bytes_ / (hb_ms * 1e-3) / 1e9 / HBM_PEAK_GBS,
                          "work": "one FP64 FMA per direction coordinate (the FP64 pipe binds before HBM: "
