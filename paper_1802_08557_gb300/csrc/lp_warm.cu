@@ -137,10 +137,17 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
         if (negb) { ok = false; break; }
         for (int j = tid; j <= n; j += nt) col_var[j] = j - 1;  // column j holds structural j-1 (0: RHS)
         for (int r = tid; r < k; r += nt) row_var[r] = n + r;   // slack of restricted row r
-        for (int r = 0; r < k; ++r) {
-            const double* Ai = A + (size_t)rows[r] * n;
-            double* Tr = T + (size_t)r * LD;
-            for (int j = tid; j <= n; j += nt) Tr[j] = (j == 0) ? bv[rows[r]] : Ai[j - 1];
+        {
+            // rows R of [b | A] in one flat pass (all loads of a thread in flight)
+            const int W = n + 1;
+            int r = tid / W, j = tid - (tid / W) * W;
+            const int dr = nt / W, dj = nt - dr * W;
+            for (int idx = tid; idx < k * W; idx += nt) {
+                T[(size_t)r * LD + j] = (j == 0) ? bv[rows[r]] : A[(size_t)rows[r] * n + j - 1];
+                r += dr;
+                j += dj;
+                if (j >= W) { j -= W; ++r; }
+            }
         }
         {
             double* To = T + (size_t)k * LD;
