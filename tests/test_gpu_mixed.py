@@ -135,9 +135,9 @@ def test_mixed_large_lps_and_their_fp64_streamed_re_solve():
     """FP32 tableaux above one CTA's shared memory run in the streamed mixed
     kernel; LPs whose FP64 tableau exceeds one CTA and that the mixed path does
     not certify (here: an entry outside the FP32 range) are re-solved by the
-    FP64 streamed kernel, whose answer equals the FP64 path's (cluster
-    kernel) bit for bit.  Every status equals the FP64 path's, every optimal
-    objective agrees within 1e-9."""
+    FP64 cluster kernel, whose answer equals the FP64 path's bit for bit.
+    Feasible and infeasible phase-I LPs are among them.  Every status equals
+    the FP64 path's, every optimal objective agrees within 1e-9."""
     rng = np.random.default_rng(5)
     lps, forced = [], []
     for t in range(8):
@@ -146,6 +146,12 @@ def test_mixed_large_lps_and_their_fp64_streamed_re_solve():
         A = rng.uniform(0.0, 1.0, (m, n))
         b = rng.uniform(1.0, 100.0, m)
         c = rng.uniform(0.0, 1.0, n)
+        if t in (2, 3, 6, 7):
+            # rows with b_i < 0 (phase I): feasible when those rows of A are
+            # negated too (t = 2, 6), infeasible with A >= 0 (t = 3, 7)
+            b[::7] = -rng.uniform(0.5, 5.0, b[::7].shape)
+            if t in (2, 6):
+                A[::7] = -A[::7]
         if t % 2 == 1:
             A[0, 0] = 2.0 ** 61  # outside the FP32 range: straight to the FP64 re-solve
         forced.append(t % 2 == 1)
@@ -161,6 +167,7 @@ def test_mixed_large_lps_and_their_fp64_streamed_re_solve():
     assert kinds == [0, 4], kinds
     assert g["plan"]["num_fallback"] >= sum(forced)
     np.testing.assert_array_equal(g["status"], f["status"])
+    assert set(f["status"][[3, 7]]) == {1} and f["status"][2] == 0 and f["status"][6] == 0
     opt = f["status"] == 0
     assert opt.any()
     np.testing.assert_allclose(g["obj"][opt], f["obj"][opt], rtol=OBJ_RTOL, atol=OBJ_RTOL)
