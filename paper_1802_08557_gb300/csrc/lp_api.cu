@@ -701,6 +701,9 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         h->mp.cert_tol = 1e-9;
         h->mp.conv_tol = std::ldexp(1.0, -43);  // componentwise backward error ~1.1e-13
         h->mp.fwd_tol = 1e-12;
+        // a component at or near 0 (a degenerate basis, a ray) is accurate to
+        // 1e-15 max|z| at best, not 1e-12 of itself
+        h->mp.fwd_floor = 1e-3;
         h->mp.max_refine = 6;
         h->fb_smem = (h->fb_smem + 1023) / 1024 * 1024;
         if ((err = alloc(h, &h->fb_queue, (size_t)h->num_fsmall, s)) || (err = alloc(h, &h->fb_len, 1, s)) ||

@@ -151,7 +151,8 @@ struct MixedParams {
     float eps_opt32, eps_piv32, eps_feas32;
     double cert_tol;     // primal (x scaled by max(1,|b|_inf)) and dual feasibility tolerance
     double conv_tol;     // refinement: every residual <= conv_tol * (|rhs| + |B||z|) ...
-    double fwd_tol;      // ... and the last correction <= fwd_tol * max(|z_i|, 1e-8 max|z|)
+    double fwd_tol;      // ... and the last correction <= fwd_tol * max(|z_i|, fwd_floor * max|z|)
+    double fwd_floor;    // (components far below the largest are judged against it)
     int32_t max_refine;  // refinement steps per vector
 };
 

@@ -517,7 +517,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
     // the FP32 one of the tableau.  Converged when the residual the last
     // correction was computed from is within conv_tol of |rhs_c| +
     // sum |B_c,i| |z_i| (backward error) and that correction moved no
-    // component by more than fwd_tol of max(|z_i|, 1e-8 max|z|) (forward
+    // component by more than fwd_tol of max(|z_i|, fwd_floor max|z|) (forward
     // error: an ill-conditioned basis stalls and is left to the FP64 re-solve).
     // The tolerance tests run in FP32 on magnitudes: |a| of A by integer
     // operations (f64_abs_to_f32_trunc; A is range-checked), z and r through
@@ -530,7 +530,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
             zloc = (abskey(z[i]) > abskey(zloc)) ? z[i] : zloc;
             zf[i] = fabs32(__double2float_rn(z[i]));
         }
-        const float zfloor = 1e-8f * __double2float_ru(block_absmax(g, zloc));  // barrier: zf complete
+        const float zfloor = (float)mp.fwd_floor * __double2float_ru(block_absmax(g, zloc));  // barrier: zf complete
         for (int it = 0; it <= mp.max_refine; ++it) {
             unsigned bad = 0;
             for (int c = tid; c < m; c += nt) {
@@ -603,7 +603,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
             yloc = (abskey(yv[c]) > abskey(yloc)) ? yv[c] : yloc;
             zf[c] = __double2float_rn(yv[c]);  // y in FP32 (signed: the dual screen uses it)
         }
-        const float yfloor = 1e-8f * __double2float_ru(block_absmax(g, yloc));  // barrier: zf complete
+        const float yfloor = (float)mp.fwd_floor * __double2float_ru(block_absmax(g, yloc));  // barrier: zf complete
         for (int it = 0; it <= mp.max_refine; ++it) {
             // rho_i = c_(v_i) - y^T col(v_i) for each basic variable (by tableau row)
             // (split over P lanes per basic variable, rows c = q, q + P, ...)
