@@ -538,7 +538,11 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
             if (need <= queue_smem_cap) {
                 ++h->num_fsmall;
                 h->fb_smem = std::max(h->fb_smem, need);
-                h->fb_threads = std::max(h->fb_threads, pick_threads(hm[k], hn[k], hk[k], 0));  // FP64 kernel's own
+                // the re-solve runs after every mixed launch, over ~1% of the
+                // LPs: its time is one LP's latency, so 4x the FP64 kernel's own
+                // thread count (50x50: 256, re-solve 0.77 -> 0.66 ms per 1e5)
+                h->fb_threads = std::max(h->fb_threads, std::min(4 * pick_threads(hm[k], hn[k], hk[k], 0),
+                                                                 lpb::kMaxThreads));
             } else {
                 ++h->num_fbig;
                 h->fbig_slot_bytes = std::max(h->fbig_slot_bytes, lpb::streamed_slot_bytes(hm[k], hn[k], hk[k]));
