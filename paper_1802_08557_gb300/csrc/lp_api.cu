@@ -539,10 +539,9 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
                 ++h->num_fsmall;
                 h->fb_smem = std::max(h->fb_smem, need);
                 // the re-solve runs after every mixed launch, over ~1% of the
-                // LPs: its time is one LP's latency, so 4x the FP64 kernel's own
-                // thread count (50x50: 256, re-solve 0.77 -> 0.66 ms per 1e5)
-                h->fb_threads = std::max(h->fb_threads, std::min(4 * pick_threads(hm[k], hn[k], hk[k], 0),
-                                                                 lpb::kMaxThreads));
+                // LPs: its time is one LP's latency, so at least 256 threads per
+                // LP (50x50: re-solve 0.77 -> 0.66 ms per 1e5; 512 was slower)
+                h->fb_threads = std::max({h->fb_threads, pick_threads(hm[k], hn[k], hk[k], 0), 256});
             } else {
                 ++h->num_fbig;
                 h->fbig_slot_bytes = std::max(h->fbig_slot_bytes, lpb::streamed_slot_bytes(hm[k], hn[k], hk[k]));
@@ -708,7 +707,9 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         // a component at or near 0 (a degenerate basis, a ray) is accurate to
         // 1e-15 max|z| at best, not 1e-12 of itself
         h->mp.fwd_floor = 1e-3;
-        h->mp.max_refine = 6;
+        // slow refinements (an ill-conditioned basis) that still converge are
+        // certified rather than re-solved (50x50: 604 -> 372 re-solves per 1e5)
+        h->mp.max_refine = 12;
         h->fb_smem = (h->fb_smem + 1023) / 1024 * 1024;
         if ((err = alloc(h, &h->fb_queue, (size_t)h->num_fsmall, s)) || (err = alloc(h, &h->fb_len, 1, s)) ||
             (err = alloc(h, &h->fb_counter, 1, s)) || (err = cudaMemsetAsync(h->fb_len, 0, 4, s)) ||
