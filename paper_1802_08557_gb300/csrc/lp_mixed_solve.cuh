@@ -463,7 +463,7 @@ __device__ __forceinline__ void mixed_solve(G& g, const DeviceBatch& B, const To
             const int p = (c < m) ? spos[c] : 0;
             int tot;
             const int pos = cnt + g.prefix_count(p > 0, tot);
-            if (p > 0) nbl[pos] = (p << 16) | c;
+            if (p > 0) nbl[pos] = (int)(((unsigned)p << 16) | (unsigned)c);  // p <= n + k, c < m: 16 bits each
             cnt += tot;
         }
         g.sync();
