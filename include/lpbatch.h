@@ -169,11 +169,13 @@ lpb_err lp_batch_results(lp_batch *h, int32_t *status, int32_t *iters, double *o
 /*
  * One call from host buffers to host results, with the copy of the inputs
  * overlapped with the solve: the batch is split into `chunks` contiguous
- * ranges of LPs (0 = 4 for 4096 LPs or more, else 1), each created and solved
- * as its own batch on its own internal stream, so that one range's inputs are
- * copied while the previous one solves; then every range's results are read.
- * Section 4.3 of the paper splits a batch over CUDA streams so that copies
- * overlap kernels; this is the same idea inside one call.
+ * ranges of LPs (0 = one per 256 MiB of A, b and c, at most 8), each created and solved
+ * as its own batch on its own internal stream.  The ranges' input copies run
+ * one after another, each range's solve starts when its copy and input check
+ * end, and the host waits for nothing until every solve is enqueued; then the
+ * input checks and the results are read.  Section 4.3 of the paper splits a
+ * batch over CUDA streams so that copies overlap kernels; this is the same
+ * idea inside one call.
  *
  *  num_lps, m, n, a_off, A, a_len, b_off, b, b_len, c_off, c, c_len, opts:
  *                 as for lp_batch_create, all in HOST memory.  Each range
@@ -187,8 +189,11 @@ lpb_err lp_batch_results(lp_batch *h, int32_t *status, int32_t *iters, double *o
  * lp_batch_solve + lp_batch_results on the whole batch with the same opts (an
  * LP's arithmetic does not depend on the batch it is solved in).  Synchronous:
  * returns when the results are in the host buffers.  Errors: LPB_EINVAL for
- * bad arguments (nothing launched) and every error of lp_batch_create /
- * lp_batch_solve / lp_batch_results; all device memory is released on return.
+ * bad arguments (nothing launched); LPB_EINVAL for a non-finite entry of A, b
+ * or c, found after the solves (the device copy of such an entry is zeroed
+ * before any solve reads it) and then no result buffer is written; every
+ * error of lp_batch_create / lp_batch_solve / lp_batch_results.  All device
+ * memory is released on return.
  */
 lpb_err lp_solve_host(int32_t num_lps, const int32_t *m, const int32_t *n,
                       const int64_t *a_off, const double *A, int64_t a_len,

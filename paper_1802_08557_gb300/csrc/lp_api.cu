@@ -168,6 +168,9 @@ struct lp_batch {
     int32_t* fb_len = nullptr;
     int32_t* fb_counter = nullptr;
     int32_t* diag = nullptr;  // 8 int32: internal-consistency failures of the last solve
+    // count of non-finite inputs when the check was left for the caller to
+    // read (lp_solve_host); null when create read it
+    unsigned long long* d_bad = nullptr;
     // internal streams: the launch groups of a solve run concurrently on them
     cudaStream_t lanes[kLanes] = {};
     cudaEvent_t ev_fork = nullptr;
@@ -391,13 +394,22 @@ const char* lpb_strerror(lpb_err e) {
 
 const char* lpb_last_error(void) { return g_last_error.c_str(); }
 
-lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const int32_t* n,
-                        const int64_t* a_off, const double* A, int64_t a_len,
-                        const int64_t* b_off, const double* b, int64_t b_len,
-                        const int64_t* c_off, const double* c, int64_t c_len,
-                        int32_t ptr_kind, const lp_batch_opts* opts, void* stream) {
+// lp_batch_create, with two more parameters for lp_solve_host: `copied`
+// (optional) is recorded on the stream right after the copies of A, b and c;
+// with `defer_check` (host inputs only) the call returns without waiting for
+// the stream, leaving the count of non-finite inputs in h->d_bad for the
+// caller to read after its solve (the check zeroes every such entry, so the
+// solve sees finite data).  Without it the call waits for the check and fails
+// on a non-finite entry.
+static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, const int32_t* n,
+                            const int64_t* a_off, const double* A, int64_t a_len,
+                            const int64_t* b_off, const double* b, int64_t b_len,
+                            const int64_t* c_off, const double* c, int64_t c_len,
+                            int32_t ptr_kind, const lp_batch_opts* opts, void* stream, cudaEvent_t copied,
+                            bool defer_check) {
     g_last_error.clear();
     if (!out) return fail(LPB_EINVAL, "out is NULL");
+    if (defer_check && ptr_kind != LPB_HOST) return fail(LPB_EINVAL, "a deferred input check needs host inputs");
     *out = nullptr;
     if (num_lps < 1) return fail(LPB_EINVAL, "num_lps < 1");
     if (!m || !n || !A || !b || !c) return fail(LPB_EINVAL, "m, n, A, b and c must be non-NULL");
@@ -489,16 +501,22 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         (err = cudaMemcpyAsync(dbv, b, (size_t)b_len * 8, kind, s)) ||
         (err = cudaMemcpyAsync(dcv, c, (size_t)c_len * 8, kind, s)))
         return bail_cuda(err, "copy of the LP data");
+    if (copied && (err = cudaEventRecord(copied, s))) return bail_cuda(err, "event record");
 
     h->d = lpb::DeviceBatch{dm, dn, da, db, dc, dx_off, dy_off, dA, dbv, dcv, dstatus, diters, dobj, dx, dy};
     h->d_order = dorder;
-    if ((err = lpb::launch_prepare(h->d, num_lps, a_len, b_len, c_len, dk, dbad, s)))
+    if (ptr_kind == LPB_DEVICE &&
+        ((err = lpb::launch_input_check(dA, a_len, dbv, b_len, dcv, c_len, dbad, s)) ||
+         (err = lpb::launch_count_negative_rhs(h->d, num_lps, dk, s))))
         return bail_cuda(err, "input check kernel");
     std::vector<int32_t> hk(num_lps);
     unsigned long long bad = 0;
     if (ptr_kind == LPB_HOST) {
-        // phase-I rows counted here while the copies and the input check run
-        // (the plan below overlaps them too); the check is read after the plan
+        // phase-I rows counted here while the copies run (the plan below
+        // overlaps them too); the input check is launched after the last
+        // upload of the plan, so that no host call of this function waits for
+        // a kernel (a kernel queued behind another stream's large grid can
+        // wait for most of that grid)
         for (int32_t k = 0; k < num_lps; ++k) {
             const double* bk = b + hb[k];
             int32_t cnt = 0;
@@ -630,8 +648,7 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         for (Group& g : h->mixed_groups) { g.gi = (int32_t)lens.size(); lens.push_back(g.count); }
         if (!lens.empty()) {
             if ((err = alloc(h, &h->group_len, lens.size(), s)) || (err = alloc(h, &h->group_counter, lens.size(), s)) ||
-                (err = cudaMemcpyAsync(h->group_len, lens.data(), lens.size() * 4, cudaMemcpyHostToDevice, s)) ||
-                (err = cudaStreamSynchronize(s)))
+                (err = cudaMemcpyAsync(h->group_len, lens.data(), lens.size() * 4, cudaMemcpyHostToDevice, s)))
                 return bail_cuda(err, "group counters");
         }
     }
@@ -686,6 +703,12 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
     h->streamed_offset = (int64_t)order.size();
     h->num_streamed = (int32_t)streamed.size();
     order.insert(order.end(), streamed.begin(), streamed.end());
+    // the last upload from pageable host memory, ahead of every memset and
+    // kernel of this function: such a copy may wait for the stream, and
+    // returns once its data is staged (so the host vectors may go out of
+    // scope before the copies run)
+    if ((err = cudaMemcpyAsync(dorder, order.data(), nl * 4, cudaMemcpyHostToDevice, s)))
+        return bail_cuda(err, "plan upload");
     if (h->num_streamed > 0) {
         int sms = 0;
         if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device)))
@@ -763,13 +786,31 @@ lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const
         if ((err = cudaStreamCreateWithFlags(&h->lanes[i], cudaStreamNonBlocking)) ||
             (err = cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming)))
             return bail_cuda(err, "stream creation");
-    if ((err = cudaMemcpyAsync(dorder, order.data(), nl * 4, cudaMemcpyHostToDevice, s)) ||
-        (ptr_kind == LPB_HOST && (err = cudaMemcpyAsync(&bad, dbad, sizeof bad, cudaMemcpyDeviceToHost, s))) ||
-        (err = lpb::fp64_kernels_prepare()) || (err = cudaStreamSynchronize(s)))
-        return bail_cuda(err, "plan upload");
+    if ((err = lpb::fp64_kernels_prepare())) return bail_cuda(err, "plan upload");
+    if (ptr_kind == LPB_HOST) {
+        if ((err = lpb::launch_input_check(dA, a_len, dbv, b_len, dcv, c_len, dbad, s)))
+            return bail_cuda(err, "input check kernel");
+        if (defer_check) {
+            h->d_bad = dbad;
+            *out = h;
+            return LPB_OK;
+        }
+        if ((err = cudaMemcpyAsync(&bad, dbad, sizeof bad, cudaMemcpyDeviceToHost, s)))
+            return bail_cuda(err, "input check");
+    }
+    if ((err = cudaStreamSynchronize(s))) return bail_cuda(err, "plan upload");
     if (bad) return bail(LPB_EINVAL, std::to_string(bad) + " non-finite entries in A, b or c");
     *out = h;
     return LPB_OK;
+}
+
+lpb_err lp_batch_create(lp_batch** out, int32_t num_lps, const int32_t* m, const int32_t* n,
+                        const int64_t* a_off, const double* A, int64_t a_len,
+                        const int64_t* b_off, const double* b, int64_t b_len,
+                        const int64_t* c_off, const double* c, int64_t c_len,
+                        int32_t ptr_kind, const lp_batch_opts* opts, void* stream) {
+    return create_batch(out, num_lps, m, n, a_off, A, a_len, b_off, b, b_len, c_off, c, c_len, ptr_kind, opts, stream,
+                        nullptr, false);
 }
 
 lpb_err lp_batch_solve(lp_batch* h, void* stream) {
@@ -1234,7 +1275,14 @@ lpb_err lp_solve_host(int32_t num_lps, const int32_t* m, const int32_t* n,
     if (!m || !n || !A || !b || !c) return fail(LPB_EINVAL, "m, n, A, b and c must be non-NULL");
     if (!status || !iters || !obj || !x) return fail(LPB_EINVAL, "status, iters, obj and x must be non-NULL");
     if (chunks < 0 || chunks > LPB_MAX_HOST_CHUNKS) return fail(LPB_EINVAL, "chunks must be in [0, LPB_MAX_HOST_CHUNKS]");
-    if (chunks == 0) chunks = num_lps >= 4096 ? 4 : 1;
+    if (chunks == 0) {
+        // one chunk per 256 MiB of input, at most 8: the first chunk's copy is
+        // the one not overlapped with a solve (1e5 dense 50 x 50 LPs, 2.08 GB
+        // from pinned memory at ~211 GB/s: 24.8 / 19.6 / 17.2 / 17.7 / 16.3 /
+        // 18.6 / 23.9 ms for 1 / 2 / 4 / 6 / 8 / 12 / 16 chunks)
+        const int64_t bytes = (a_len + b_len + c_len) * 8, per = int64_t(256) << 20;
+        chunks = (int32_t)std::min<int64_t>(8, std::max<int64_t>(1, (bytes + per - 1) / per));
+    }
     chunks = std::min(chunks, num_lps);
     // every LP's offsets (packed when NULL); each chunk passes the smallest
     // ranges of A, b and c that hold its LPs, with offsets rebased to them
@@ -1252,13 +1300,18 @@ lpb_err lp_solve_host(int32_t num_lps, const int32_t* m, const int32_t* n,
             return fail(LPB_EINVAL, "LP " + std::to_string(k) + ": offset out of range");
     }
     std::vector<cudaStream_t> streams(chunks, nullptr);
+    std::vector<cudaEvent_t> copied(chunks, nullptr);
     std::vector<lp_batch*> hs(chunks, nullptr);
     std::vector<int32_t> k0s(chunks + 1);
     std::vector<int64_t> xs(chunks), ys(chunks);
     lpb_err e = LPB_OK;
     int64_t px = 0, py = 0;
     for (int32_t i = 0; i <= chunks; ++i) k0s[i] = (int32_t)((int64_t)num_lps * i / chunks);
-    // chunk i+1 is created (its inputs copied) while chunk i solves
+    // Every chunk is created and its solve enqueued without waiting for the
+    // device: the copies run back to back (chunk i+1's copy waits for chunk
+    // i's, so the first chunk has the bandwidth to itself), each solve starts
+    // when its chunk's copy and input check end, and the input checks are
+    // read after the solves.
     for (int32_t i = 0; i < chunks && e == LPB_OK; ++i) {
         const int32_t k0 = k0s[i], k1 = k0s[i + 1];
         xs[i] = px;
@@ -1278,13 +1331,27 @@ lpb_err lp_solve_host(int32_t num_lps, const int32_t* m, const int32_t* n,
             sc[k - k0] = hc[k] - clo;
         }
         cudaError_t err = cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
+        if (err == cudaSuccess && i > 0) err = cudaStreamWaitEvent(streams[i], copied[i - 1], 0);
         if (err != cudaSuccess) {
             e = cuda_fail(err, "stream creation");
             break;
         }
-        e = lp_batch_create(&hs[i], k1 - k0, m + k0, n + k0, sa.data(), A + alo, ahi - alo, sb.data(), b + blo,
-                            bhi - blo, sc.data(), c + clo, chi - clo, LPB_HOST, opts, streams[i]);
+        e = create_batch(&hs[i], k1 - k0, m + k0, n + k0, sa.data(), A + alo, ahi - alo, sb.data(), b + blo,
+                         bhi - blo, sc.data(), c + clo, chi - clo, LPB_HOST, opts, streams[i], copied[i], true);
         if (e == LPB_OK) e = lp_batch_solve(hs[i], streams[i]);
+    }
+    // the input checks (each read waits for its chunk's solve); results only
+    // when every chunk's inputs were finite
+    for (int32_t i = 0; i < chunks && e == LPB_OK; ++i) {
+        unsigned long long bad = 0;
+        cudaError_t err = cudaMemcpyAsync(&bad, hs[i]->d_bad, sizeof bad, cudaMemcpyDeviceToHost, streams[i]);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(streams[i]);
+        if (err != cudaSuccess)
+            e = cuda_fail(err, "input check");
+        else if (bad)
+            e = fail(LPB_EINVAL, "LPs " + std::to_string(k0s[i]) + ".." + std::to_string(k0s[i + 1] - 1) + ": " +
+                                     std::to_string(bad) + " non-finite entries in A, b or c");
     }
     for (int32_t i = 0; i < chunks && e == LPB_OK; ++i) {
         const int32_t k0 = k0s[i];
@@ -1298,6 +1365,8 @@ lpb_err lp_solve_host(int32_t num_lps, const int32_t* m, const int32_t* n,
             cudaStreamDestroy(streams[i]);
         }
     }
+    for (int32_t i = 0; i < chunks; ++i)
+        if (copied[i]) cudaEventDestroy(copied[i]);
     if (e != LPB_OK) return fail(e, msg);
     return LPB_OK;
 }

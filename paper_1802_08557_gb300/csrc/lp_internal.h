@@ -293,7 +293,11 @@ void api_clear_error();
 cudaError_t launch_hyperbox(const double* L, const double* lo, const double* hi, bool box_per_lp, double* obj,
                             double* x, int64_t num_lps, int dim, cudaStream_t stream);
 
-cudaError_t launch_prepare(const DeviceBatch& B, int32_t num_lps, int64_t a_len, int64_t b_len,
-                           int64_t c_len, int32_t* k, unsigned long long* bad, cudaStream_t stream);
+// Input check of a batch's own device copies of A, b, c: *bad = the number of
+// non-finite entries, each of which is set to 0.
+cudaError_t launch_input_check(double* A, int64_t a_len, double* b, int64_t b_len, double* c, int64_t c_len,
+                               unsigned long long* bad, cudaStream_t stream);
+// k[lp] = the number of rows of LP lp with b_i < 0 (rows that get an artificial).
+cudaError_t launch_count_negative_rhs(const DeviceBatch& B, int32_t num_lps, int32_t* k, cudaStream_t stream);
 
 }  // namespace lpb

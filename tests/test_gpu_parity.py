@@ -305,8 +305,9 @@ def test_solve_host_equals_create_solve_results(prec):
 
 def test_solve_host_reports_errors_of_a_later_chunk():
     """A non-finite entry in the last chunk: lp_solve_host returns LPB_EINVAL
-    (from that chunk's create) after solving the earlier chunks, releases
-    everything, and a later call on good data still works."""
+    (the chunks' input checks are read after their solves; the check zeroes
+    the entry in the device copy, so the solve runs on finite data), writes no
+    results, releases everything, and a later call on good data still works."""
     batch = W.mixed_sign_dense(400, 10, 8, start=5)
     A = batch.A.copy()
     A[-1] = np.inf
@@ -317,6 +318,8 @@ def test_solve_host_reports_errors_of_a_later_chunk():
         lpb.lp_solve_host(batch.m, batch.n, batch.a_off, A, batch.b_off, batch.b, batch.c_off, batch.c,
                           st, it, ob, x, chunks=4)
     assert e.value.code == lpb.LPB_EINVAL
+    assert "non-finite" in str(e.value)
+    assert not st.any() and not it.any() and not ob.any() and not x.any()
     lpb.lp_solve_host(batch.m, batch.n, batch.a_off, batch.A, batch.b_off, batch.b, batch.c_off, batch.c,
                       st, it, ob, x, chunks=4)
     ref = gpu_solve(batch)
