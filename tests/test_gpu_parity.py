@@ -324,3 +324,28 @@ def test_solve_host_reports_errors_of_a_later_chunk():
                       st, it, ob, x, chunks=4)
     ref = gpu_solve(batch)
     np.testing.assert_array_equal(ob, ref["obj"])
+
+
+def test_solve_host_non_finite_rhs_in_a_middle_chunk():
+    """b_i = -inf counts as a phase-I row in the host's plan, while the
+    device copy the solve reads holds 0 (the check zeroes it): the solve needs
+    no more shared memory than planned, and the call returns LPB_EINVAL with
+    no results written.  NaN in c: the same.  Then a good call still works."""
+    batch = W.mixed_sign_dense(600, 12, 9, start=40)
+    N = batch.num_lps
+    st, it, ob = np.zeros(N, np.int32), np.zeros(N, np.int32), np.zeros(N)
+    x = np.zeros(int(batch.n.astype(np.int64).sum()))
+    for which in ("b", "c"):
+        b, c = batch.b.copy(), batch.c.copy()
+        if which == "b":
+            b[int(batch.b_off[300]) + 3] = -np.inf
+        else:
+            c[int(batch.c_off[301]) + 1] = np.nan
+        with pytest.raises(lpb.LPBError) as e:
+            lpb.lp_solve_host(batch.m, batch.n, batch.a_off, batch.A, batch.b_off, b, batch.c_off, c,
+                              st, it, ob, x, chunks=3)
+        assert e.value.code == lpb.LPB_EINVAL and "non-finite" in str(e.value)
+        assert not st.any() and not ob.any() and not x.any()
+    lpb.lp_solve_host(batch.m, batch.n, batch.a_off, batch.A, batch.b_off, batch.b, batch.c_off, batch.c,
+                      st, it, ob, x, chunks=3)
+    np.testing.assert_array_equal(ob, gpu_solve(batch)["obj"])
