@@ -1280,8 +1280,10 @@ lpb_err lp_solve_host(int32_t num_lps, const int32_t* m, const int32_t* n,
         // the one not overlapped with a solve (1e5 dense 50 x 50 LPs, 2.08 GB
         // from pinned memory at ~211 GB/s: 24.8 / 19.6 / 17.2 / 17.7 / 16.3 /
         // 18.6 / 23.9 ms for 1 / 2 / 4 / 6 / 8 / 12 / 16 chunks)
-        const int64_t bytes = (a_len + b_len + c_len) * 8, per = int64_t(256) << 20;
-        chunks = (int32_t)std::min<int64_t>(8, std::max<int64_t>(1, (bytes + per - 1) / per));
+        const double per = 256.0 * 1024 * 1024;
+        const double bytes = 8.0 * ((double)std::max<int64_t>(a_len, 0) + (double)std::max<int64_t>(b_len, 0) +
+                                    (double)std::max<int64_t>(c_len, 0));
+        chunks = (int32_t)std::min(8.0, std::max(1.0, std::ceil(bytes / per)));
     }
     chunks = std::min(chunks, num_lps);
     // every LP's offsets (packed when NULL); each chunk passes the smallest
