@@ -148,9 +148,10 @@ def test_host_and_device_inputs_agree_and_resolve_is_deterministic():
 
 def test_errors_are_codes():
     bad = W.pack("nan", [(np.array([[np.nan]]), np.array([1.0]), np.array([1.0]))])
-    with pytest.raises(lpb.LPBError) as ei:
-        lpb.BatchSolver(bad)
-    assert ei.value.code == lpb.LPB_EINVAL
+    for device_data in (True, False):
+        with pytest.raises(lpb.LPBError) as ei:
+            lpb.BatchSolver(bad, device_data=device_data)
+        assert ei.value.code == lpb.LPB_EINVAL and "non-finite" in str(ei.value)
     s = lpb.BatchSolver(W.positive_dense(2, 3, 3))
     with pytest.raises(lpb.LPBError) as ei:
         lpb.lp_batch_results(s.h, np.zeros(2, np.int32))
