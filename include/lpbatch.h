@@ -301,7 +301,9 @@ lpb_err lp_batch_stage_times(lp_batch *h, float *stage_ms, int32_t *num_solves);
  *  status, iters, obj [device, num_lps]; x [device, num_lps*n]; y [device,
  *                 num_lps*m] or NULL: the outputs of lp_batch_results, packed
  *                 the same way.
- *  opts           NULL = defaults (opts->schedule and block_threads are ignored).
+ *  opts           NULL = defaults (opts->schedule and block_threads are ignored;
+ *                 opts->precision must be LP_PREC_FP64, else LPB_EINVAL: only
+ *                 the FP64 streamed kernel runs here).
  *  stream         cudaStream_t (NULL = legacy default); the call is
  *                 asynchronous and returns once the work is enqueued.
  *
@@ -309,9 +311,11 @@ lpb_err lp_batch_stage_times(lp_batch *h, float *stage_ms, int32_t *num_solves);
  * loads the library until the process exits.  It holds ~52 bytes per LP plus
  * at least one tableau workspace of about 8*(m+2)*(n+m+4) bytes; a batch that
  * does not fit returns LPB_ETOOBIG before any GPU work (e.g. up to ~1.2
- * million 50 x 50 LPs per call).  The first call on a device looks up the
- * array's device address (a one-time set-up with that device current); make
- * that first call before capturing any stream.  All calls share the array, so
+ * million 50 x 50 LPs per call).  Every call looks up the array's device
+ * address in the current context (a lookup, no allocation), so a call after
+ * cudaDeviceReset or under another context uses that context's copy; the
+ * first call on a device may load the library's device code, so make it
+ * before capturing any stream.  All calls share the array, so
  * calls that overlap on the GPU race and give wrong results: serialise them
  * (one stream, or wait for the previous call).  Errors are reported by the
  * return code only (LPB_EINVAL, LPB_ETOOBIG, LPB_ECUDA); lpb_last_error is not

@@ -25,7 +25,7 @@
  * is kept beside it (the paper's first auxiliary column).  A second objective
  * row carries the auxiliary (phase-I) objective while phase I runs.
  *
- * Readings of points the paper leaves open (all listed in the design doc):
+ * Readings of points the paper leaves open (the CUDA solver takes the same):
  *  - Sign convention: the objective row holds reduced costs d_j, initially
  *    -c_j; the most negative d_j enters; the ratio is beta_i / t_ie over rows
  *    with t_ie > eps_piv.  This is the paper's "maximum of the last row" and

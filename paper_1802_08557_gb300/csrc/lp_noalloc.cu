@@ -21,7 +21,6 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
-#include <mutex>
 
 #include "lp_internal.h"
 #include "lpbatch.h"
@@ -30,15 +29,9 @@ namespace lpb {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB
-constexpr int kMaxDevices = 64;
 
 // Scratch: [0, 256) work counter | per-LP descriptors | tableau slots.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-// Host-side copies of the scratch's device address, one per device, filled on
-// the first call made with that device current.
-std::mutex g_mu;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
 
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -83,16 +76,16 @@ __global__ void fill_uniform_descriptors(DescPtrs d, int32_t num_lps, int32_t m,
     d.y_off[k] = k * (int64_t)m;
 }
 
-// Device address of the scratch array on the current device (set up once).
-cudaError_t scratch_address(int dev, unsigned char** out) {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (err != cudaSuccess) return err;
-        g_scratch_addr[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_scratch_addr[dev];
+// Device address of the scratch array in the current context.  Looked up on
+// every call (the lookup allocates nothing): after cudaDeviceReset, or with
+// another context current, the module is loaded again and the array can sit
+// at another address, so a cached pointer could point at freed or foreign
+// memory.
+cudaError_t scratch_address(unsigned char** out) {
+    void* p = nullptr;
+    const cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (err != cudaSuccess) return err;
+    *out = static_cast<unsigned char*>(p);
     return cudaSuccess;
 }
 
@@ -111,6 +104,9 @@ extern "C" lpb_err lp_solve_uniform_noalloc(int32_t num_lps, int32_t m, int32_t 
     lpb_default_opts(&o);
     if (opts) o = *opts;
     if (!(o.eps_opt >= 0) || !(o.eps_piv >= 0) || !(o.eps_feas >= 0) || !(o.tau >= 0)) return LPB_EINVAL;
+    // Only the FP64 streamed kernel runs here; the mixed-precision path needs
+    // its own workspaces and re-solve queues, which this entry point has not.
+    if (o.precision != LP_PREC_FP64) return LPB_EINVAL;
 
     // Room: the counter, the descriptors, and at least one tableau slot sized
     // for the widest phase-I tableau (every row with b_i < 0).
@@ -121,9 +117,8 @@ extern "C" lpb_err lp_solve_uniform_noalloc(int32_t num_lps, int32_t m, int32_t 
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return LPB_ECUDA;
-    if (dev < 0 || dev >= kMaxDevices) return LPB_ECUDA;
     unsigned char* base = nullptr;
-    if ((err = scratch_address(dev, &base)) != cudaSuccess) return LPB_ECUDA;
+    if ((err = scratch_address(&base)) != cudaSuccess) return LPB_ECUDA;
     int sms = 0;
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return LPB_ECUDA;
 
