@@ -414,7 +414,46 @@ lpb_err lp_mlp_train_step(lp_mlp *net, const float *x, const float *y, int32_t b
  * parameter layout) and the loss; waits for the GPU. */
 lpb_err lp_mlp_gradients(lp_mlp *net, const float *x, const float *y, int32_t batch, float pos_weight,
                          float *grads, double *loss, void *stream);
+/*
+ * The backward pass at given forward values: like lp_mlp_gradients, but the
+ * forward products are not run; the pre-activations a1 [batch x n_h1], a2
+ * [batch x n_h2] and the logits z [batch x n_out] (device, FP32) are taken
+ * from the caller, and h1 = relu(a1), h2 = relu(a2) are rounded to BF16 from
+ * them exactly as the forward pass rounds its own.  x, y as for
+ * lp_mlp_gradients.  Used to check the backward kernels layer by layer on the
+ * same inputs as a reference implementation; waits for the GPU.
+ */
+lpb_err lp_mlp_gradients_at(lp_mlp *net, const float *x, const float *a1, const float *a2, const float *z,
+                            const float *y, int32_t batch, float pos_weight, float *grads, double *loss,
+                            void *stream);
 lpb_err lp_mlp_destroy(lp_mlp *net);
+
+/* Epilogues of the network's product kernel (lp_mlp_gemm_bf16). */
+enum {
+    LPB_EPI_STORE = 0,      /* C = acc                                                   */
+    LPB_EPI_BIAS_RELU = 1,  /* v = acc + bias[col]; C = v (if C); h = hT^T = bf16(max(v, 0)) */
+    LPB_EPI_BIAS = 2,       /* C = acc + bias[col]                                       */
+    LPB_EPI_MASK_GRAD = 3   /* v = pre > 0 ? acc : 0 (pre at C's index); C = v; h = hT^T = bf16(v) */
+};
+/* Kernel forms of the product: AUTO picks as the network does (128 x 128 tiles
+ * when they give at least one per SM, else 64 x 64); the others force one. */
+enum { LPB_GEMM_AUTO = 0, LPB_GEMM_MMA64 = 1, LPB_GEMM_MMA128 = 2 };
+
+/*
+ * The network's matrix product on caller buffers: acc[M x N] = A[M x K] .
+ * B[N x K]^T with BF16 operands (bit patterns as uint16_t, row-major, K
+ * contiguous; lda, ldb >= K and multiples of 8; A and B 16-byte aligned; K a
+ * multiple of 32 -- pad with zeros), FP32 accumulation on the tensor cores,
+ * then the epilogue above: C FP32 [M x ldc], h BF16 [M x ldh], hT BF16 [N x
+ * ldt] (the transposed copy; may be NULL for LPB_EPI_BIAS_RELU).  Every
+ * array is device memory of the current device; asynchronous on `stream`.
+ * This is the building block of lp_mlp_forward / lp_mlp_train_step, exposed
+ * so that each product can be checked on its own.  Errors: LPB_EINVAL (bad
+ * sizes, alignment, missing array, host memory), LPB_ETOOBIG, LPB_ECUDA.
+ */
+lpb_err lp_mlp_gemm_bf16(int32_t epilogue, int32_t form, int32_t M, int32_t N, int32_t K, const uint16_t *A,
+                         int32_t lda, const uint16_t *B, int32_t ldb, float *C, int32_t ldc, const float *bias,
+                         const float *pre, uint16_t *h, int32_t ldh, uint16_t *hT, int32_t ldt, void *stream);
 
 /*
  * Solve the batch from the warm-start network's proposal.  For every LP the

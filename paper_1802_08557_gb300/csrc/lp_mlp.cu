@@ -252,12 +252,15 @@ __global__ void __launch_bounds__(kTThreads) gemm_nt_tiled_kernel(const GemmArgs
             }
 }
 
+// Kernel forms of the product (lp_mlp_gemm_bf16's `form`).
+enum GemmForm : int { kFormAuto = 0, kFormMma64 = 1, kFormMma128 = 2 };
+
 // 128 x 128 tiles when they give at least one per SM, else 64 x 64 (small
 // products, e.g. the weight gradients of one training batch): same results.
 template <int kEpi>
-cudaError_t gemm(const GemmArgs& a, cudaStream_t s) {
+cudaError_t gemm(const GemmArgs& a, cudaStream_t s, int form = kFormAuto) {
     const int64_t big_tiles = (int64_t)((a.N + kTN - 1) / kTN) * ((a.M + kTM - 1) / kTM);
-    if (big_tiles >= 152) {
+    if (form == kFormMma128 || (form == kFormAuto && big_tiles >= 152)) {
         const dim3 grid((a.N + kTN - 1) / kTN, (a.M + kTM - 1) / kTM);
         gemm_nt_tiled_kernel<kEpi><<<grid, kTThreads, 0, s>>>(a);
     } else {
@@ -388,6 +391,23 @@ __global__ void zero_cols_kernel(__nv_bfloat16* __restrict__ buf, int rows, int 
     }
 }
 
+// h = bf16(relu(a)) of given pre-activations a [batch x n] (FP32), as the
+// forward epilogue writes it: hb [batch x ldh] and hbT [n x ldt] (rows
+// batch..ldt-1 of hbT zeroed: the batch padding of the weight-gradient sums).
+__global__ void relu_bf16_kernel(const float* __restrict__ a, int batch, int n, __nv_bfloat16* __restrict__ hb,
+                                 int ldh, __nv_bfloat16* __restrict__ hbT, int ldt) {
+    const int64_t total = (int64_t)ldt * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), c = (int)(e - (int64_t)r * n);
+        __nv_bfloat16 h = __float2bfloat16_rn(0.0f);
+        if (r < batch) {
+            h = __float2bfloat16_rn(fmaxf(a[(size_t)r * n + c], 0.0f));
+            hb[(size_t)r * ldh + c] = h;
+        }
+        hbT[(size_t)c * ldt + r] = h;
+    }
+}
+
 inline unsigned grid_for(int64_t n, int threads = 256) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 16));
 }
@@ -514,12 +534,14 @@ cudaError_t mlp_forward(MlpModel* m, const float* x, int batch, float* logits, c
     return cudaGetLastError();
 }
 
-// Forward + backward; gradients into L[l].gW / gb; loss into m->loss.
-cudaError_t mlp_backward(MlpModel* m, const float* x, const float* y, int batch, float pos_weight, cudaStream_t s) {
+// Backward pass from the forward values a1, a2 (pre-activations) and z
+// (logits), with the BF16 activations (x, h1, h2, both orientations) already
+// in the model's buffers; gradients into L[l].gW / gb; loss into m->loss.
+cudaError_t mlp_backward_from(MlpModel* m, const float* y, int batch, float pos_weight, const float* a1,
+                              const float* a2, const float* z, cudaStream_t s) {
     cudaError_t e;
-    if ((e = mlp_forward(m, x, batch, nullptr, s))) return e;
     const int bT = pad_to(batch, kPadK);
-    loss_grad_kernel<<<(bT + 127) / 128, 128, 0, s>>>(m->z, y, batch, m->n_out, pos_weight, m->g3, m->g3b,
+    loss_grad_kernel<<<(bT + 127) / 128, 128, 0, s>>>(z, y, batch, m->n_out, pos_weight, m->g3, m->g3b,
                                                       m->L[2].out_pad, m->g3bT, bT, m->row_loss);
     sum_kernel<<<1, 1, 0, s>>>(m->row_loss, batch, m->loss);
     if ((e = cudaGetLastError())) return e;
@@ -532,7 +554,7 @@ cudaError_t mlp_backward(MlpModel* m, const float* x, const float* y, int batch,
     // g2 = (g3 W3) * [a2 > 0] : [batch x h2], K = n_out (B operand = W3^T [h2 x out_pad])
     g = GemmArgs{};
     g.A = m->g3b; g.lda = m->L[2].out_pad; g.B = m->L[2].WbT; g.ldb = m->L[2].out_pad; g.M = batch; g.N = m->h2;
-    g.K = m->L[2].out_pad; g.C = m->g2; g.ldc = m->h2; g.pre = m->a2; g.hbf = m->g2b; g.ldh = m->L[2].in_pad;
+    g.K = m->L[2].out_pad; g.C = m->g2; g.ldc = m->h2; g.pre = a2; g.hbf = m->g2b; g.ldh = m->L[2].in_pad;
     g.hbfT = m->g2bT; g.ldt = bT;
     if ((e = gemm<kEpiMaskGrad>(g, s))) return e;
     // dW2 = g2^T h1
@@ -544,7 +566,7 @@ cudaError_t mlp_backward(MlpModel* m, const float* x, const float* y, int batch,
     // g1 = (g2 W2) * [a1 > 0]
     g = GemmArgs{};
     g.A = m->g2b; g.lda = m->L[1].out_pad; g.B = m->L[1].WbT; g.ldb = m->L[1].out_pad; g.M = batch; g.N = m->h1;
-    g.K = m->L[1].out_pad; g.C = m->g1; g.ldc = m->h1; g.pre = m->a1; g.hbf = m->g1b; g.ldh = m->L[1].in_pad;
+    g.K = m->L[1].out_pad; g.C = m->g1; g.ldc = m->h1; g.pre = a1; g.hbf = m->g1b; g.ldh = m->L[1].in_pad;
     g.hbfT = m->g1bT; g.ldt = bT;
     if ((e = gemm<kEpiMaskGrad>(g, s))) return e;
     // dW1 = g1^T x
@@ -554,6 +576,44 @@ cudaError_t mlp_backward(MlpModel* m, const float* x, const float* y, int batch,
     if ((e = gemm<kEpiStore>(g, s))) return e;
     colsum_kernel<<<(m->h1 + 127) / 128, 128, 0, s>>>(m->g1, batch, m->h1, m->h1, m->L[0].gb);
     return cudaGetLastError();
+}
+
+// Forward + backward; gradients into L[l].gW / gb; loss into m->loss.
+cudaError_t mlp_backward(MlpModel* m, const float* x, const float* y, int batch, float pos_weight, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = mlp_forward(m, x, batch, nullptr, s))) return e;
+    return mlp_backward_from(m, y, batch, pos_weight, m->a1, m->a2, m->z, s);
+}
+
+// The backward pass at given forward values (layer-wise checks of the
+// backward kernels): x's BF16 copies by the features kernel, h1 and h2 as
+// bf16(relu(a)) in both orientations, then mlp_backward_from on a1, a2, z.
+cudaError_t mlp_backward_at(MlpModel* m, const float* x, const float* a1, const float* a2, const float* z,
+                            const float* y, int batch, float pos_weight, cudaStream_t s) {
+    cudaError_t e;
+    const int bT = pad_to(batch, kPadK);
+    features_kernel<<<grid_for((int64_t)bT * m->n_in), 256, 0, s>>>(x, batch, m->n_in, m->mean, m->inv_std, m->xb,
+                                                                      m->L[0].in_pad, m->xbT, bT);
+    relu_bf16_kernel<<<grid_for((int64_t)bT * m->h1), 256, 0, s>>>(a1, batch, m->h1, m->h1b, m->L[1].in_pad,
+                                                                     m->h1bT, bT);
+    relu_bf16_kernel<<<grid_for((int64_t)bT * m->h2), 256, 0, s>>>(a2, batch, m->h2, m->h2b, m->L[2].in_pad,
+                                                                     m->h2bT, bT);
+    if (bT > batch) {
+        zero_cols_kernel<<<grid_for((int64_t)m->h2 * (bT - batch)), 256, 0, s>>>(m->g2bT, m->h2, bT, batch, bT);
+        zero_cols_kernel<<<grid_for((int64_t)m->h1 * (bT - batch)), 256, 0, s>>>(m->g1bT, m->h1, bT, batch, bT);
+    }
+    if ((e = cudaGetLastError())) return e;
+    return mlp_backward_from(m, y, batch, pos_weight, a1, a2, z, s);
+}
+
+// One product through a chosen kernel form (lp_mlp_gemm_bf16).
+cudaError_t mlp_gemm_dispatch(int epi, int form, const GemmArgs& g, cudaStream_t s) {
+    switch (epi) {
+        case kEpiStore: return gemm<kEpiStore>(g, s, form);
+        case kEpiBiasReLU: return gemm<kEpiBiasReLU>(g, s, form);
+        case kEpiBias: return gemm<kEpiBias>(g, s, form);
+        default: return gemm<kEpiMaskGrad>(g, s, form);
+    }
 }
 
 cudaError_t mlp_adam(MlpModel* m, float lr, cudaStream_t s) {
@@ -801,6 +861,33 @@ lpb_err lp_mlp_train_step(lp_mlp* net, const float* x, const float* y, int32_t b
     return LPB_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Gradients of the last backward pass (parameter layout) and its loss to the host.
+lpb_err copy_gradients(lp_mlp* net, float* grads, double* loss) {
+    cudaError_t e;
+    size_t off = 0;
+    for (lpb::MlpLayer& L : net->m.L) {
+        const size_t nw = (size_t)L.out * L.in;
+        if ((e = cudaMemcpy(grads + off, L.gW, nw * 4, cudaMemcpyDeviceToHost))) return api_cuda_fail(e, "gradients");
+        off += nw;
+        if ((e = cudaMemcpy(grads + off, L.gb, (size_t)L.out * 4, cudaMemcpyDeviceToHost)))
+            return api_cuda_fail(e, "gradients");
+        off += L.out;
+    }
+    if (loss && (e = cudaMemcpy(loss, net->m.loss, sizeof(double), cudaMemcpyDeviceToHost)))
+        return api_cuda_fail(e, "loss");
+    return LPB_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
 lpb_err lp_mlp_gradients(lp_mlp* net, const float* x, const float* y, int32_t batch, float pos_weight, float* grads,
                          double* loss, void* stream) {
     lpb::api_clear_error();
@@ -814,17 +901,62 @@ lpb_err lp_mlp_gradients(lp_mlp* net, const float* x, const float* y, int32_t ba
     cudaError_t e = lpb::mlp_backward(&net->m, x, y, batch, pos_weight, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return api_cuda_fail(e, "forward/backward");
-    size_t off = 0;
-    for (lpb::MlpLayer& L : net->m.L) {
-        const size_t nw = (size_t)L.out * L.in;
-        if ((e = cudaMemcpy(grads + off, L.gW, nw * 4, cudaMemcpyDeviceToHost))) return api_cuda_fail(e, "gradients");
-        off += nw;
-        if ((e = cudaMemcpy(grads + off, L.gb, (size_t)L.out * 4, cudaMemcpyDeviceToHost)))
-            return api_cuda_fail(e, "gradients");
-        off += L.out;
-    }
-    if (loss && (e = cudaMemcpy(loss, net->m.loss, sizeof(double), cudaMemcpyDeviceToHost)))
-        return api_cuda_fail(e, "loss");
+    return copy_gradients(net, grads, loss);
+}
+
+lpb_err lp_mlp_gradients_at(lp_mlp* net, const float* x, const float* a1, const float* a2, const float* z,
+                            const float* y, int32_t batch, float pos_weight, float* grads, double* loss,
+                            void* stream) {
+    lpb::api_clear_error();
+    if (!net || !x || !a1 || !a2 || !z || !y || !grads) return api_fail(LPB_EINVAL, "a pointer argument is NULL");
+    if (batch < 1 || batch > net->m.train_batch) return api_fail(LPB_EINVAL, "batch must be in [1, max_batch]");
+    if (!(pos_weight > 0.0f)) return api_fail(LPB_EINVAL, "pos_weight must be > 0");
+    Dev guard(net->device);
+    for (const void* p : {(const void*)x, (const void*)a1, (const void*)a2, (const void*)z, (const void*)y})
+        if (!on_device(p, net->device))
+            return api_fail(LPB_EINVAL, "x, a1, a2, z and y must be device memory of the network's device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = lpb::mlp_backward_at(&net->m, x, a1, a2, z, y, batch, pos_weight, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return api_cuda_fail(e, "backward");
+    return copy_gradients(net, grads, loss);
+}
+
+lpb_err lp_mlp_gemm_bf16(int32_t epilogue, int32_t form, int32_t M, int32_t N, int32_t K, const uint16_t* A,
+                         int32_t lda, const uint16_t* B, int32_t ldb, float* C, int32_t ldc, const float* bias,
+                         const float* pre, uint16_t* h, int32_t ldh, uint16_t* hT, int32_t ldt, void* stream) {
+    lpb::api_clear_error();
+    if (epilogue < LPB_EPI_STORE || epilogue > LPB_EPI_MASK_GRAD) return api_fail(LPB_EINVAL, "unknown epilogue");
+    if (form < LPB_GEMM_AUTO || form > LPB_GEMM_MMA128) return api_fail(LPB_EINVAL, "unknown kernel form");
+    if (M < 1 || N < 1 || K < 1 || K % 32 != 0) return api_fail(LPB_EINVAL, "M, N >= 1 and K a positive multiple of 32");
+    if (M > LPB_MAX_MLP_BATCH * 8 || N > LPB_MAX_MLP_BATCH * 8 || K > LPB_MAX_MLP_BATCH * 8)
+        return api_fail(LPB_ETOOBIG, "a dimension exceeds the limit");
+    if (!A || !B || lda < K || ldb < K || lda % 8 != 0 || ldb % 8 != 0 || !aligned16(A) || !aligned16(B))
+        return api_fail(LPB_EINVAL, "A and B: 16-byte aligned, lda and ldb >= K and multiples of 8");
+    const bool need_c = epilogue != LPB_EPI_BIAS_RELU;
+    const bool need_bias = epilogue == LPB_EPI_BIAS || epilogue == LPB_EPI_BIAS_RELU;
+    const bool need_h = epilogue == LPB_EPI_BIAS_RELU || epilogue == LPB_EPI_MASK_GRAD;
+    if ((need_c && !C) || (C && ldc < N) || (need_bias && !bias) || (epilogue == LPB_EPI_MASK_GRAD && (!pre || !C)))
+        return api_fail(LPB_EINVAL, "C (ldc >= N), bias or pre missing for this epilogue");
+    if ((need_h && (!h || ldh < N)) || (epilogue == LPB_EPI_MASK_GRAD && !hT) || (hT && ldt < M))
+        return api_fail(LPB_EINVAL, "h (ldh >= N) or hT (ldt >= M) missing for this epilogue");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (const void* p : {(const void*)A, (const void*)B, (const void*)C, (const void*)bias, (const void*)pre,
+                          (const void*)h, (const void*)hT})
+        if (p && !on_device(p, dev)) return api_fail(LPB_EINVAL, "arrays must be device memory of the current device");
+    lpb::GemmArgs g{};
+    g.A = reinterpret_cast<const __nv_bfloat16*>(A);
+    g.B = reinterpret_cast<const __nv_bfloat16*>(B);
+    g.C = C;
+    g.M = M; g.N = N; g.K = K; g.lda = lda; g.ldb = ldb; g.ldc = ldc;
+    g.bias = need_bias ? bias : nullptr;
+    g.pre = epilogue == LPB_EPI_MASK_GRAD ? pre : nullptr;
+    g.hbf = need_h ? reinterpret_cast<__nv_bfloat16*>(h) : nullptr;
+    g.hbfT = need_h ? reinterpret_cast<__nv_bfloat16*>(hT) : nullptr;
+    g.ldh = ldh; g.ldt = ldt;
+    const cudaError_t e = lpb::mlp_gemm_dispatch(epilogue, form, g, static_cast<cudaStream_t>(stream));
+    if (e) return api_cuda_fail(e, "product");
     return LPB_OK;
 }
 

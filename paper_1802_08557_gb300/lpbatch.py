@@ -22,6 +22,8 @@ LPB_HOST, LPB_DEVICE = 0, 1
 LP_PREC_FP64, LP_PREC_FP32_REFINE = 0, 1
 LPB_SCHED_AUTO, LPB_SCHED_STREAMED = 0, 1
 LPB_MAX_DIM = 16384
+LPB_EPI_STORE, LPB_EPI_BIAS_RELU, LPB_EPI_BIAS, LPB_EPI_MASK_GRAD = 0, 1, 2, 3
+LPB_GEMM_AUTO, LPB_GEMM_MMA64, LPB_GEMM_MMA128 = 0, 1, 2
 
 # Every symbol include/lpbatch.h declares.
 EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_results",
@@ -30,7 +32,8 @@ EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_r
             "lp_mlp_create", "lp_mlp_num_params", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_set_scaling",
             "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients", "lp_mlp_destroy", "lp_batch_solve_warm",
             "lp_batch_features", "lp_batch_active_labels", "lp_batch_solve_graph", "lp_batch_autotune",
-            "lp_batch_group_info", "lp_batch_set_group_form", "lp_solve_host")
+            "lp_batch_group_info", "lp_batch_set_group_form", "lp_solve_host", "lp_mlp_gradients_at",
+            "lp_mlp_gemm_bf16")
 
 
 class LPBatchOpts(ctypes.Structure):
@@ -129,6 +132,10 @@ def load(path: str | None = None):
                                         ctypes.POINTER(ctypes.c_double), _vp]
         L.lp_mlp_gradients.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, _vp, ctypes.POINTER(ctypes.c_double),
                                        _vp]
+        L.lp_mlp_gradients_at.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, _vp,
+                                          ctypes.POINTER(ctypes.c_double), _vp]
+        L.lp_mlp_gemm_bf16.argtypes = [_i32, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _i32, _vp, _i32, _vp, _vp,
+                                       _vp, _i32, _vp, _i32, _vp]
         L.lp_mlp_destroy.argtypes = [_vp]
         L.lp_batch_solve_graph.argtypes = [_vp, _vp]
         L.lp_batch_solve_graph.restype = ctypes.c_int
@@ -149,7 +156,7 @@ def load(path: str | None = None):
         L.lp_batch_active_labels.restype = ctypes.c_int
         for f in ("lp_mlp_create", "lp_mlp_num_params", "lp_mlp_set_params", "lp_mlp_get_params",
                   "lp_mlp_set_scaling", "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients",
-                  "lp_mlp_destroy"):
+                  "lp_mlp_gradients_at", "lp_mlp_gemm_bf16", "lp_mlp_destroy"):
             getattr(L, f).restype = ctypes.c_int
         L.lp_hyperbox_solve.argtypes = [_i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _i32, _vp]
         L.lp_hyperbox_solve.restype = ctypes.c_int
@@ -333,6 +340,15 @@ class Mlp:
                                        ctypes.byref(loss), _stream_handle(stream)), "lp_mlp_gradients")
         return g, loss.value
 
+    def gradients_at(self, x, a1, a2, z, y, pos_weight: float = 1.0, stream=None):
+        """Gradients from given forward values a1, a2, z (device FP32)."""
+        g = np.empty(self.num_params, np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(load().lp_mlp_gradients_at(self.h, _addr(x), _addr(a1), _addr(a2), _addr(z), _addr(y),
+                                          int(x.shape[0]), pos_weight, g.ctypes.data, ctypes.byref(loss),
+                                          _stream_handle(stream)), "lp_mlp_gradients_at")
+        return g, loss.value
+
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             load().lp_mlp_destroy(self.h)
@@ -343,6 +359,15 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def lp_mlp_gemm_bf16(epilogue, form, M, N, K, A, lda, B, ldb, C=None, ldc=0, bias=None, pre=None, h=None, ldh=0,
+                     hT=None, ldt=0, stream=None):
+    """The network's product kernel on caller device buffers (see
+    include/lpbatch.h); A, B, h, hT are BF16 tensors (torch.bfloat16)."""
+    _check(load().lp_mlp_gemm_bf16(int(epilogue), int(form), int(M), int(N), int(K), _addr(A), int(lda), _addr(B),
+                                   int(ldb), _addr(C), int(ldc), _addr(bias), _addr(pre), _addr(h), int(ldh),
+                                   _addr(hT), int(ldt), _stream_handle(stream)), "lp_mlp_gemm_bf16")
 
 
 def lp_solve_uniform_noalloc(num_lps, m, n, A, b, c, status, iters, obj, x, y=None,

@@ -1,19 +1,22 @@
 """GPU kernels of the warm-start network against the network oracle
-(oracle/mlp.py), through the C ABI: forward logits, every gradient, one Adam
-step, training progress and determinism.
+(oracle/mlp.py), through the C ABI, element by element: each matrix product
+with its epilogue on identical BF16 operands, the backward pass from the
+oracle's forward values (layer by layer), the whole network on weights whose
+forward pass is exact on both sides, one Adam step, training progress and
+determinism.
 
-Tolerances.  Both sides round the same operands to BF16; the GPU accumulates
-products in FP32 (error ~ K * 2^-24 of the summed magnitudes, K <= 512), the
-oracle in FP64.  A hidden activation whose FP32 value lies within that error of
-a BF16 rounding boundary can round the other way (one BF16 step, 2^-8
-relative) and move the later layers slightly, so gradients are compared per
-parameter block in norm (1e-2 relative) rather than element by element, and
-logits element by element with a tolerance scaled to their spread."""
+Bounds (tests/mlp_bounds.py): the GPU accumulates BF16 products in FP32, the
+oracle exactly enough in FP64, so each accumulator is within K 2^-23 sum|a||b|
+of the oracle's; an operand the GPU rounded to BF16 itself may sit one BF16
+step from the oracle's where its FP32 value lies within its own bound of a
+rounding boundary, and that width is carried into the next product.  No
+block is compared in norm."""
 from __future__ import annotations
 
 import numpy as np
 import pytest
 
+import mlp_bounds as MB
 from oracle import mlp as omlp
 from paper_1802_08557_gb300 import lpbatch as lpb
 
@@ -56,62 +59,211 @@ def _net_with_oracle_params(sizes, seed, max_batch):
     return net, params
 
 
-@pytest.mark.parametrize("batch", [1, 37, 300])
-def test_forward_matches_oracle(batch):
+def dyadic_network(sizes, seed, batch):
+    """Weights in {-1, 0, 1} 2^-3 with sparse rows, biases and inputs on
+    coarse binary grids: every partial sum of the forward pass is exact in
+    FP32 in any order and every hidden activation is exact in BF16, so the
+    GPU's forward values equal the oracle's bit for bit (asserted from the
+    oracle's values below) and only the backward pass rounds."""
+    rng = np.random.default_rng(seed)
+    params = []
+    for (fi, fo), d, bq, br in zip(zip(sizes[:-1], sizes[1:]), (0.05, 0.01, 0.02), (3, 6, 9), (8, 16, 16)):
+        W = (rng.choice([-1.0, 0.0, 1.0], size=(fo, fi), p=[d / 2, 1 - d, d / 2]) * 0.125).astype(np.float32)
+        b = (rng.integers(-br, br + 1, fo) * 2.0 ** -bq).astype(np.float32)
+        params.append((W, b))
+    x = rng.integers(-2, 3, (batch, sizes[0])).astype(np.float32)
+    y = (rng.random((batch, sizes[-1])) < 0.1).astype(np.float32)
+    _, (_, a1, _, a2, _, _) = omlp.forward(params, x)
+    for a in (a1, a2):
+        r = np.maximum(a, 0.0)
+        assert np.array_equal(omlp.bf16_round(r), r), "hidden activations must be exact in BF16"
+    return params, x, y
+
+
+def _check_blocks(got_flat, bounds, sizes, keys=("dW1", "db1", "dW2", "db2", "dW3", "db3")):
+    got = unflat(got_flat, sizes)
+    named = {"dW1": got[0][0], "db1": got[0][1], "dW2": got[1][0], "db2": got[1][1],
+             "dW3": got[2][0], "db3": got[2][1]}
+    for k in keys:
+        want, bound = bounds[k]
+        MB.check(k, named[k], want, bound)
+
+
+# ---- each product on identical BF16 operands ---------------------------------
+
+def _bf16_dev(a):
     import torch
-    net, params = _net_with_oracle_params(SIZES, seed=4, max_batch=512)
-    x, _ = _data(batch, SIZES, seed=batch)
+    return torch.from_numpy(np.ascontiguousarray(omlp.bf16_round(a))).to(torch.bfloat16).cuda()
+
+
+# (M, N, K used, K padded, epilogue): the network's eight products at batch 250
+# (K = 300 padded to 320, n_out 200 to 224, batch 250 to 256), and ragged
+# small shapes at K = 32, 320, 512
+NETWORK_PRODUCTS = [
+    ("a1 = x W1^T", 250, 512, 300, 320, lpb.LPB_EPI_BIAS_RELU),
+    ("a2 = h1 W2^T", 250, 512, 512, 512, lpb.LPB_EPI_BIAS_RELU),
+    ("z = h2 W3^T", 250, 200, 512, 512, lpb.LPB_EPI_BIAS),
+    ("dW3 = g3^T h2", 200, 512, 250, 256, lpb.LPB_EPI_STORE),
+    ("g2 = g3 W3 * mask", 250, 512, 200, 224, lpb.LPB_EPI_MASK_GRAD),
+    ("dW2 = g2^T h1", 512, 512, 250, 256, lpb.LPB_EPI_STORE),
+    ("g1 = g2 W2 * mask", 250, 512, 512, 512, lpb.LPB_EPI_MASK_GRAD),
+    ("dW1 = g1^T x", 512, 300, 250, 256, lpb.LPB_EPI_STORE),
+    ("ragged K=32", 77, 45, 32, 32, lpb.LPB_EPI_BIAS_RELU),
+    ("ragged K=320", 130, 200, 300, 320, lpb.LPB_EPI_MASK_GRAD),
+    ("ragged K=512", 129, 65, 512, 512, lpb.LPB_EPI_BIAS),
+    ("ragged K=32 store", 1, 1, 32, 32, lpb.LPB_EPI_STORE),
+]
+
+
+@pytest.mark.parametrize("form", [lpb.LPB_GEMM_MMA64, lpb.LPB_GEMM_MMA128])
+@pytest.mark.parametrize("case", NETWORK_PRODUCTS, ids=[c[0] for c in NETWORK_PRODUCTS])
+def test_product_elementwise(case, form):
+    """One product with its epilogue through lp_mlp_gemm_bf16 against the
+    oracle's product (_mm) of the same BF16 operands, element by element;
+    padding of every output left untouched; h and hT the BF16 rounding of
+    the kernel's own FP32 value, bit for bit."""
+    import torch
+    name, M, N, K, Kp, epi = case
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    lda, ldb = Kp + 8, Kp
+    A = np.zeros((M, lda), np.float32)
+    A[:, :K] = rng.standard_normal((M, K))
+    B = np.zeros((N, ldb), np.float32)
+    B[:, :K] = rng.uniform(-0.2, 0.2, (N, K))
+    A, B = omlp.bf16_round(A), omlp.bf16_round(B)
+    bias = (rng.standard_normal(N) * 0.3).astype(np.float32)
+    pre = rng.standard_normal((M, N)).astype(np.float32)
+    pre[rng.random((M, N)) < 0.05] = 0.0
+    ldc, ldh, ldt = N + 3, N + 5, M + 7
+    C = torch.full((M + 1, ldc), float("nan"), dtype=torch.float32, device="cuda")
+    pre_d = torch.zeros((M, ldc), dtype=torch.float32, device="cuda")
+    pre_d[:, :N] = torch.from_numpy(pre).cuda()
+    sentinel = -3072.0  # exact in BF16
+    h = torch.full((M + 1, ldh), sentinel, dtype=torch.bfloat16, device="cuda")
+    hT = torch.full((N + 1, ldt), sentinel, dtype=torch.bfloat16, device="cuda")
+    use_h = epi in (lpb.LPB_EPI_BIAS_RELU, lpb.LPB_EPI_MASK_GRAD)
+    lpb.lp_mlp_gemm_bf16(epi, form, M, N, Kp, _bf16_dev(A), lda, _bf16_dev(B), ldb, C, ldc,
+                         _dev(bias), pre_d, h if use_h else None, ldh, hT if use_h else None, ldt)
+    torch.cuda.synchronize()
+    Cn = C.cpu().numpy()
+    got = Cn[:M, :N].astype(np.float64)
+    assert np.isnan(Cn[M]).all() and np.isnan(Cn[:, N:]).all(), "C written outside [M x N]"
+    acc = omlp._mm(A[:, :Kp], B[:, :Kp].T).astype(np.float64)
+    e = MB.mm_err(A[:, :Kp].astype(np.float64), 0.0, B[:, :Kp].T.astype(np.float64), 0.0, Kp)
+    if epi == lpb.LPB_EPI_STORE:
+        want, bound = acc, e
+    elif epi in (lpb.LPB_EPI_BIAS, lpb.LPB_EPI_BIAS_RELU):
+        want = (acc.astype(np.float32) + bias).astype(np.float64)
+        bound = MB.bias_err(e, want)
+    else:
+        want = np.where(pre > 0, acc, 0.0)
+        bound = np.where(pre > 0, e, 0.0)
+    MB.check(name, got, want, bound)
+    if use_h:
+        hn = h.float().cpu().numpy()
+        hTn = hT.float().cpu().numpy()
+        assert (hn[M] == sentinel).all() and (hn[:, N:] == sentinel).all(), "h written outside [M x N]"
+        assert (hTn[N] == sentinel).all() and (hTn[:, M:] == sentinel).all(), "hT written outside [N x M]"
+        own = np.maximum(got, 0.0) if epi == lpb.LPB_EPI_BIAS_RELU else got
+        np.testing.assert_array_equal(hn[:M, :N], omlp.bf16_round(own.astype(np.float32)))
+        np.testing.assert_array_equal(hTn[:N, :M], hn[:M, :N].T)
+
+
+def test_product_argument_errors():
+    import torch
+    z = torch.zeros((64, 64), dtype=torch.bfloat16, device="cuda")
+    C = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
+    with pytest.raises(lpb.LPBError) as e:      # K not a multiple of 32
+        lpb.lp_mlp_gemm_bf16(lpb.LPB_EPI_STORE, 0, 64, 64, 48, z, 64, z, 64, C, 64)
+    assert e.value.code == lpb.LPB_EINVAL
+    with pytest.raises(lpb.LPBError) as e:      # bias missing
+        lpb.lp_mlp_gemm_bf16(lpb.LPB_EPI_BIAS, 0, 64, 64, 64, z, 64, z, 64, C, 64)
+    assert e.value.code == lpb.LPB_EINVAL
+    with pytest.raises(lpb.LPBError) as e:      # host memory
+        lpb.lp_mlp_gemm_bf16(lpb.LPB_EPI_STORE, 0, 4, 4, 32, np.zeros((4, 32), np.uint16), 32,
+                             np.zeros((4, 32), np.uint16), 32, np.zeros((4, 4), np.float32), 4)
+    assert e.value.code == lpb.LPB_EINVAL
+    with pytest.raises(lpb.LPBError) as e:      # unknown form
+        lpb.lp_mlp_gemm_bf16(lpb.LPB_EPI_STORE, 99, 64, 64, 64, z, 64, z, 64, C, 64)
+    assert e.value.code == lpb.LPB_EINVAL
+
+
+# ---- the network -----------------------------------------------------------------
+
+@pytest.mark.parametrize("batch", [1, 37, 300])
+def test_forward_exact_network_bitwise(batch):
+    """On a network whose forward pass is exact on both sides the logits equal
+    the oracle's bit for bit (every product, bias and ReLU of lp_mlp_forward
+    checked at once, in both GEMM forms for the larger batch sizes)."""
+    import torch
+    params, x, _ = dyadic_network(SIZES, seed=batch, batch=batch)
+    net = lpb.Mlp(*SIZES, max_batch=512, seed=0)
+    net.set_params(flat(params))
     logits = torch.empty((batch, SIZES[-1]), dtype=torch.float32, device="cuda")
     net.forward(_dev(x), logits)
     torch.cuda.synchronize()
-    got = logits.cpu().numpy()
     want, _ = omlp.forward(params, x)
-    scale = float(np.std(want)) + 1e-6
-    assert np.max(np.abs(got - want)) <= 2e-2 * scale, np.max(np.abs(got - want)) / scale
-    assert np.mean(np.abs(got - want)) <= 1e-3 * scale
+    np.testing.assert_array_equal(logits.cpu().numpy(), want)
     net.close()
 
 
 def test_large_batch_forward_tiled_kernel():
     """Batches whose 128 x 128 tiles fill the GPU take the tiled GEMM (cp.async
-    stages, ldmatrix fragments): logits match the oracle, and bit for bit the
-    small-tile kernel's on the same rows (forwarded in pieces too small for the
-    tiled kernel; each row's result does not depend on the batch)."""
+    stages, ldmatrix fragments): logits bit for bit the small-tile kernel's on
+    the same rows (forwarded in pieces too small for the tiled kernel), and,
+    on an exact network, bit for bit the oracle's."""
     import torch
-    net, params = _net_with_oracle_params(SIZES, seed=5, max_batch=512)
-    batch = 6000
-    x, _ = _data(batch, SIZES, seed=17)
-    dx = _dev(x)
-    whole = torch.empty((batch, SIZES[-1]), dtype=torch.float32, device="cuda")
-    net.forward(dx, whole)
-    pieces = torch.empty_like(whole)
-    for r0 in range(0, batch, 1000):
-        net.forward(dx[r0:r0 + 1000], pieces[r0:r0 + 1000])
-    torch.cuda.synchronize()
-    np.testing.assert_array_equal(whole.cpu().numpy(), pieces.cpu().numpy())
-    want, _ = omlp.forward(params, x)
-    got = whole.cpu().numpy()
-    scale = float(np.std(want)) + 1e-6
-    assert np.max(np.abs(got - want)) <= 2e-2 * scale
-    assert np.mean(np.abs(got - want)) <= 1e-3 * scale
+    for kind in ("random", "exact"):
+        batch = 6000
+        if kind == "random":
+            net, params = _net_with_oracle_params(SIZES, seed=5, max_batch=512)
+            x, _ = _data(batch, SIZES, seed=17)
+        else:
+            params, x, _ = dyadic_network(SIZES, seed=23, batch=batch)
+            net = lpb.Mlp(*SIZES, max_batch=512, seed=0)
+            net.set_params(flat(params))
+        dx = _dev(x)
+        whole = torch.empty((batch, SIZES[-1]), dtype=torch.float32, device="cuda")
+        net.forward(dx, whole)
+        pieces = torch.empty_like(whole)
+        for r0 in range(0, batch, 1000):
+            net.forward(dx[r0:r0 + 1000], pieces[r0:r0 + 1000])
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(whole.cpu().numpy(), pieces.cpu().numpy())
+        if kind == "exact":
+            want, _ = omlp.forward(params, x)
+            np.testing.assert_array_equal(whole.cpu().numpy(), want)
+        net.close()
+
+
+@pytest.mark.parametrize("batch", [64, 250])
+def test_gradients_layerwise_elementwise(batch):
+    """lp_mlp_gradients_at from the oracle's own forward values (x, a1, a2,
+    z): the loss and every gradient element within its propagated bound."""
+    net, params = _net_with_oracle_params(SIZES, seed=7, max_batch=256)
+    x, y = _data(batch, SIZES, seed=11)
+    _, (_, a1, _, a2, _, z) = omlp.forward(params, x)
+    g, loss = net.gradients_at(_dev(x), _dev(a1), _dev(a2), _dev(z), _dev(y), pos_weight=5.0)
+    bounds = MB.network_bounds(params, x, y.astype(np.float64), 5.0, forward_exact=True)
+    want_loss, e_loss = bounds["loss"]
+    assert abs(loss - want_loss) <= e_loss, (loss, want_loss)
+    _check_blocks(g, bounds, SIZES)
     net.close()
 
 
 @pytest.mark.parametrize("batch", [64, 250])
-def test_gradients_match_oracle(batch):
-    net, params = _net_with_oracle_params(SIZES, seed=7, max_batch=256)
-    x, y = _data(batch, SIZES, seed=11)
-    g, loss = net.gradients(_dev(x), _dev(y), pos_weight=5.0)
-    z, cache = omlp.forward(params, x)
-    want_loss, g3 = omlp.loss_and_grad_logits(z, y, pos_weight=5.0)
-    want = flat(omlp.backward(params, cache, g3))
-    assert loss == pytest.approx(want_loss, rel=1e-3)
-    got_blocks = unflat(g, SIZES)
-    want_blocks = unflat(want, SIZES)
-    for li, ((gW, gb), (wW, wb)) in enumerate(zip(got_blocks, want_blocks)):
-        for name, a, b in (("W", gW, wW), ("b", gb, wb)):
-            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-            assert rel <= 1e-2, f"layer {li + 1} d{name}: relative error {rel:.3e}"
+def test_gradients_whole_network_elementwise(batch):
+    """lp_mlp_gradients (forward and backward in one call) on a network whose
+    forward pass is exact: the loss and every gradient element within the
+    backward pass's propagated bound."""
+    params, x, y = dyadic_network(SIZES, seed=100 + batch, batch=batch)
+    net = lpb.Mlp(*SIZES, max_batch=256, seed=0)
+    net.set_params(flat(params))
+    g, loss = net.gradients(_dev(x), _dev(y), pos_weight=3.0)
+    bounds = MB.network_bounds(params, x, y.astype(np.float64), 3.0, forward_exact=True)
+    want_loss, e_loss = bounds["loss"]
+    assert abs(loss - want_loss) <= e_loss, (loss, want_loss)
+    _check_blocks(g, bounds, SIZES)
     net.close()
 
 
