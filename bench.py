@@ -30,11 +30,13 @@ if ROOT not in sys.path:
 
 METRIC = "LPs solved/s on 1 GB300 vs plain FP64 GPU simplex at <=1e-9 rel obj err; % roofline"
 DEFAULT_WORKLOAD = "dense50x50_phase1_100k"
-# FP64 roofline denominator: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
-# (the GB300's nominal 1.25 TFLOP/s FP64 at the maximum SM clock).
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
-# FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz.
-FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
+# Nominal unit throughputs (used only if the library's own microbenchmarks,
+# lpb_measure_peaks, cannot run): FP64 FMA pipe 152 SMs x 2 FMA/clk x 2 flop x
+# 2.07 GHz (the GB300's nominal 1.25 TFLOP/s FP64); FP32 FMA pipe 152 x 128 x 2
+# x 2.07 GHz; shared memory 152 SMs x 128 bytes/clk x 2.07 GHz.
+FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.070
+FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.070
+SMEM_NOMINAL_GBS = 152 * 128 * 2.070
 # HBM bandwidth of a GB300 measured with a STREAM-style copy (read + write bytes)
 HBM_PEAK_GBS = 6784.5
 # DRAM bytes per LP (read + write) from ncu captures of the kernels as they are
@@ -59,6 +61,8 @@ def parse():
     p.add_argument("--num-lps", type=int, default=None, help="override the workload's batch size")
     p.add_argument("--cpu-sample", type=int, default=20000, help="LPs timed for the CPU oracle baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--per-lp-file", default=None,
+                   help="write the headline's per-LP errors against the oracle (npz) to this path")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-chunks", type=int, default=0,
                    help="chunks of lp_solve_host in the end-to-end measurement (0: the library's choice)")
@@ -66,6 +70,9 @@ def parse():
     p.add_argument("--no-warm", action="store_true", help="skip the learned warm-start measurement")
     p.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch measurement")
     p.add_argument("--no-support", action="store_true", help="skip the support-function measurement")
+    p.add_argument("--no-c1", action="store_true", help="skip the 1000 LPs of 5 x 5 measurement")
+    p.add_argument("--oracle-sample", type=int, default=2000,
+                   help="LPs of each secondary workload compared with the oracle (uneven: a fifth of it)")
     p.add_argument("--support-dirs", type=int, default=100_000, help="directions of the support-function measurement")
     p.add_argument("--uneven-lps", type=int, default=20_000, help="LPs of the uneven-batch measurement")
     p.add_argument("--warm-train", type=int, default=1_000_000, help="self-solved LPs the network is trained on")
@@ -155,18 +162,53 @@ class ClockSampler:
         return out
 
 
-def cpu_oracle_rate(batch, sample: int, threads: int):
-    """The oracle as it stands, on `sample` LPs of the batch, on `threads`
-    host threads.  Returns LPs/s and the wall time."""
+def sample_indices(num_lps: int, sample: int) -> np.ndarray:
+    """`sample` evenly spaced LP indices of a batch."""
+    k = min(sample, num_lps)
+    return np.linspace(0, num_lps - 1, k).astype(np.int64)
+
+
+def cpu_oracle_run(batch, idx, threads: int):
+    """The oracle as it stands on LPs idx of the batch, on `threads` host
+    threads.  Returns (LPs/s, wall seconds, oracle results)."""
     import oracle
-    k = min(sample, batch.num_lps)
-    idx = np.linspace(0, batch.num_lps - 1, k).astype(np.int64)
     lps = [batch.lp(int(i)) for i in idx]
     oracle.lib()
     t0 = time.perf_counter()
-    oracle.solve_batch(lps, threads=threads)
+    res = oracle.solve_batch(lps, threads=threads)
     dt = time.perf_counter() - t0
-    return k / dt, dt, k
+    return len(idx) / dt, dt, res
+
+
+def cpu_oracle_rate(batch, sample: int, threads: int):
+    """Oracle LPs/s on `sample` evenly spaced LPs (rate, wall time, count)."""
+    idx = sample_indices(batch.num_lps, sample)
+    rate, dt, _ = cpu_oracle_run(batch, idx, threads)
+    return rate, dt, len(idx)
+
+
+def vs_oracle(status, obj, idx, ores) -> dict:
+    """Per-LP agreement of GPU results (status, obj over the whole batch) with
+    the oracle's on LPs idx: status mismatches and the distribution of the
+    relative objective error |obj - obj*| / max(1, |obj*|) over the LPs the
+    oracle finds optimal."""
+    st = np.asarray(status)[idx]
+    so = np.asarray(ores["status"])
+    opt = so == 0
+    rel = np.abs(np.asarray(obj)[idx][opt] - np.asarray(ores["obj"])[opt]) / np.maximum(1.0, np.abs(ores["obj"][opt]))
+    out = {"lps_compared": int(len(idx)), "status_mismatches": int(np.sum(st != so)),
+           "optimal_lps": int(opt.sum())}
+    if rel.size:
+        out["rel_obj_err"] = {"max": float(rel.max()), "p99": float(np.quantile(rel, 0.99)),
+                              "median": float(np.median(rel)), "count_above_1e-9": int(np.sum(rel > 1e-9))}
+    return out
+
+
+def bench_config(workload: str, batch) -> dict:
+    """The workload description shared by both arms' JSON lines."""
+    in_bytes = (batch.A.size + batch.b.size + batch.c.size) * 8
+    return {"workload": workload, "num_lps_per_gpu": int(batch.num_lps),
+            "l2": f"inputs larger than L2 ({in_bytes / 1e9:.2f} GB of A,b,c per step vs 0.13 GB L2)"}
 
 
 def run_reference(args):
@@ -189,7 +231,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "num_lps": batch.num_lps},
+        "config": bench_config(args.workload, batch),
         "cpu_baseline": {"value": value, "unit": "LPs/s", "cores": threads, "kind": "oracle",
                          "sample": f"{sample} of {batch.num_lps} LPs per step, evenly spaced indices"},
         "e2e": {"value": value, "unit": "LPs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -212,6 +254,18 @@ def run_ours(args):
     from paper_1802_08557_gb300 import workloads as W
     build.build()
     lpb.load()
+
+    # roofline denominators of the FP64 / FP32 / shared-memory bound kernels,
+    # measured on this device by the library's microbenchmarks
+    try:
+        peaks = lpb.lpb_measure_peaks(torch.cuda.current_stream(dev))
+        peaks["source"] = "measured (lpb_measure_peaks: FMA chains and 16-byte shared-memory loads+stores, all SMs)"
+    except Exception as ex:  # noqa: BLE001
+        peaks = {"fp64_gflops": FP64_NOMINAL_GFLOPS, "fp32_gflops": FP32_NOMINAL_GFLOPS,
+                 "smem_gbs": SMEM_NOMINAL_GBS, "source": f"nominal (measurement failed: {ex})"}
+    FP64_PEAK_GFLOPS = peaks["fp64_gflops"]
+    FP32_PEAK_GFLOPS = peaks["fp32_gflops"]
+    SMEM_PEAK_GBS = peaks["smem_gbs"]
 
     batch = make_batch(args.workload, args.num_lps, rank)
     N = batch.num_lps
@@ -287,6 +341,7 @@ def run_ours(args):
 
     # ---- plain FP64 GPU simplex on the same data (the comparison) ----------
     fp64 = None
+    r64 = None
     if head_prec != lpb.LP_PREC_FP64:
         h64 = create(lpb.LP_PREC_FP64)
         e64, s64, _, stages64 = timed(h64, args.steps, args.warmup)
@@ -296,8 +351,9 @@ def run_ours(args):
         rel = np.abs(res["obj"][opt] - r64["obj"][opt]) / np.maximum(1.0, np.abs(r64["obj"][opt]))
         fp64 = {"value": N * ws * args.steps / (e64 * 1e-3), "unit": "LPs/s", "ms_per_step": e64 / args.steps,
                 "speedup_of_headline": value / (N * ws * args.steps / (e64 * 1e-3)),
-                "status_mismatches": int(np.sum(res["status"] != r64["status"])),
-                "max_rel_obj_err_on_optimal": float(rel.max()) if rel.size else 0.0}
+                "headline_vs_fp64_gpu": {"lps_compared": N,
+                                         "status_mismatches": int(np.sum(res["status"] != r64["status"])),
+                                         "max_rel_obj_err_on_optimal": float(rel.max()) if rel.size else 0.0}}
         fp64_fmas = algorithmic_fmas(batch, r64["iters"])
         fp64_kernel_ms = stages64[0]
         fp64["roofline"] = {"bound": "alu", "kernel": "fp64_resident_kernel",
@@ -316,24 +372,30 @@ def run_ours(args):
         roofline = {"bound": "alu", "kernel": "fp64_resident_kernel", "achieved": achieved,
                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
                     "traffic": None, "kernel_ms": kernel_ms,
-                    "peak_note": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF)",
+                    "peak_source": peaks["source"],
                     "work": "sum over LPs of pivots x (m+1)(n+1) FMAs"}
     else:
-        # FP32 tableau pivots: (m+1)(n+1) FMAs each on the FP32 pipe
-        achieved = 2.0 * fmas / (kernel_ms * 1e-3) / 1e9
+        # FP32 tableau pivots in shared memory: each pivot reads and writes the
+        # (m+1)(n+1) FP32 tableau once (algorithmic bytes), and does (m+1)(n+1)
+        # FMAs on the FP32 pipe
+        smem_bytes = 2.0 * 4.0 * fmas
+        achieved = smem_bytes / (kernel_ms * 1e-3) / 1e9
+        flops = 2.0 * fmas / (kernel_ms * 1e-3) / 1e9
         mixed_threads = {g["threads"] for g in lpb.lp_batch_groups(h) if g["kind"] == 0}
         mixed_name = "mixed_warp_kernel" if mixed_threads == {32} else "mixed_kernel"
-        roofline = {"bound": "alu", "kernel": mixed_name, "achieved": achieved,
-                    "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP32_PEAK_GFLOPS,
+        roofline = {"bound": "smem", "kernel": mixed_name, "achieved": achieved,
+                    "peak": SMEM_PEAK_GBS, "unit": "GB/s", "frac": achieved / SMEM_PEAK_GBS,
+                    "peak_source": peaks["source"],
                     "traffic": MIXED_DRAM_BYTES_PER_LP * N if mixed_name == "mixed_warp_kernel" else None,
                     "traffic_note": "DRAM bytes per step: the ncu capture's read+write per LP (A, b, c once, "
-                                    "outputs) x the step's LPs; algorithmic bytes of the inputs alone: "
-                                    f"{in_bytes:.4g}",
+                                    "outputs) x the step's LPs; the tableau itself never leaves shared memory; "
+                                    f"algorithmic DRAM bytes of the inputs alone: {in_bytes:.4g}",
                     "kernel_ms": kernel_ms, "fallback_ms": fallback_ms,
-                    "peak_note": "FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz",
-                    "work": "sum over LPs of reported pivots x (m+1)(n+1) FMAs (FP32 pivots of certified LPs; "
-                            "the FP64 re-solve's pivots stand in for those of uncertified LPs; FP64 certificate "
-                            "work not counted)",
+                    "work": "shared-memory bytes: sum over LPs of reported pivots x 2 x (m+1)(n+1) x 4 (the FP32 "
+                            "tableau read and written once per pivot; FP32 pivots of certified LPs, the FP64 "
+                            "re-solve's pivots for uncertified ones; build and FP64 certificate not counted)",
+                    "fp32_pipe": {"achieved_gflops": flops, "peak_gflops": FP32_PEAK_GFLOPS,
+                                  "frac": flops / FP32_PEAK_GFLOPS},
                     "timing": f"CUDA events around the solve's launch groups (all {mixed_name} launches, "
                               "fork to join), mean of the timed steps"}
 
@@ -409,10 +471,45 @@ def run_ours(args):
         rel = np.abs(r32s["obj"][opt] - r64s["obj"][opt]) / np.maximum(1.0, np.abs(r64s["obj"][opt]))
         support["value"] = support["fp32r"]["value"]
         support["speedup_over_fp64"] = support["fp32r"]["value"] / support["fp64"]["value"]
-        support["status_mismatches"] = int(np.sum(r32s["status"] != r64s["status"]))
-        support["max_rel_obj_err_on_optimal"] = float(rel.max()) if rel.size else 0.0
+        support["fp32r_vs_fp64_gpu"] = {"lps_compared": int(sb.num_lps),
+                                        "status_mismatches": int(np.sum(r32s["status"] != r64s["status"])),
+                                        "max_rel_obj_err_on_optimal": float(rel.max()) if rel.size else 0.0}
+        if rank == 0:
+            idx_s = sample_indices(sb.num_lps, args.oracle_sample)
+            _, _, o_s = cpu_oracle_run(sb, idx_s, os.cpu_count() or 1)
+            support["vs_oracle"] = {lab: vs_oracle(res_s[lab]["status"], res_s[lab]["obj"], idx_s, o_s)
+                                    for lab in ("fp64", "fp32r")}
         support["timing"] = "CUDA events on the solve's stream around K whole solves"
         del sb, res_s
+
+    # ---- 1000 LPs of 5 x 5 (positive data, slack basis feasible) -----------
+    c1 = None
+    if not args.no_c1:
+        b1 = make_batch("dense5x5_1k", None, rank)
+        c1 = {"workload": f"dense5x5_{b1.num_lps}", "unit": "LPs/s"}
+        for label, prec in (("fp64", lpb.LP_PREC_FP64), ("fp32r", lpb.LP_PREC_FP32_REFINE)):
+            h1_ = lpb.BatchSolver(b1, opts=lpb.lpb_default_opts(precision=prec), stream=stream)
+            ms = ev_time(lambda: lpb.lp_batch_solve(h1_.h, stream))
+            r1 = h1_.results()
+            h1_.close()
+            fl1 = 2.0 * algorithmic_fmas(b1, r1["iters"])
+            c1[label] = {"value": b1.num_lps * ws / (ms * 1e-3), "ms_per_step": ms, "result": r1,
+                         "fp64_pipe_frac": fl1 / (ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS}
+        c1["value"] = c1["fp64"]["value"]
+        c1["timing"] = ("CUDA events on the solve's stream around K whole solves; one launch of 1000 tiny CTAs, "
+                        "so the time is launch and latency, not throughput")
+        if rank == 0:
+            idx1 = np.arange(b1.num_lps)
+            r_one, dt_one, o1 = cpu_oracle_run(b1, idx1, 1)
+            r_all, dt_all, _ = cpu_oracle_run(b1, idx1, os.cpu_count() or 1)
+            c1["cpu_oracle"] = {"one_thread": r_one, "all_threads": r_all, "cores": os.cpu_count() or 1,
+                                "unit": "LPs/s", "sample": f"all {b1.num_lps} LPs"}
+            for label in ("fp64", "fp32r"):
+                c1[label]["vs_oracle"] = vs_oracle(c1[label]["result"]["status"], c1[label]["result"]["obj"],
+                                                   idx1, o1)
+        for label in ("fp64", "fp32r"):
+            del c1[label]["result"]
+        del b1
 
     # ---- uneven batch: m, n log-uniform in [10, 500], 2e4 LPs ----------------
     uneven = None
@@ -421,6 +518,7 @@ def run_ours(args):
         um, un = ub.m.astype(np.float64), ub.n.astype(np.float64)
 
         uneven = {"workload": f"uneven10to500_{ub.num_lps}", "unit": "LPs/s"}
+        res_u = {}
         for label, prec in (("fp64", lpb.LP_PREC_FP64), ("fp32r", lpb.LP_PREC_FP32_REFINE)):
             hu = lpb.BatchSolver(ub, opts=lpb.lpb_default_opts(precision=prec), stream=stream)
             ms_default = ev_time(lambda: lpb.lp_batch_solve(hu.h, stream))
@@ -429,6 +527,7 @@ def run_ours(args):
             ms_tuned = ev_time(lambda: lpb.lp_batch_solve(hu.h, stream))
             ms_graph = ev_time(lambda: lpb.lp_batch_solve_graph(hu.h, stream))
             rt = hu.results()
+            res_u[label] = rt
             groups = lpb.lp_batch_groups(hu.h)
             hu.close()
             best = min(ms_tuned, ms_graph)
@@ -442,6 +541,19 @@ def run_ours(args):
                 "achieved_gflops": fl / (best * 1e-3) / 1e9, "fp64_peak_gflops": FP64_PEAK_GFLOPS,
             }
         uneven["value"] = max(uneven["fp64"]["value"], uneven["fp32r"]["value"])
+        opt_u = res_u["fp64"]["status"] == 0
+        rel_u = (np.abs(res_u["fp32r"]["obj"][opt_u] - res_u["fp64"]["obj"][opt_u])
+                 / np.maximum(1.0, np.abs(res_u["fp64"]["obj"][opt_u])))
+        uneven["fp32r_vs_fp64_gpu"] = {
+            "lps_compared": int(ub.num_lps),
+            "status_mismatches": int(np.sum(res_u["fp32r"]["status"] != res_u["fp64"]["status"])),
+            "max_rel_obj_err_on_optimal": float(rel_u.max()) if rel_u.size else 0.0}
+        if rank == 0:
+            idx_u = sample_indices(ub.num_lps, max(50, args.oracle_sample // 5))
+            _, dt_u, o_u = cpu_oracle_run(ub, idx_u, os.cpu_count() or 1)
+            uneven["vs_oracle"] = {lab: vs_oracle(res_u[lab]["status"], res_u[lab]["obj"], idx_u, o_u)
+                                   for lab in ("fp64", "fp32r")}
+            uneven["vs_oracle"]["sample"] = f"{len(idx_u)} evenly spaced LPs (oracle {dt_u:.1f} s)"
         uneven["timing"] = "CUDA events on the solve's stream around K whole solves (default plan, autotuned plan, graph replay)"
         del ub
 
@@ -493,6 +605,12 @@ def run_ours(args):
         opt = rc["status"] == 0
         rel = np.abs(rw["obj"][opt] - rc["obj"][opt]) / np.maximum(1.0, np.abs(rc["obj"][opt]))
         nt_ = test_set.num_lps
+        warm_oracle = None
+        if rank == 0:
+            idx_w = sample_indices(nt_, args.oracle_sample)
+            _, _, o_w = cpu_oracle_run(test_set, idx_w, os.cpu_count() or 1)
+            warm_oracle = {"warm": vs_oracle(rw["status"], rw["obj"], idx_w, o_w),
+                           "cold_fp64": vs_oracle(rc["status"], rc["obj"], idx_w, o_w)}
         warm = {
             "workload": f"shared200x100_test{nt_}",
             "value": nt_ * ws * args.steps / (e_warm * 1e-3), "unit": "LPs/s", "ms_per_step": e_warm / args.steps,
@@ -500,8 +618,10 @@ def run_ours(args):
             "speedup_over_cold_fp64": e_cold / e_warm,
             "certified_fraction": pw["num_warm_certified"] / nt_,
             "restricted_solves_per_lp": pw["num_warm_rounds"] / nt_,
-            "status_mismatches_vs_cold": int(np.sum(rw["status"] != rc["status"])),
-            "max_rel_obj_err_vs_cold": float(rel.max()) if rel.size else 0.0,
+            "warm_vs_cold_fp64_gpu": {"lps_compared": int(nt_),
+                                      "status_mismatches": int(np.sum(rw["status"] != rc["status"])),
+                                      "max_rel_obj_err_on_optimal": float(rel.max()) if rel.size else 0.0},
+            "vs_oracle": warm_oracle,
             "training": {"lps": tinfo["train_lps"], "steps": tinfo["steps"], "seconds": train_s,
                          "first_loss": tinfo["first_loss"], "last_loss": tinfo["last_loss"],
                          "what": "cold FP64 solve of the training LPs + features/labels + Adam steps, all on the GPU"},
@@ -536,7 +656,7 @@ def run_ours(args):
 
         e2e_step()
         torch.cuda.synchronize()
-        e2e_steps = max(1, min(args.steps, 3))
+        e2e_steps = max(3, args.steps)
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
@@ -549,11 +669,27 @@ def run_ours(args):
                       f"in {'the library default' if args.e2e_chunks == 0 else args.e2e_chunks} chunks)"}
 
     cpu = None
+    headline_vs_oracle = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        rate, dt, k = cpu_oracle_rate(batch, args.cpu_sample, threads)
+        idx_h = sample_indices(N, args.cpu_sample)
+        rate, dt, o_h = cpu_oracle_run(batch, idx_h, threads)
+        idx_1 = sample_indices(N, max(100, args.cpu_sample // 10))
+        rate_1, dt_1, _ = cpu_oracle_run(batch, idx_1, 1)
         cpu = {"value": rate, "unit": "LPs/s", "cores": threads, "kind": "oracle",
-               "sample": f"{k} of {N} LPs (evenly spaced indices), {dt:.1f} s wall"}
+               "sample": f"{len(idx_h)} of {N} LPs (evenly spaced indices), {dt:.1f} s wall",
+               "one_thread": {"value": rate_1, "unit": "LPs/s", "cores": 1,
+                              "sample": f"{len(idx_1)} of {N} LPs (evenly spaced), {dt_1:.1f} s wall"}}
+        # per-LP accuracy of both GPU paths against the oracle on the same LPs
+        headline_vs_oracle = vs_oracle(res["status"], res["obj"], idx_h, o_h)
+        if fp64 is not None:
+            fp64["vs_oracle"] = vs_oracle(r64["status"], r64["obj"], idx_h, o_h)
+        if args.per_lp_file:
+            st_h = res["status"][idx_h]
+            rel_h = np.where(o_h["status"] == 0,
+                             np.abs(res["obj"][idx_h] - o_h["obj"]) / np.maximum(1.0, np.abs(o_h["obj"])), np.nan)
+            np.savez_compressed(args.per_lp_file, lp_index=idx_h, oracle_status=o_h["status"], gpu_status=st_h,
+                                oracle_obj=o_h["obj"], gpu_obj=res["obj"][idx_h], rel_obj_err=rel_h)
 
     lpb.lp_batch_destroy(h)
     if rank == 0:
@@ -565,10 +701,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if head_prec == lpb.LP_PREC_FP64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "num_lps_per_gpu": N,
-                       "precision": "fp64" if head_prec == lpb.LP_PREC_FP64 else
-                       "fp32 tableau + fp64 certificate (fp64 re-solve of uncertified LPs)",
-                       "l2": f"inputs larger than L2 ({in_bytes / 1e9:.2f} GB of A,b,c per step vs 0.13 GB L2)",
+            "config": bench_config(args.workload, batch),
+            "run": {"precision": "fp64" if head_prec == lpb.LP_PREC_FP64 else
+                    "fp32 tableau + fp64 certificate (fp64 re-solve of uncertified LPs)",
                        "launch_groups": launches, "phase1_lps": info["num_phase1"],
                        "fp64_fallback_lps": info["num_fallback"],
                        "kernel_self_check_failures": info["internal_errors"],
@@ -577,7 +712,10 @@ def run_ours(args):
                                          "numerical": int(counts[4])},
                        "mean_pivots": float(res["iters"].mean())},
             "roofline": roofline,
+            "vs_oracle": headline_vs_oracle,
+            "peaks": peaks,
             "fp64_plain": fp64,
+            "dense5x5": c1,
             "hyperbox": hyperbox,
             "warm_start": warm,
             "support_function": support,

@@ -480,6 +480,20 @@ lpb_err lp_batch_solve_warm(lp_batch *h, lp_mlp *net, float threshold, void *str
 lpb_err lp_batch_features(lp_batch *h, float *x, void *stream);
 lpb_err lp_batch_active_labels(lp_batch *h, float *labels, void *stream);
 
+/* Throughputs of the units the solver's kernels are bound by, measured on the
+ * current device by microbenchmarks (CUDA events, best of 5 launches over
+ * every SM): FP64 and FP32 fused multiply-add (2 flops each), and shared
+ * memory (16-byte loads plus stores, bytes moved both ways).  They are the
+ * denominators of the roofline fractions the benchmark reports.  Waits for
+ * the GPU; allocates a small temporary buffer.  No counterpart in the paper. */
+typedef struct {
+    double fp64_gflops;
+    double fp32_gflops;
+    double smem_gbs;
+    int32_t num_sms;
+} lpb_peaks;
+lpb_err lpb_measure_peaks(lpb_peaks *out, void *stream);
+
 /* Free the batch (waits for its pending work).  NULL is accepted. */
 lpb_err lp_batch_destroy(lp_batch *h);
 

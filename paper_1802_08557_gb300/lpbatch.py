@@ -33,7 +33,7 @@ EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_r
             "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients", "lp_mlp_destroy", "lp_batch_solve_warm",
             "lp_batch_features", "lp_batch_active_labels", "lp_batch_solve_graph", "lp_batch_autotune",
             "lp_batch_group_info", "lp_batch_set_group_form", "lp_solve_host", "lp_mlp_gradients_at",
-            "lp_mlp_gemm_bf16")
+            "lp_mlp_gemm_bf16", "lpb_measure_peaks")
 
 
 class LPBatchOpts(ctypes.Structure):
@@ -58,6 +58,15 @@ class LPBatchGroup(ctypes.Structure):
         ("smem_bytes", ctypes.c_int64),
         ("tuned_ms", ctypes.c_float),
         ("cluster_ctas", ctypes.c_int32),
+    ]
+
+
+class LPBPeaks(ctypes.Structure):
+    _fields_ = [
+        ("fp64_gflops", ctypes.c_double),
+        ("fp32_gflops", ctypes.c_double),
+        ("smem_gbs", ctypes.c_double),
+        ("num_sms", ctypes.c_int32),
     ]
 
 
@@ -171,6 +180,8 @@ def load(path: str | None = None):
         L.lp_solve_uniform_noalloc.argtypes = [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                                ctypes.POINTER(LPBatchOpts), _vp]
         L.lp_solve_uniform_noalloc.restype = ctypes.c_int
+        L.lpb_measure_peaks.argtypes = [ctypes.POINTER(LPBPeaks), _vp]
+        L.lpb_measure_peaks.restype = ctypes.c_int
         L.lpb_last_error.argtypes = []
         L.lpb_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -359,6 +370,14 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def lpb_measure_peaks(stream=None) -> dict:
+    """Measured FP64/FP32 FMA and shared-memory throughputs of the device."""
+    p = LPBPeaks()
+    _check(load().lpb_measure_peaks(ctypes.byref(p), _stream_handle(stream)), "lpb_measure_peaks")
+    return {"fp64_gflops": p.fp64_gflops, "fp32_gflops": p.fp32_gflops, "smem_gbs": p.smem_gbs,
+            "num_sms": p.num_sms}
 
 
 def lp_mlp_gemm_bf16(epilogue, form, M, N, K, A, lda, B, ldb, C=None, ldc=0, bias=None, pre=None, h=None, ldh=0,

@@ -28,7 +28,12 @@ def test_reference_arm_prints_one_json_line():
         assert key in d, key
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "LPs/s"
     assert d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
-    assert d["config"]["workload"] == "dense50x50_phase1_100k" and d["config"]["num_lps"] == 300
+    assert d["config"]["workload"] == "dense50x50_phase1_100k" and d["config"]["num_lps_per_gpu"] == 300
+    # the same config object as the GPU arm's line (bench.bench_config of the same batch)
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1802_08557_gb300 import workloads as W
+    assert d["config"] == bench.bench_config("dense50x50_phase1_100k", W.mixed_sign_dense(300, 50, 50))
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "LPs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
