@@ -401,6 +401,12 @@ lpb_err lp_mlp_set_params(lp_mlp *net, const float *params);
 lpb_err lp_mlp_get_params(lp_mlp *net, float *params);
 /* Input scaling (host arrays of n_in values). */
 lpb_err lp_mlp_set_scaling(lp_mlp *net, const float *mean, const float *inv_std);
+lpb_err lp_mlp_get_scaling(lp_mlp *net, float *mean, float *inv_std);
+/* Set the input scaling from data: mean and 1/std (population) of each of the
+ * n_in features over x [rows x n_in] (device, FP32), summed in FP64 in a
+ * fixed order (the same result on every call); a constant feature gets
+ * inv_std = 1.  Waits for the GPU. */
+lpb_err lp_mlp_fit_scaling(lp_mlp *net, const float *x, int64_t rows, void *stream);
 /* logits [batch x n_out] (device, FP32) of x [batch x n_in] (device, FP32,
  * unscaled); asynchronous on stream. */
 lpb_err lp_mlp_forward(lp_mlp *net, const float *x, int64_t batch, float *logits, void *stream);

@@ -391,6 +391,52 @@ __global__ void zero_cols_kernel(__nv_bfloat16* __restrict__ buf, int rows, int 
     }
 }
 
+// Input statistics (lp_mlp_fit_scaling), two deterministic passes: per
+// column chunk sums of x (pass 0) or of (x - mean)^2 (pass 1) in FP64 over
+// rows [chunk*rows_per_chunk, ...), thread (tx, ty) of a 32 x 8 block taking
+// column blockIdx.x*32 + tx and every 8th row; partials [chunks x n] in a
+// fixed order, then reduce_columns_kernel sums them in chunk order.
+constexpr int kStatRows = 8;
+__global__ void column_partials_kernel(const float* __restrict__ x, int64_t rows, int n, int64_t rows_per_chunk,
+                                       const double* __restrict__ mean, double* __restrict__ partial) {
+    __shared__ double red[kStatRows][32];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+    const int64_t r1 = min(rows, r0 + rows_per_chunk);
+    double acc = 0.0;
+    if (c < n) {
+        const double mu = mean ? mean[c] : 0.0;
+        for (int64_t r = r0 + threadIdx.y; r < r1; r += kStatRows) {
+            const double v = (double)x[r * n + c];
+            acc = mean ? __fma_rn(v - mu, v - mu, acc) : acc + v;
+        }
+    }
+    red[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < n) {
+        double s = 0.0;
+        for (int i = 0; i < kStatRows; ++i) s += red[i][threadIdx.x];
+        partial[(size_t)blockIdx.y * n + c] = s;
+    }
+}
+
+// mean (pass 0) or 1/std (pass 1; 1 for a constant feature) from the partials.
+__global__ void reduce_columns_kernel(const double* __restrict__ partial, int chunks, int n, int64_t rows,
+                                      double* __restrict__ mean, float* __restrict__ mean32,
+                                      float* __restrict__ inv_std, int pass) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double s = 0.0;
+    for (int k = 0; k < chunks; ++k) s += partial[(size_t)k * n + c];
+    if (pass == 0) {
+        mean[c] = s / (double)rows;
+        mean32[c] = (float)(s / (double)rows);
+    } else {
+        const double sd = sqrt(s / (double)rows);
+        inv_std[c] = sd > 0.0 ? (float)(1.0 / sd) : 1.0f;
+    }
+}
+
 // h = bf16(relu(a)) of given pre-activations a [batch x n] (FP32), as the
 // forward epilogue writes it: hb [batch x ldh] and hbT [n x ldt] (rows
 // batch..ldt-1 of hbT zeroed: the batch padding of the weight-gradient sums).
@@ -818,6 +864,47 @@ lpb_err lp_mlp_set_scaling(lp_mlp* net, const float* mean, const float* inv_std)
     cudaError_t e;
     if ((e = cudaMemcpy(net->m.mean, mean, (size_t)net->m.n_in * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(net->m.inv_std, inv_std, (size_t)net->m.n_in * 4, cudaMemcpyHostToDevice)))
+        return api_cuda_fail(e, "input scaling");
+    return LPB_OK;
+}
+
+lpb_err lp_mlp_fit_scaling(lp_mlp* net, const float* x, int64_t rows, void* stream) {
+    lpb::api_clear_error();
+    if (!net || !x) return api_fail(LPB_EINVAL, "net or x is NULL");
+    if (rows < 1) return api_fail(LPB_EINVAL, "rows must be >= 1");
+    Dev guard(net->device);
+    if (!on_device(x, net->device)) return api_fail(LPB_EINVAL, "x must be device memory of the network's device");
+    const int n = net->m.n_in;
+    const int64_t per_chunk = std::max<int64_t>(4096, (rows + 1023) / 1024);
+    const int chunks = (int)((rows + per_chunk - 1) / per_chunk);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *partial = nullptr, *mean = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&partial, (size_t)chunks * n * sizeof(double), s);
+    if (!e) e = cudaMallocAsync((void**)&mean, (size_t)n * sizeof(double), s);
+    if (!e) {
+        const dim3 grid((n + 31) / 32, chunks), block(32, lpb::kStatRows);
+        lpb::column_partials_kernel<<<grid, block, 0, s>>>(x, rows, n, per_chunk, nullptr, partial);
+        lpb::reduce_columns_kernel<<<(n + 127) / 128, 128, 0, s>>>(partial, chunks, n, rows, mean, net->m.mean,
+                                                                   nullptr, 0);
+        lpb::column_partials_kernel<<<grid, block, 0, s>>>(x, rows, n, per_chunk, mean, partial);
+        lpb::reduce_columns_kernel<<<(n + 127) / 128, 128, 0, s>>>(partial, chunks, n, rows, nullptr, nullptr,
+                                                                   net->m.inv_std, 1);
+        e = cudaGetLastError();
+    }
+    if (partial) cudaFreeAsync(partial, s);
+    if (mean) cudaFreeAsync(mean, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return api_cuda_fail(e, "input statistics");
+    return LPB_OK;
+}
+
+lpb_err lp_mlp_get_scaling(lp_mlp* net, float* mean, float* inv_std) {
+    lpb::api_clear_error();
+    if (!net || !mean || !inv_std) return api_fail(LPB_EINVAL, "net, mean or inv_std is NULL");
+    Dev guard(net->device);
+    cudaError_t e;
+    if ((e = cudaMemcpy(mean, net->m.mean, (size_t)net->m.n_in * 4, cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(inv_std, net->m.inv_std, (size_t)net->m.n_in * 4, cudaMemcpyDeviceToHost)))
         return api_cuda_fail(e, "input scaling");
     return LPB_OK;
 }

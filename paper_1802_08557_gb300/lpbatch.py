@@ -33,7 +33,7 @@ EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_r
             "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients", "lp_mlp_destroy", "lp_batch_solve_warm",
             "lp_batch_features", "lp_batch_active_labels", "lp_batch_solve_graph", "lp_batch_autotune",
             "lp_batch_group_info", "lp_batch_set_group_form", "lp_solve_host", "lp_mlp_gradients_at",
-            "lp_mlp_gemm_bf16", "lpb_measure_peaks")
+            "lp_mlp_gemm_bf16", "lpb_measure_peaks", "lp_mlp_fit_scaling", "lp_mlp_get_scaling")
 
 
 class LPBatchOpts(ctypes.Structure):
@@ -136,6 +136,8 @@ def load(path: str | None = None):
         L.lp_mlp_set_params.argtypes = [_vp, _vp]
         L.lp_mlp_get_params.argtypes = [_vp, _vp]
         L.lp_mlp_set_scaling.argtypes = [_vp, _vp, _vp]
+        L.lp_mlp_get_scaling.argtypes = [_vp, _vp, _vp]
+        L.lp_mlp_fit_scaling.argtypes = [_vp, _vp, _i64, _vp]
         L.lp_mlp_forward.argtypes = [_vp, _vp, _i64, _vp, _vp]
         L.lp_mlp_train_step.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float,
                                         ctypes.POINTER(ctypes.c_double), _vp]
@@ -165,7 +167,8 @@ def load(path: str | None = None):
         L.lp_batch_active_labels.restype = ctypes.c_int
         for f in ("lp_mlp_create", "lp_mlp_num_params", "lp_mlp_set_params", "lp_mlp_get_params",
                   "lp_mlp_set_scaling", "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients",
-                  "lp_mlp_gradients_at", "lp_mlp_gemm_bf16", "lp_mlp_destroy"):
+                  "lp_mlp_gradients_at", "lp_mlp_gemm_bf16", "lp_mlp_destroy", "lp_mlp_get_scaling",
+                  "lp_mlp_fit_scaling"):
             getattr(L, f).restype = ctypes.c_int
         L.lp_hyperbox_solve.argtypes = [_i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _i32, _vp]
         L.lp_hyperbox_solve.restype = ctypes.c_int
@@ -332,6 +335,17 @@ class Mlp:
         mean = np.ascontiguousarray(mean, np.float32)
         inv_std = np.ascontiguousarray(inv_std, np.float32)
         _check(load().lp_mlp_set_scaling(self.h, mean.ctypes.data, inv_std.ctypes.data), "lp_mlp_set_scaling")
+
+    def get_scaling(self):
+        mean = np.empty(self.sizes[0], np.float32)
+        inv = np.empty(self.sizes[0], np.float32)
+        _check(load().lp_mlp_get_scaling(self.h, mean.ctypes.data, inv.ctypes.data), "lp_mlp_get_scaling")
+        return mean, inv
+
+    def fit_scaling(self, x, stream=None):
+        """Input scaling from device features x [rows x n_in] (FP32)."""
+        _check(load().lp_mlp_fit_scaling(self.h, _addr(x), int(x.shape[0]), _stream_handle(stream)),
+               "lp_mlp_fit_scaling")
 
     def forward(self, x, logits, stream=None):
         _check(load().lp_mlp_forward(self.h, _addr(x), int(x.shape[0]), _addr(logits), _stream_handle(stream)),

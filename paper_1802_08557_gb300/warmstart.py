@@ -10,21 +10,22 @@ from __future__ import annotations
 
 import math
 
-import numpy as np
-
 from . import lpbatch as lpb
 
 
-def feature_scaling(batch):
-    """Per-feature mean and 1/std of (b, c) over a batch of equal-size LPs."""
+def batch_features(batch, stream=None):
+    """The network's input features (b, c as FP32) of a batch of equal-size
+    LPs, as a device tensor (lp_batch_features; no solve)."""
+    import torch
     N, m, n = batch.num_lps, int(batch.m[0]), int(batch.n[0])
-    b = np.stack([batch.b[batch.b_off[k]:batch.b_off[k] + m] for k in range(0, N, max(1, N // 20000))])
-    c = np.stack([batch.c[batch.c_off[k]:batch.c_off[k] + n] for k in range(0, N, max(1, N // 20000))])
-    f = np.concatenate([b, c], axis=1)
-    mean = f.mean(axis=0).astype(np.float32)
-    std = f.std(axis=0)
-    inv = np.where(std > 0, 1.0 / np.maximum(std, 1e-30), 1.0).astype(np.float32)
-    return mean, inv
+    s = lpb.BatchSolver(batch, opts=lpb.lpb_default_opts(precision=lpb.LP_PREC_FP64))
+    try:
+        x = torch.empty((N, m + n), dtype=torch.float32, device="cuda")
+        lpb.lp_batch_features(s.h, x, stream)
+        torch.cuda.synchronize()
+    finally:
+        s.close()
+    return x
 
 
 def solved_training_data(batch, stream=None):
@@ -50,7 +51,7 @@ def train(batch, epochs: float = 3.0, batch_size: int = 1024, lr: float = 2e-3, 
     N, m, n = batch.num_lps, int(batch.m[0]), int(batch.n[0])
     x, y = solved_training_data(batch)
     net = lpb.Mlp(m + n, hidden[0], hidden[1], m, max_batch=batch_size, seed=seed)
-    net.set_scaling(*feature_scaling(batch))
+    net.fit_scaling(x)  # per-feature mean and 1/std of the training features, on the GPU
     steps = max(1, int(epochs * N / batch_size))
     first = last = None
     for t in range(steps):

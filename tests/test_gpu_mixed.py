@@ -107,6 +107,28 @@ def test_mixed_extreme_scales_fall_back_correctly():
     assert g["plan"]["num_fallback"] >= int((~in_range).sum())
 
 
+def test_mixed_uneven_shapes_against_oracle():
+    """The uneven workload's shapes (m, n log-uniform in [10, 500]): its 60
+    largest LPs of the first 1500 (FP32 tableaux above one CTA's shared
+    memory: the streamed mixed kernel, with FP64 re-solves on thread-block
+    clusters or streamed) and 90 evenly spaced others (shared-memory kernels),
+    in one batch.  Status equal to the oracle's, objective within 1e-9, and
+    every optimum certified in numpy."""
+    full = W.uneven_dense(1500, start=0)
+    size = full.m.astype(np.int64) * full.n.astype(np.int64)
+    big = np.argsort(-size, kind="stable")[:60]
+    rest = np.setdiff1d(np.arange(full.num_lps), big)[::15][:90]
+    batch = full.subset(np.sort(np.concatenate([big, rest])))
+    g, r = check_mixed(batch)
+    s = lpb.BatchSolver(batch, opts=mixed_opts())
+    try:
+        kinds = {gr["kind"] for gr in lpb.lp_batch_groups(s.h)}
+    finally:
+        s.close()
+    assert 4 in kinds and 0 in kinds, kinds  # both the streamed and the shared-memory mixed kernels ran
+    assert int(np.sum(r["status"] == 0)) == batch.num_lps  # positive data: all optimal
+
+
 def test_mixed_streamed_matches_shared_memory_bitwise():
     """LPB_SCHED_STREAMED with FP32_REFINE puts every LP's FP32 tableau in a
     global workspace slot (persistent 512-thread CTAs, group kind 4).  The

@@ -267,6 +267,36 @@ def test_gradients_whole_network_elementwise(batch):
     net.close()
 
 
+def test_fit_scaling_is_mean_and_inverse_std_per_feature():
+    """lp_mlp_fit_scaling: per-feature mean and 1/std (population) of device
+    features, against numpy in FP64 on the same FP32 values; a constant
+    feature gets scale 1; the same bits on a repeat call; the scaled
+    features have mean 0 and std 1."""
+    rng = np.random.default_rng(3)
+    rows, n_in = 50_000, 30
+    x = (rng.standard_normal((rows, n_in)) * rng.uniform(0.1, 50, n_in) + rng.uniform(-5, 5, n_in)).astype(np.float32)
+    x[:, 7] = 0.25
+    net = lpb.Mlp(n_in, 16, 16, 4, max_batch=64, seed=0)
+    dx = _dev(x)
+    net.fit_scaling(dx)
+    mean, inv = net.get_scaling()
+    f = x.astype(np.float64)
+    want_mean = f.mean(axis=0)
+    std = f.std(axis=0)
+    np.testing.assert_allclose(mean, want_mean.astype(np.float32), rtol=1e-6, atol=1e-7)
+    ok = std > 0
+    np.testing.assert_allclose(inv[ok], (1.0 / std[ok]).astype(np.float32), rtol=1e-6)
+    assert mean[7] == np.float32(0.25) and inv[7] == 1.0
+    net.fit_scaling(dx)
+    m2, i2 = net.get_scaling()
+    np.testing.assert_array_equal(m2, mean)
+    np.testing.assert_array_equal(i2, inv)
+    z = (f - mean) * inv
+    np.testing.assert_allclose(z[:, ok].mean(axis=0), 0.0, atol=1e-5)
+    np.testing.assert_allclose(z[:, ok].std(axis=0), 1.0, rtol=1e-5)
+    net.close()
+
+
 def test_gradients_are_deterministic():
     net, _ = _net_with_oracle_params(SIZES, seed=8, max_batch=128)
     x, y = _data(128, SIZES, seed=3)

@@ -80,7 +80,7 @@ def test_trained_network_certifies_what_an_untrained_one_cannot(trained, test_ba
     trained_rate = plan["num_warm_certified"] / test_batch.num_lps
     assert plan["num_warm_certified"] + plan["num_fallback"] == test_batch.num_lps
     untrained = lpb.Mlp(M + N_, 512, 512, M, max_batch=1024, seed=7)
-    untrained.set_scaling(*WS.feature_scaling(train))
+    untrained.fit_scaling(WS.batch_features(train))
     r0, plan0 = WS.solve_warm(test_batch, untrained, threshold=0.2)
     untrained_rate = plan0["num_warm_certified"] / test_batch.num_lps
     untrained.close()
@@ -95,7 +95,7 @@ def test_fallback_lps_are_the_cold_fp64_results(trained, test_batch):
     the cold FP64 solve, bit for bit."""
     _, train = trained
     untrained = lpb.Mlp(M + N_, 512, 512, M, max_batch=1024, seed=11)
-    untrained.set_scaling(*WS.feature_scaling(train))
+    untrained.fit_scaling(WS.batch_features(train))
     batch = test_batch.subset(np.arange(1000))
     r, plan = WS.solve_warm(batch, untrained, threshold=0.5)
     untrained.close()
