@@ -441,9 +441,12 @@ enum {
     LPB_EPI_BIAS = 2,       /* C = acc + bias[col]                                       */
     LPB_EPI_MASK_GRAD = 3   /* v = pre > 0 ? acc : 0 (pre at C's index); C = v; h = hT^T = bf16(v) */
 };
-/* Kernel forms of the product: AUTO picks as the network does (128 x 128 tiles
- * when they give at least one per SM, else 64 x 64); the others force one. */
-enum { LPB_GEMM_AUTO = 0, LPB_GEMM_MMA64 = 1, LPB_GEMM_MMA128 = 2 };
+/* Kernel forms of the product: AUTO picks as the network does; MMA64 and
+ * MMA128 are warp-level mma.sync kernels (64 x 64 and 128 x 128 tiles, the
+ * same results bit for bit); TC is the tcgen05 kernel (TMA-staged 128 x 128
+ * tiles, FP32 accumulator in tensor memory; another accumulation order, so
+ * equal to the others within the FP32 accumulation bound). */
+enum { LPB_GEMM_AUTO = 0, LPB_GEMM_MMA64 = 1, LPB_GEMM_MMA128 = 2, LPB_GEMM_TC = 3 };
 
 /*
  * The network's matrix product on caller buffers: acc[M x N] = A[M x K] .
@@ -460,6 +463,11 @@ enum { LPB_GEMM_AUTO = 0, LPB_GEMM_MMA64 = 1, LPB_GEMM_MMA128 = 2 };
 lpb_err lp_mlp_gemm_bf16(int32_t epilogue, int32_t form, int32_t M, int32_t N, int32_t K, const uint16_t *A,
                          int32_t lda, const uint16_t *B, int32_t ldb, float *C, int32_t ldc, const float *bias,
                          const float *pre, uint16_t *h, int32_t ldh, uint16_t *hT, int32_t ldt, void *stream);
+
+/* Tiles of the tcgen05 product kernel that gave up on a wait (for a copy or
+ * the tensor cores) since the library was loaded: 0 in a correct run.  Such a
+ * tile's outputs are NaN.  Its waits are bounded at about two seconds. */
+lpb_err lp_mlp_tc_faults(int32_t *count);
 
 /*
  * Solve the batch from the warm-start network's proposal.  For every LP the

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "lp_internal.h"
+#include "lp_mlp_gemm.cuh"
 #include "lpbatch.h"
 
 namespace lpb {
@@ -40,26 +41,6 @@ namespace {
 
 constexpr int kBM = 64, kBN = 64, kBK = 32, kGemmThreads = 128;
 
-// Epilogue variants of the GEMM.
-enum Epi : int {
-    kEpiStore = 0,   // C = acc (FP32)
-    kEpiBiasReLU,    // pre = acc + bias -> C; h = relu(pre) -> hbf [M x ldh], hbfT [N x ldt]
-    kEpiBias,        // C = acc + bias
-    kEpiMaskGrad,    // g = acc * (pre > 0) -> C; g -> hbf, hbfT
-};
-
-struct GemmArgs {
-    const __nv_bfloat16* A;  // [M x K], lda
-    const __nv_bfloat16* B;  // [N x K], ldb
-    float* C;                // [M x N], ldc
-    int M, N, K, lda, ldb, ldc;
-    const float* bias;       // [N]
-    const float* pre;        // [M x N] (ld = ldc): ReLU mask source
-    __nv_bfloat16* hbf;      // [M x ldh]
-    __nv_bfloat16* hbfT;     // [N x ldt]
-    int ldh, ldt;
-};
-
 __device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
@@ -68,31 +49,6 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         "{%0,%1,%2,%3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// Epilogue of one output element (row, col) with accumulator v.
-template <int kEpi>
-__device__ __forceinline__ void epilogue(const GemmArgs& g, int row, int col, float v) {
-    const size_t ci = (size_t)row * g.ldc + col;
-    if (kEpi == kEpiStore) {
-        g.C[ci] = v;
-    } else if (kEpi == kEpiBias) {
-        g.C[ci] = v + g.bias[col];
-    } else if (kEpi == kEpiBiasReLU) {
-        // (inference: no pre-activation and no transposed copy,
-        // which only the backward pass reads)
-        v = v + g.bias[col];
-        if (g.C) g.C[ci] = v;
-        const __nv_bfloat16 h = __float2bfloat16_rn(fmaxf(v, 0.0f));
-        g.hbf[(size_t)row * g.ldh + col] = h;
-        if (g.hbfT) g.hbfT[(size_t)col * g.ldt + row] = h;
-    } else {  // kEpiMaskGrad
-        v = (g.pre[ci] > 0.0f) ? v : 0.0f;
-        g.C[ci] = v;
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        g.hbf[(size_t)row * g.ldh + col] = h;
-        g.hbfT[(size_t)col * g.ldt + row] = h;
-    }
 }
 
 template <int kEpi>
@@ -253,12 +209,13 @@ __global__ void __launch_bounds__(kTThreads) gemm_nt_tiled_kernel(const GemmArgs
 }
 
 // Kernel forms of the product (lp_mlp_gemm_bf16's `form`).
-enum GemmForm : int { kFormAuto = 0, kFormMma64 = 1, kFormMma128 = 2 };
+enum GemmForm : int { kFormAuto = 0, kFormMma64 = 1, kFormMma128 = 2, kFormTc = 3 };
 
 // 128 x 128 tiles when they give at least one per SM, else 64 x 64 (small
 // products, e.g. the weight gradients of one training batch): same results.
 template <int kEpi>
 cudaError_t gemm(const GemmArgs& a, cudaStream_t s, int form = kFormAuto) {
+    if (form == kFormTc) return gemm_tc(kEpi, &a, s);
     const int64_t big_tiles = (int64_t)((a.N + kTN - 1) / kTN) * ((a.M + kTM - 1) / kTM);
     if (form == kFormMma128 || (form == kFormAuto && big_tiles >= 152)) {
         const dim3 grid((a.N + kTN - 1) / kTN, (a.M + kTM - 1) / kTM);
@@ -1014,7 +971,7 @@ lpb_err lp_mlp_gemm_bf16(int32_t epilogue, int32_t form, int32_t M, int32_t N, i
                          const float* pre, uint16_t* h, int32_t ldh, uint16_t* hT, int32_t ldt, void* stream) {
     lpb::api_clear_error();
     if (epilogue < LPB_EPI_STORE || epilogue > LPB_EPI_MASK_GRAD) return api_fail(LPB_EINVAL, "unknown epilogue");
-    if (form < LPB_GEMM_AUTO || form > LPB_GEMM_MMA128) return api_fail(LPB_EINVAL, "unknown kernel form");
+    if (form < LPB_GEMM_AUTO || form > LPB_GEMM_TC) return api_fail(LPB_EINVAL, "unknown kernel form");
     if (M < 1 || N < 1 || K < 1 || K % 32 != 0) return api_fail(LPB_EINVAL, "M, N >= 1 and K a positive multiple of 32");
     if (M > LPB_MAX_MLP_BATCH * 8 || N > LPB_MAX_MLP_BATCH * 8 || K > LPB_MAX_MLP_BATCH * 8)
         return api_fail(LPB_ETOOBIG, "a dimension exceeds the limit");
@@ -1043,7 +1000,18 @@ lpb_err lp_mlp_gemm_bf16(int32_t epilogue, int32_t form, int32_t M, int32_t N, i
     g.hbfT = need_h ? reinterpret_cast<__nv_bfloat16*>(hT) : nullptr;
     g.ldh = ldh; g.ldt = ldt;
     const cudaError_t e = lpb::mlp_gemm_dispatch(epilogue, form, g, static_cast<cudaStream_t>(stream));
+    if (e == cudaErrorNotSupported) return api_fail(LPB_EINVAL, "no tensor map for these operands");
     if (e) return api_cuda_fail(e, "product");
+    return LPB_OK;
+}
+
+lpb_err lp_mlp_tc_faults(int32_t* count) {
+    lpb::api_clear_error();
+    if (!count) return api_fail(LPB_EINVAL, "count is NULL");
+    int c = 0;
+    const cudaError_t e = lpb::gemm_tc_faults(&c);
+    if (e) return api_cuda_fail(e, "fault counter");
+    *count = c;
     return LPB_OK;
 }
 

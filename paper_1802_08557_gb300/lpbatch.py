@@ -23,7 +23,7 @@ LP_PREC_FP64, LP_PREC_FP32_REFINE = 0, 1
 LPB_SCHED_AUTO, LPB_SCHED_STREAMED = 0, 1
 LPB_MAX_DIM = 16384
 LPB_EPI_STORE, LPB_EPI_BIAS_RELU, LPB_EPI_BIAS, LPB_EPI_MASK_GRAD = 0, 1, 2, 3
-LPB_GEMM_AUTO, LPB_GEMM_MMA64, LPB_GEMM_MMA128 = 0, 1, 2
+LPB_GEMM_AUTO, LPB_GEMM_MMA64, LPB_GEMM_MMA128, LPB_GEMM_TC = 0, 1, 2, 3
 
 # Every symbol include/lpbatch.h declares.
 EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_results",
@@ -33,7 +33,8 @@ EXPORTED = ("lpb_default_opts", "lp_batch_create", "lp_batch_solve", "lp_batch_r
             "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients", "lp_mlp_destroy", "lp_batch_solve_warm",
             "lp_batch_features", "lp_batch_active_labels", "lp_batch_solve_graph", "lp_batch_autotune",
             "lp_batch_group_info", "lp_batch_set_group_form", "lp_solve_host", "lp_mlp_gradients_at",
-            "lp_mlp_gemm_bf16", "lpb_measure_peaks", "lp_mlp_fit_scaling", "lp_mlp_get_scaling")
+            "lp_mlp_gemm_bf16", "lpb_measure_peaks", "lp_mlp_fit_scaling", "lp_mlp_get_scaling",
+            "lp_mlp_tc_faults")
 
 
 class LPBatchOpts(ctypes.Structure):
@@ -147,6 +148,7 @@ def load(path: str | None = None):
                                           ctypes.POINTER(ctypes.c_double), _vp]
         L.lp_mlp_gemm_bf16.argtypes = [_i32, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _i32, _vp, _i32, _vp, _vp,
                                        _vp, _i32, _vp, _i32, _vp]
+        L.lp_mlp_tc_faults.argtypes = [ctypes.POINTER(_i32)]
         L.lp_mlp_destroy.argtypes = [_vp]
         L.lp_batch_solve_graph.argtypes = [_vp, _vp]
         L.lp_batch_solve_graph.restype = ctypes.c_int
@@ -168,7 +170,7 @@ def load(path: str | None = None):
         for f in ("lp_mlp_create", "lp_mlp_num_params", "lp_mlp_set_params", "lp_mlp_get_params",
                   "lp_mlp_set_scaling", "lp_mlp_forward", "lp_mlp_train_step", "lp_mlp_gradients",
                   "lp_mlp_gradients_at", "lp_mlp_gemm_bf16", "lp_mlp_destroy", "lp_mlp_get_scaling",
-                  "lp_mlp_fit_scaling"):
+                  "lp_mlp_fit_scaling", "lp_mlp_tc_faults"):
             getattr(L, f).restype = ctypes.c_int
         L.lp_hyperbox_solve.argtypes = [_i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _i32, _vp]
         L.lp_hyperbox_solve.restype = ctypes.c_int
@@ -384,6 +386,13 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def lp_mlp_tc_faults() -> int:
+    """Tiles of the tcgen05 product kernel that gave up on a wait (0 normally)."""
+    c = _i32(0)
+    _check(load().lp_mlp_tc_faults(ctypes.byref(c)), "lp_mlp_tc_faults")
+    return int(c.value)
 
 
 def lpb_measure_peaks(stream=None) -> dict:

@@ -115,7 +115,8 @@ NETWORK_PRODUCTS = [
 ]
 
 
-@pytest.mark.parametrize("form", [lpb.LPB_GEMM_MMA64, lpb.LPB_GEMM_MMA128])
+@pytest.mark.parametrize("form", [lpb.LPB_GEMM_MMA64, lpb.LPB_GEMM_MMA128, lpb.LPB_GEMM_TC],
+                         ids=["mma64", "mma128", "tcgen05"])
 @pytest.mark.parametrize("case", NETWORK_PRODUCTS, ids=[c[0] for c in NETWORK_PRODUCTS])
 def test_product_elementwise(case, form):
     """One product with its epilogue through lp_mlp_gemm_bf16 against the
@@ -167,6 +168,44 @@ def test_product_elementwise(case, form):
         own = np.maximum(got, 0.0) if epi == lpb.LPB_EPI_BIAS_RELU else got
         np.testing.assert_array_equal(hn[:M, :N], omlp.bf16_round(own.astype(np.float32)))
         np.testing.assert_array_equal(hTn[:N, :M], hn[:M, :N].T)
+    assert lpb.lp_mlp_tc_faults() == 0
+
+
+def test_tcgen05_product_aligned_rows_and_tail_tiles():
+    """The tcgen05 kernel's 16-byte epilogue path (rows 16-byte aligned: ldc a
+    multiple of 4, ldh of 8) on a product with full and partial 128 x 128
+    tiles, in the three epilogues that write h, against the oracle's product;
+    h bit for bit the BF16 rounding of the kernel's own FP32 value."""
+    import torch
+    rng = np.random.default_rng(42)
+    M, N, K = 1000, 200, 320
+    A = omlp.bf16_round(rng.standard_normal((M, K)).astype(np.float32))
+    B = omlp.bf16_round(rng.uniform(-0.2, 0.2, (N, K)).astype(np.float32))
+    bias = (rng.standard_normal(N) * 0.3).astype(np.float32)
+    pre = rng.standard_normal((M, N)).astype(np.float32)
+    acc = omlp._mm(A, B.T).astype(np.float64)
+    e = MB.mm_err(A.astype(np.float64), 0.0, B.T.astype(np.float64), 0.0, K)
+    for epi in (lpb.LPB_EPI_BIAS_RELU, lpb.LPB_EPI_MASK_GRAD, lpb.LPB_EPI_BIAS):
+        C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+        h = torch.zeros((M, N), dtype=torch.bfloat16, device="cuda")
+        hT = torch.zeros((N, M), dtype=torch.bfloat16, device="cuda")
+        use_h = epi != lpb.LPB_EPI_BIAS
+        lpb.lp_mlp_gemm_bf16(epi, lpb.LPB_GEMM_TC, M, N, K, _bf16_dev(A), K, _bf16_dev(B), K, C, N, _dev(bias),
+                             _dev(pre), h if use_h else None, N, hT if use_h else None, M)
+        torch.cuda.synchronize()
+        got = C.cpu().numpy().astype(np.float64)
+        if epi == lpb.LPB_EPI_MASK_GRAD:
+            want, bound = np.where(pre > 0, acc, 0.0), np.where(pre > 0, e, 0.0)
+        else:
+            want = (acc.astype(np.float32) + bias).astype(np.float64)
+            bound = MB.bias_err(e, want)
+        MB.check(f"epilogue {epi}", got, want, bound)
+        if use_h:
+            own = np.maximum(got, 0.0) if epi == lpb.LPB_EPI_BIAS_RELU else got
+            hn = h.float().cpu().numpy()
+            np.testing.assert_array_equal(hn, omlp.bf16_round(own.astype(np.float32)))
+            np.testing.assert_array_equal(hT.float().cpu().numpy(), hn.T)
+    assert lpb.lp_mlp_tc_faults() == 0
 
 
 def test_product_argument_errors():
