@@ -37,8 +37,20 @@ DEFAULT_WORKLOAD = "dense50x50_phase1_100k"
 FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.070
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.070
 SMEM_NOMINAL_GBS = 152 * 128 * 2.070
-# HBM bandwidth of a GB300 measured with a STREAM-style copy (read + write bytes)
-HBM_PEAK_GBS = 6784.5
+def _measured_peaks():
+    """HBM copy bandwidth and BF16 tensor throughput measured on this machine's
+    GB300s (MEASURED_PEAKS.json beside this file), else the earlier measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "MEASURED_PEAKS.json"
+    except Exception:  # noqa: BLE001
+        return 6784.5, 1958.9, "earlier measurement (MEASURED_PEAKS.json absent)"
+
+
+# HBM bandwidth (STREAM-style copy, read + write bytes) and dense BF16 tensor
+# throughput (cuBLAS GEMM, burst) of a GB300
+HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAKS_SOURCE = _measured_peaks()
 # DRAM bytes per LP (read + write) from ncu captures of the kernels as they are
 # now, for the roofline's `traffic` (scaled to a launch by the LPs it solves):
 # profiles/mixed_warp_kernel__dense50x50_20k__ncu.md (k = 0 group, 15629 LPs:
@@ -46,8 +58,6 @@ HBM_PEAK_GBS = 6784.5
 # (2^20 LPs in R^28: 234.9 MB + 7.6 MB).
 MIXED_DRAM_BYTES_PER_LP = (349.375232e6 + 12.406528e6) / 15629
 HYPERBOX_DRAM_BYTES_PER_LP_DIM28 = (234.9e6 + 7.6e6) / (1 << 20)
-# dense BF16 tensor throughput of a GB300 measured with a cuBLAS GEMM (burst)
-BF16_PEAK_TFLOPS = 1958.9
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -600,6 +610,27 @@ def run_ours(args):
         torch.cuda.synchronize()
         fwd_ms = f0.elapsed_time(f1) / args.steps
         mlp_flops = 2.0 * test_set.num_lps * (300 * 512 + 512 * 512 + 512 * 200)
+        # the first layer's product alone (1e5 x 320 . 512 x 320^T, bias + ReLU
+        # into BF16 activations) through the same kernel, on operands of its shape
+        nl = test_set.num_lps
+        a1_in = torch.randn((nl, 320), device=dev).to(torch.bfloat16)
+        w1 = (torch.rand((512, 320), device=dev) * 0.2 - 0.1).to(torch.bfloat16)
+        b1 = torch.zeros(512, dtype=torch.float32, device=dev)
+        h1 = torch.empty((nl, 512), dtype=torch.bfloat16, device=dev)
+
+        def layer1_call():
+            lpb.lp_mlp_gemm_bf16(lpb.LPB_EPI_BIAS_RELU, lpb.LPB_GEMM_TC, nl, 512, 320, a1_in, 320, w1, 320, None, 0,
+                                 b1, None, h1, 512, None, 0, stream)
+
+        l1_ms = ev_time(layer1_call)
+        l1_flops = 2.0 * nl * 512 * 320
+        l1_bytes = 2.0 * nl * (320 + 512) + 2.0 * 512 * 320
+        layer1 = {"shape": f"{nl} x 320 . 512 x 320^T, bias + ReLU -> BF16", "ms": l1_ms,
+                  "achieved_tflops": l1_flops / (l1_ms * 1e-3) / 1e12, "peak_tflops": BF16_PEAK_TFLOPS,
+                  "frac": l1_flops / (l1_ms * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
+                  "hbm_gbs": l1_bytes / (l1_ms * 1e-3) / 1e9, "hbm_frac": l1_bytes / (l1_ms * 1e-3) / 1e9 / HBM_PEAK_GBS,
+                  "tc_faults": lpb.lp_mlp_tc_faults()}
+        del a1_in, w1, b1, h1
         hw.close()
         net.close()
         opt = rc["status"] == 0
@@ -626,9 +657,11 @@ def run_ours(args):
                          "first_loss": tinfo["first_loss"], "last_loss": tinfo["last_loss"],
                          "what": "cold FP64 solve of the training LPs + features/labels + Adam steps, all on the GPU"},
             "network_forward": {"ms": fwd_ms, "achieved_tflops": mlp_flops / (fwd_ms * 1e-3) / 1e12,
-                                "peak_tflops": BF16_PEAK_TFLOPS,
+                                "peak_tflops": BF16_PEAK_TFLOPS, "peak_source": PEAKS_SOURCE,
                                 "frac": mlp_flops / (fwd_ms * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
-                                "note": "BF16 mma.sync GEMMs; 300->512->512->200 over the test set"},
+                                "note": "tcgen05 GEMMs (TMA tiles, TMEM accumulators) with fused bias/ReLU/BF16 "
+                                        "epilogues; 300->512->512->200 over the test set, one chunk"},
+            "layer1_product": layer1,
             "timing": "CUDA events on the solve's stream around K whole warm solves "
                       "(features, network, restricted solves, cold FP64 re-solve)",
         }

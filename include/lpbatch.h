@@ -391,8 +391,9 @@ typedef struct lp_mlp lp_mlp;   /* opaque; owned by the library */
 /* Create a network with He-uniform weights (rounded to BF16 values; splitmix64
  * stream from `seed`), zero biases, identity input scaling; max_batch = the
  * largest batch of lp_mlp_train_step / lp_mlp_gradients (lp_mlp_forward takes
- * any batch, in chunks of max(max_batch, 16384) rows).  Allocates on the
- * current device: about 23 KB per chunk row for the 300-512-512-200 network. */
+ * any batch, in chunks of max(max_batch, 131072) rows).  Allocates on the
+ * current device, for the 300-512-512-200 network: about 2.7 KB per
+ * inference-chunk row and 23 KB per max_batch row. */
 lpb_err lp_mlp_create(lp_mlp **out, int32_t n_in, int32_t n_h1, int32_t n_h2, int32_t n_out, int32_t max_batch,
                       uint64_t seed);
 lpb_err lp_mlp_num_params(const lp_mlp *net, int64_t *count);

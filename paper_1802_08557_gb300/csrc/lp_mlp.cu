@@ -3,10 +3,12 @@
 // counterpart in the paper (its solver always starts from the slack basis).
 //
 // Precision scheme: every matrix product takes BF16 operands (round to
-// nearest even) and accumulates in FP32 on the tensor cores (warp-level
-// mma.sync m16n8k16); biases, pre-activations, the loss and all gradients are
-// FP32; an operand is rounded to BF16 only where it enters a product.  Master
-// weights and Adam moments are FP32.
+// nearest even) and accumulates in FP32 on the tensor cores; biases,
+// pre-activations, the loss and all gradients are FP32; an operand is rounded
+// to BF16 only where it enters a product.  Master weights and Adam moments
+// are FP32.  The products run on the tcgen05 kernel (lp_mlp_tc.cu: TMA tiles,
+// TMEM accumulator); the warp-level mma.sync m16n8k16 kernels below take the
+// products it cannot address and serve as selectable reference forms.
 //
 // Every product is one NT GEMM, C[M x N] = A[M x K] . B[N x K]^T with both
 // operands row-major and K contiguous.  To get there the network keeps each
@@ -33,7 +35,7 @@
 namespace lpb {
 
 constexpr int kPadK = 32;        // K dimensions are padded to this multiple
-constexpr int kInferRows = 16384;  // rows of activations held for inference chunks
+constexpr int kInferRows = 131072;  // rows of BF16 activations held for inference chunks
 
 inline int pad_to(int v, int q) { return (v + q - 1) / q * q; }
 
@@ -215,7 +217,12 @@ enum GemmForm : int { kFormAuto = 0, kFormMma64 = 1, kFormMma128 = 2, kFormTc = 
 // products, e.g. the weight gradients of one training batch): same results.
 template <int kEpi>
 cudaError_t gemm(const GemmArgs& a, cudaStream_t s, int form = kFormAuto) {
-    if (form == kFormTc) return gemm_tc(kEpi, &a, s);
+    if (form == kFormTc || form == kFormAuto) {
+        // the tcgen05 kernel; in AUTO the mma.sync kernels take the products
+        // it cannot address (no tensor map for these strides or alignment)
+        const cudaError_t e = gemm_tc(kEpi, &a, s);
+        if (form == kFormTc || e != cudaErrorNotSupported) return e;
+    }
     const int64_t big_tiles = (int64_t)((a.N + kTN - 1) / kTN) * ((a.M + kTM - 1) / kTM);
     if (form == kFormMma128 || (form == kFormAuto && big_tiles >= 152)) {
         const dim3 grid((a.N + kTN - 1) / kTN, (a.M + kTM - 1) / kTM);
@@ -429,7 +436,8 @@ struct MlpModel {
     int n_in, h1, h2, n_out, max_batch, train_batch, bpad;
     MlpLayer L[3];
     float *mean, *inv_std;
-    // activations (batch capacity bpad rows)
+    // activations: xb, h1b, h2b for max_batch rows (the inference chunk), the
+    // rest (training only) for bpad rows
     __nv_bfloat16 *xb, *xbT, *h1b, *h1bT, *h2b, *h2bT, *g3b, *g3bT, *g2b, *g2bT, *g1b, *g1bT;
     float *a1, *a2, *z, *g3, *g2, *g1, *tmp;
     double *row_loss, *loss;
@@ -468,11 +476,12 @@ cudaError_t mlp_alloc(MlpModel* m) {
             return e;
     }
     const size_t B = (size_t)m->bpad;
+    const size_t BI = (size_t)std::max(m->max_batch, m->bpad);
     const int in_pad = m->L[0].in_pad, h1p = m->L[1].in_pad, h2p = m->L[2].in_pad, outp = m->L[2].out_pad;
     if ((e = zalloc(m, &m->mean, m->n_in)) || (e = zalloc(m, &m->inv_std, m->n_in)) ||
-        (e = zalloc(m, &m->xb, B * in_pad)) || (e = zalloc(m, &m->xbT, (size_t)m->n_in * B)) ||
-        (e = zalloc(m, &m->h1b, B * h1p)) || (e = zalloc(m, &m->h1bT, (size_t)m->h1 * B)) ||
-        (e = zalloc(m, &m->h2b, B * h2p)) || (e = zalloc(m, &m->h2bT, (size_t)m->h2 * B)) ||
+        (e = zalloc(m, &m->xb, BI * in_pad)) || (e = zalloc(m, &m->xbT, (size_t)m->n_in * B)) ||
+        (e = zalloc(m, &m->h1b, BI * h1p)) || (e = zalloc(m, &m->h1bT, (size_t)m->h1 * B)) ||
+        (e = zalloc(m, &m->h2b, BI * h2p)) || (e = zalloc(m, &m->h2bT, (size_t)m->h2 * B)) ||
         (e = zalloc(m, &m->g3b, B * outp)) || (e = zalloc(m, &m->g3bT, (size_t)m->n_out * B)) ||
         (e = zalloc(m, &m->g2b, B * h2p)) || (e = zalloc(m, &m->g2bT, (size_t)m->h2 * B)) ||
         (e = zalloc(m, &m->g1b, B * h1p)) || (e = zalloc(m, &m->g1bT, (size_t)m->h1 * B)) ||
@@ -756,11 +765,12 @@ lpb_err lp_mlp_create(lp_mlp** out, int32_t n_in, int32_t n_h1, int32_t n_h2, in
     cudaGetDevice(&net->device);
     lpb::MlpModel& m = net->m;
     m.n_in = n_in; m.h1 = n_h1; m.h2 = n_h2; m.n_out = n_out;
-    // activations for at least kInferRows rows, so that inference runs in
-    // large chunks (whole-GPU GEMMs) even when training batches are small
+    // BF16 activations for at least kInferRows rows, so that inference runs
+    // in large chunks (whole-GPU GEMMs) even when training batches are small;
+    // the training buffers for max_batch rows only
     m.max_batch = std::max<int>(max_batch, lpb::kInferRows);
     m.train_batch = max_batch;
-    m.bpad = lpb::pad_to(m.max_batch, lpb::kPadK);
+    m.bpad = lpb::pad_to(max_batch, lpb::kPadK);
     cudaError_t e = lpb::mlp_alloc(&m);
     if (e) {
         lpb::mlp_free(&m);

@@ -246,11 +246,11 @@ def test_forward_exact_network_bitwise(batch):
     net.close()
 
 
-def test_large_batch_forward_tiled_kernel():
-    """Batches whose 128 x 128 tiles fill the GPU take the tiled GEMM (cp.async
-    stages, ldmatrix fragments): logits bit for bit the small-tile kernel's on
-    the same rows (forwarded in pieces too small for the tiled kernel), and,
-    on an exact network, bit for bit the oracle's."""
+def test_large_batch_forward_in_one_and_in_pieces():
+    """A 6000-row forward (many 128 x 128 tiles per product) gives the same
+    logits bit for bit as the same rows forwarded in pieces of 1000 (a row's
+    result does not depend on the batch or the tile it lands in), and, on an
+    exact network, bit for bit the oracle's."""
     import torch
     for kind in ("random", "exact"):
         batch = 6000
