@@ -558,6 +558,34 @@ def run_ours(args):
             "lps_compared": int(ub.num_lps),
             "status_mismatches": int(np.sum(res_u["fp32r"]["status"] != res_u["fp64"]["status"])),
             "max_rel_obj_err_on_optimal": float(rel_u.max()) if rel_u.size else 0.0}
+        # the LPs above one CTA's shared memory alone: through the streamed FP64
+        # kernel (tableau in a global workspace slot, 16-byte rank-1 updates; the
+        # default for them) and on thread-block clusters (tableau split over the
+        # cluster's shared memory): the same bits.  The streamed kernel is HBM/L2
+        # bound: its roofline is the algorithmic bytes 2 (m+1)(n+1) 8 per pivot
+        big_lp = np.nonzero((um + 2.0) * (un + 1.0) * 8.0 > 227 * 1024)[0]
+        if big_lp.size:
+            bsub = ub.subset(big_lp)
+            big = {}
+            for lab, sch in (("streamed", lpb.LPB_SCHED_STREAMED), ("cluster", lpb.LPB_SCHED_CLUSTER)):
+                hs = lpb.BatchSolver(bsub, opts=lpb.lpb_default_opts(precision=lpb.LP_PREC_FP64, schedule=sch),
+                                     stream=stream)
+                big[lab] = (ev_time(lambda: lpb.lp_batch_solve(hs.h, stream)), hs.results())
+                hs.close()
+            ms_s, rs = big["streamed"]
+            bm, bn = bsub.m.astype(np.float64), bsub.n.astype(np.float64)
+            sbytes = 2.0 * 8.0 * float(np.sum(rs["iters"] * (bm + 1.0) * (bn + 1.0)))
+            same = all(np.array_equal(rs[k], big["cluster"][1][k]) and np.array_equal(rs[k], res_u["fp64"][k][big_lp])
+                       for k in ("status", "iters", "obj"))
+            uneven["fp64_large_lps"] = {
+                "lps": int(big_lp.size), "what": "the LPs whose FP64 tableau exceeds one CTA (~227 KB)",
+                "streamed_ms": ms_s, "cluster_ms": big["cluster"][0],
+                "streamed_roofline": {"bound": "hbm", "achieved": sbytes / (ms_s * 1e-3) / 1e9, "peak": HBM_PEAK_GBS,
+                                      "unit": "GB/s", "frac": sbytes / (ms_s * 1e-3) / 1e9 / HBM_PEAK_GBS,
+                                      "work": "sum over LPs of pivots x 2 (m+1)(n+1) x 8 bytes (the condensed "
+                                              "tableau read and written once per pivot; part of it from L2)"},
+                "same_status_iters_obj_streamed_cluster_default": bool(same)}
+            del bsub, big
         if rank == 0:
             idx_u = sample_indices(ub.num_lps, max(50, args.oracle_sample // 5))
             _, dt_u, o_u = cpu_oracle_run(ub, idx_u, os.cpu_count() or 1)

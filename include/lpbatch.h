@@ -87,15 +87,17 @@ typedef struct {
 } lp_batch_opts;
 
 /* Kernel choice.  AUTO: shared-memory-resident tableau when it fits in one
- * CTA; else split by rows over the shared memory of a thread-block cluster of
- * 2-16 CTAs (the smallest that holds it; all CTAs take the same decisions, so
- * the results are those of the one-CTA kernel); else a global workspace.
- * With LP_PREC_FP32_REFINE the FP32 tableau is in one CTA's shared memory when
- * it fits, else in a global workspace (no cluster form); the FP64 re-solve of
- * an uncertified LP runs in one CTA when its FP64 tableau fits, else streamed.
+ * CTA, else a global workspace slot per LP (persistent CTAs, many LPs at
+ * once).  With LP_PREC_FP32_REFINE the FP32 tableau is in one CTA's shared
+ * memory when it fits, else in a global workspace; the FP64 re-solve of an
+ * uncertified LP runs in one CTA when its FP64 tableau fits, else on a
+ * thread-block cluster (one LP's latency matters there).
  * STREAMED: global workspace for every LP (FP32_REFINE: the FP32 tableau of
- * every LP; results are bit-identical to AUTO's). */
-enum { LPB_SCHED_AUTO = 0, LPB_SCHED_STREAMED = 1 };
+ * every LP).  CLUSTER: as AUTO, but an FP64 tableau above one CTA is split by
+ * rows over the shared memory of a thread-block cluster of 2-16 CTAs (the
+ * smallest that holds it; all CTAs take the same decisions).  Results are
+ * bit-identical under every schedule. */
+enum { LPB_SCHED_AUTO = 0, LPB_SCHED_STREAMED = 1, LPB_SCHED_CLUSTER = 2 };
 
 typedef struct lp_batch lp_batch;   /* opaque; owned by the library */
 

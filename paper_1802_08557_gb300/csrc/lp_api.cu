@@ -419,7 +419,8 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
     if (opts) o = *opts;
     if (o.precision != LP_PREC_FP64 && o.precision != LP_PREC_FP32_REFINE)
         return fail(LPB_EINVAL, "unsupported precision");
-    if (o.schedule != LPB_SCHED_AUTO && o.schedule != LPB_SCHED_STREAMED) return fail(LPB_EINVAL, "unknown schedule");
+    if (o.schedule != LPB_SCHED_AUTO && o.schedule != LPB_SCHED_STREAMED && o.schedule != LPB_SCHED_CLUSTER)
+        return fail(LPB_EINVAL, "unknown schedule");
     if (!(o.eps_opt >= 0) || !(o.eps_piv >= 0) || !(o.eps_feas >= 0) || !(o.tau >= 0))
         return fail(LPB_EINVAL, "tolerances must be >= 0");
 
@@ -566,7 +567,7 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
                 fbig_lps.push_back(k);
             }
             const size_t mneed = lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]);
-            if (o.schedule == LPB_SCHED_AUTO && mneed <= queue_smem_cap) {
+            if (o.schedule != LPB_SCHED_STREAMED && mneed <= queue_smem_cap) {
                 const int threads = mixed_threads(hm[k], hn[k], hk[k], o.block_threads);
                 // shared memory rounded to 1 KiB for the one-warp form (it sets
                 // how many LPs share an SM), to 8 KiB otherwise: fewer, larger
@@ -582,7 +583,10 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
             }
             continue;
         }
-        if (need > lpb::kMaxSmemPerBlock && o.schedule == LPB_SCHED_AUTO) {
+        // (measured on GB300: the streamed kernel, 304 LPs at once, beats the
+        // clusters, ~50 LPs at once, on every large-LP workload tried --
+        // 1.04-1.34x, more with more pivots -- so clusters are on request)
+        if (need > lpb::kMaxSmemPerBlock && o.schedule == LPB_SCHED_CLUSTER) {
             // the smallest cluster whose CTAs hold the tableau's rows
             int C = 0;
             for (int c = 2; c <= lpb::kMaxClusterCtas && !C; ++c)

@@ -196,12 +196,19 @@ __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int
         __syncthreads();
         const int left = col_var[e];
         const int rows = max(0, min(Ract, r_lo + rp) - r_lo);
-        const int total = rows * Cact;
+        // this CTA's rows except the pivot row, element by element with the
+        // (row, column) position stepped incrementally (no division per element)
+        const int lloc = (q == ql) ? l - r_lo : rows;  // local index of the pivot row (rows: not here)
+        const int total = (rows - (lloc < rows ? 1 : 0)) * Cact;
+        int ii = tid / Cact, jj = tid - ii * Cact;
+        const int di = nt / Cact, dj = nt - di * Cact;
         for (int idx = tid; idx < total; idx += nt) {
-            const int lr = idx / Cact, j = idx - lr * Cact;
-            if (r_lo + lr == l) continue;
-            double* t = T + (size_t)lr * LD + j;
-            *t = __fma_rn(-colE[lr], ob[j], (j == e) ? 0.0 : *t);
+            const int lr = ii + (ii >= lloc ? 1 : 0);
+            double* t = T + (size_t)lr * LD + jj;
+            *t = __fma_rn(-colE[lr], ob[jj], (jj == e) ? 0.0 : *t);
+            ii += di;
+            jj += dj;
+            if (jj >= Cact) { jj -= Cact; ++ii; }
         }
         __syncthreads();
         if (left >= nm) {

@@ -81,6 +81,11 @@ struct Tab {
 // colE[0..Ract) must hold column e on entry.  Returns the variable that left
 // the basis (now the label of column e), read by every thread between the two
 // barriers, where nothing writes it.
+// kPairs (the streamed kernel: rows 32-byte aligned in global memory, LD a
+// multiple of 4): the update takes two adjacent columns per thread with
+// 16-byte loads and stores -- the same FMA for every element, so the same
+// results; the pair beyond an odd Cact is padding (updated, never read).
+template <bool kPairs = false>
 __device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int LD = tb.LD;
@@ -99,6 +104,31 @@ __device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e) 
     }
     __syncthreads();
     const int left = tb.col_var[e];
+    if (kPairs) {
+        const int Cp = (Cact + 1) >> 1;
+        const int total = (Ract - 1) * Cp;
+        int ii = tid / Cp;
+        int jp = tid - ii * Cp;
+        const int di = nt / Cp;
+        const int dj = nt - di * Cp;
+        const double2* Tl2 = reinterpret_cast<const double2*>(Tl);
+        for (int idx = tid; idx < total; idx += nt) {
+            const int r = ii + (ii >= l ? 1 : 0);
+            double2* t = reinterpret_cast<double2*>(T + (size_t)r * LD) + jp;
+            const double2 old = *t;
+            const double2 p = Tl2[jp];
+            const double c = -colE[r];
+            double2 v;
+            v.x = __fma_rn(c, p.x, (2 * jp == e) ? 0.0 : old.x);
+            v.y = __fma_rn(c, p.y, (2 * jp + 1 == e) ? 0.0 : old.y);
+            *t = v;
+            ii += di;
+            jp += dj;
+            if (jp >= Cp) { jp -= Cp; ++ii; }
+        }
+        __syncthreads();
+        return left;
+    }
     const int total = (Ract - 1) * Cact;
     int ii = tid / Cact;
     int jj = tid - ii * Cact;
@@ -293,7 +323,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
                 const int e = (int)(sel & 0xffffu);
                 for (int r = tid; r < m + 1; r += nt) tb.colE[r] = T[(size_t)r * LD + e];
                 __syncthreads();
-                const int left = pivot(tb, m + 1, Cvar + 1, i, e);
+                const int left = pivot<kStreamed>(tb, m + 1, Cvar + 1, i, e);
                 ++iters;
                 if (left >= nm) retire_column(tb, m + 1, e, Cvar);
             }
@@ -389,7 +419,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         if (iters >= max_iters) { status = kIterLimit; break; }
 
         // ---- Step 3: pivot ---------------------------------------------------
-        const int left = pivot(tb, Ract, Cvar + 1, l, e);
+        const int left = pivot<kStreamed>(tb, Ract, Cvar + 1, l, e);
         ++iters;
         if (left >= nm) retire_column(tb, Ract, e, Cvar);
     }

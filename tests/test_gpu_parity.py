@@ -237,12 +237,12 @@ def test_streamed_kernel_matches_resident_bitwise():
         np.testing.assert_array_equal(a[key], b[key], err_msg=key)
 
 
-@pytest.mark.parametrize("schedule", ["auto", "streamed"])
+@pytest.mark.parametrize("schedule", ["auto", "streamed", "cluster"])
 def test_large_lps_take_the_cluster_or_streamed_path(schedule):
-    """Tableaux above one CTA's shared memory (e.g. 500 x 500) are split over a
-    thread-block cluster's shared memory (AUTO) or solved in a global
-    workspace (STREAMED); compared with the oracle bit for bit, phase I
-    included."""
+    """Tableaux above one CTA's shared memory (e.g. 500 x 500) are solved in a
+    global workspace (AUTO: those LPs only; STREAMED: every LP) or split over a
+    thread-block cluster's shared memory (CLUSTER); compared with the oracle
+    bit for bit, phase I included."""
     rng = np.random.default_rng(8)
     lps = []
     for m, n in [(500, 500), (320, 260), (180, 420), (260, 200), (400, 90)]:
@@ -255,10 +255,13 @@ def test_large_lps_take_the_cluster_or_streamed_path(schedule):
     lps.append((rng.uniform(-1, 1, (300, 300)), rng.uniform(-5, 10, 300), rng.uniform(-1, 1, 300)))
     lps += [W.mixed_sign_dense(30, 40, 40, start=9).lp(k) for k in range(30)]  # resident ones alongside
     batch = W.pack("large", lps)
-    opts = None if schedule == "auto" else lpb.lpb_default_opts(schedule=lpb.LPB_SCHED_STREAMED)
-    g, r, n, bitwise = _check(batch, opts=opts)
-    if schedule == "auto":
+    sched = {"auto": lpb.LPB_SCHED_AUTO, "streamed": lpb.LPB_SCHED_STREAMED, "cluster": lpb.LPB_SCHED_CLUSTER}
+    g, r, n, bitwise = _check(batch, opts=lpb.lpb_default_opts(schedule=sched[schedule]))
+    if schedule == "cluster":
         assert g["plan"]["num_cluster"] == 7 and g["plan"]["num_streamed"] == 0
+        assert g["plan"]["num_resident"] == 30
+    elif schedule == "auto":
+        assert g["plan"]["num_streamed"] == 7 and g["plan"]["num_cluster"] == 0
         assert g["plan"]["num_resident"] == 30
     else:
         assert g["plan"]["num_streamed"] == batch.num_lps
@@ -269,7 +272,7 @@ def test_cluster_kernel_matches_streamed_bitwise():
     """Mixed-sign 260 x 260 LPs (phase I, infeasible and unbounded ones among
     them) on thread-block clusters and in the global workspace: identical."""
     batch = W.mixed_sign_dense(24, 260, 260, start=4321)
-    a = gpu_solve(batch)
+    a = gpu_solve(batch, opts=lpb.lpb_default_opts(schedule=lpb.LPB_SCHED_CLUSTER))
     b = gpu_solve(batch, opts=lpb.lpb_default_opts(schedule=lpb.LPB_SCHED_STREAMED))
     assert a["plan"]["num_cluster"] == batch.num_lps and b["plan"]["num_cluster"] == 0
     assert len(set(a["status"].tolist())) >= 2
