@@ -550,6 +550,20 @@ def run_ours(args):
                 "results_unchanged_by_tuning": bool(all(np.array_equal(ru[k], rt[k]) for k in ("status", "obj", "x"))),
                 "achieved_gflops": fl / (best * 1e-3) / 1e9, "fp64_peak_gflops": FP64_PEAK_GFLOPS,
             }
+        # FP64 in one persistent launch (LPB_SCHED_SINGLE: one work queue,
+        # longest work first, shared memory or a global slot per LP)
+        hs1 = lpb.BatchSolver(ub, opts=lpb.lpb_default_opts(precision=lpb.LP_PREC_FP64,
+                                                             schedule=lpb.LPB_SCHED_SINGLE), stream=stream)
+        ms_single = ev_time(lambda: lpb.lp_batch_solve(hs1.h, stream))
+        ms_single_graph = ev_time(lambda: lpb.lp_batch_solve_graph(hs1.h, stream))
+        r1 = hs1.results()
+        uneven["fp64_single_launch"] = {
+            "ms": ms_single, "ms_graph": ms_single_graph, "launches_per_solve": hs1.plan_info()["num_groups"],
+            "default_plan_launches_per_solve": uneven["fp64"]["groups"],
+            "value": ub.num_lps * ws / (min(ms_single, ms_single_graph) * 1e-3),
+            "results_identical_to_default_plan": bool(all(np.array_equal(r1[k], res_u["fp64"][k])
+                                                          for k in ("status", "iters", "obj", "x", "y")))}
+        hs1.close()
         uneven["value"] = max(uneven["fp64"]["value"], uneven["fp32r"]["value"])
         opt_u = res_u["fp64"]["status"] == 0
         rel_u = (np.abs(res_u["fp32r"]["obj"][opt_u] - res_u["fp64"]["obj"][opt_u])

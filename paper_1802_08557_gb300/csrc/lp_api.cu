@@ -114,6 +114,10 @@ constexpr int kTimingRing = 64;
 // Cap of the streamed kernel's global workspace (slots x largest tableau).
 constexpr int64_t kMaxWorkspaceBytes = int64_t(16) << 30;
 
+// LPB_SCHED_SINGLE: the largest tableau kept in shared memory (two 512-thread
+// CTAs per SM); larger ones go to the CTA's global workspace slot.
+constexpr size_t kSingleSmemCap = 110 * 1024;
+
 int pick_threads(int m, int n, int k, int requested) {
     if (requested > 0) return std::min(std::max(32, (requested + 31) / 32 * 32), lpb::kMaxThreads);
     const int64_t e = (int64_t)(m + 1 + (k > 0)) * (n + k + 1);
@@ -225,6 +229,13 @@ struct lp_batch {
     std::vector<ClusterGroup> cluster_groups;
     int32_t* cluster_counter = nullptr;
     int32_t num_cluster = 0;
+    // LPB_SCHED_SINGLE: every LP in one persistent launch over order[single_offset ...)
+    int64_t single_offset = 0;
+    int32_t num_single = 0, num_single_streamed = 0, single_ctas = 0;
+    size_t single_smem = 0, single_slot_bytes = 0;
+    uint8_t* d_resident = nullptr;     // per LP: 1 = tableau in shared memory
+    unsigned char* single_workspace = nullptr;
+    int32_t* single_counter = nullptr;
     // captured solve (lp_batch_solve_graph)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -300,6 +311,7 @@ lpb_err enqueue_solve(lp_batch* h, cudaStream_t s, bool timing) {
     for (const Group& g : h->mixed_groups) jobs.push_back({0, &g, g.count});
     for (const Group& g : h->groups) jobs.push_back({1, &g, g.count});
     if (h->num_streamed > 0) jobs.push_back({2, nullptr, h->num_streamed});
+    if (h->num_single > 0) jobs.push_back({5, nullptr, h->num_single});
     if (h->num_mstream > 0) jobs.push_back({4, nullptr, h->num_mstream});
     for (size_t ci = 0; ci < h->cluster_groups.size(); ++ci)
         jobs.push_back({3, reinterpret_cast<const Group*>(ci), h->cluster_groups[ci].count});
@@ -316,7 +328,11 @@ lpb_err enqueue_solve(lp_batch* h, cudaStream_t s, bool timing) {
             used[lane] = true;
         }
         const Job& j = jobs[i];
-        if (j.kind == 2) {
+        if (j.kind == 5) {
+            err = lpb::launch_fp64_single(h->d, h->tol, h->d_order + h->single_offset, h->d_resident, h->num_single,
+                                          h->single_ctas, h->single_smem, h->single_workspace, h->single_slot_bytes,
+                                          h->single_counter, h->diag, ls);
+        } else if (j.kind == 2) {
             err = lpb::launch_fp64_streamed(h->d, h->tol, h->d_order + h->streamed_offset, h->num_streamed,
                                             h->streamed_slots, h->workspace, h->slot_bytes, h->counter, h->diag, ls);
         } else if (j.kind == 4) {
@@ -419,8 +435,11 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
     if (opts) o = *opts;
     if (o.precision != LP_PREC_FP64 && o.precision != LP_PREC_FP32_REFINE)
         return fail(LPB_EINVAL, "unsupported precision");
-    if (o.schedule != LPB_SCHED_AUTO && o.schedule != LPB_SCHED_STREAMED && o.schedule != LPB_SCHED_CLUSTER)
+    if (o.schedule != LPB_SCHED_AUTO && o.schedule != LPB_SCHED_STREAMED && o.schedule != LPB_SCHED_CLUSTER &&
+        o.schedule != LPB_SCHED_SINGLE)
         return fail(LPB_EINVAL, "unknown schedule");
+    if (o.schedule == LPB_SCHED_SINGLE && o.precision != LP_PREC_FP64)
+        return fail(LPB_EINVAL, "LPB_SCHED_SINGLE is for LP_PREC_FP64");
     if (!(o.eps_opt >= 0) || !(o.eps_piv >= 0) || !(o.eps_feas >= 0) || !(o.tau >= 0))
         return fail(LPB_EINVAL, "tolerances must be >= 0");
 
@@ -540,6 +559,8 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
     std::map<int, std::vector<int32_t>> cluster_buckets;  // cluster size -> LPs
     std::vector<int32_t> mstream;                         // mixed precision, tableau in global memory
     std::vector<int32_t> fbig_lps;                        // mixed LPs whose FP64 re-solve exceeds one CTA
+    std::vector<int32_t> single;                          // LPB_SCHED_SINGLE: every LP
+    std::vector<uint8_t> single_resident;                 // ... per LP: 1 = in shared memory
     const size_t queue_smem_cap = lpb::kMaxSmemPerBlock - 1024;
     h->uniform_m = hm[0];
     h->uniform_n = hn[0];
@@ -580,6 +601,20 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
                 mstream.push_back(k);
                 h->mslot_bytes = std::max(h->mslot_bytes, (lpb::mixed_layout(hm[k], hn[k], hk[k]).total + 255) &
                                                               ~size_t(255));
+            }
+            continue;
+        }
+        if (o.schedule == LPB_SCHED_SINGLE) {
+            // one launch for all: shared memory up to kSingleSmemCap (two
+            // 512-thread CTAs per SM), else this CTA's global workspace slot
+            if (single_resident.empty()) single_resident.assign((size_t)num_lps, 0);
+            single.push_back(k);
+            if (need <= kSingleSmemCap) {
+                single_resident[k] = 1;
+                h->single_smem = std::max(h->single_smem, need);
+            } else {
+                ++h->num_single_streamed;
+                h->single_slot_bytes = std::max(h->single_slot_bytes, lpb::streamed_slot_bytes(hm[k], hn[k], hk[k]));
             }
             continue;
         }
@@ -703,6 +738,10 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
         if ((err = alloc(h, &h->mworkspace, (size_t)slots * h->mslot_bytes, s)) || (err = alloc(h, &h->mcounter, 1, s)))
             return bail_cuda(err, "mixed streamed workspace allocation");
     }
+    lpt(single);
+    h->single_offset = (int64_t)order.size();
+    h->num_single = (int32_t)single.size();
+    order.insert(order.end(), single.begin(), single.end());
     lpt(streamed);
     h->streamed_offset = (int64_t)order.size();
     h->num_streamed = (int32_t)streamed.size();
@@ -713,6 +752,26 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
     // scope before the copies run)
     if ((err = cudaMemcpyAsync(dorder, order.data(), nl * 4, cudaMemcpyHostToDevice, s)))
         return bail_cuda(err, "plan upload");
+    if (h->num_single > 0) {
+        if ((err = alloc(h, &h->d_resident, (size_t)num_lps, s)) ||
+            (err = cudaMemcpyAsync(h->d_resident, single_resident.data(), (size_t)num_lps, cudaMemcpyHostToDevice, s)))
+            return bail_cuda(err, "plan upload");
+        int sms = 0;
+        h->single_smem = (std::max(h->single_smem, lpb::SmallLayout::total) + 1023) / 1024 * 1024;
+        if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device)) ||
+            (err = lpb::fp64_single_prepare(h->single_smem)))
+            return bail_cuda(err, "single launch set-up");
+        const int per_sm = std::max(1, lpb::fp64_single_ctas_per_sm(h->single_smem));
+        int64_t ctas = std::min<int64_t>((int64_t)sms * per_sm, h->num_single);
+        if (h->num_single_streamed > 0) {
+            h->single_slot_bytes = (h->single_slot_bytes + 255) & ~size_t(255);
+            ctas = std::min<int64_t>(ctas, std::max<int64_t>(1, kMaxWorkspaceBytes / (int64_t)h->single_slot_bytes));
+            if ((err = alloc(h, &h->single_workspace, (size_t)ctas * h->single_slot_bytes, s)))
+                return bail_cuda(err, "single-launch workspace allocation");
+        }
+        h->single_ctas = (int32_t)ctas;
+        if ((err = alloc(h, &h->single_counter, 1, s))) return bail_cuda(err, "single-launch counter");
+    }
     if (h->num_streamed > 0) {
         int sms = 0;
         if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device)))
@@ -961,9 +1020,19 @@ lpb_err lp_batch_group_info(lp_batch* h, int32_t index, lp_batch_group* out) {
     const int32_t nr = (int32_t)h->groups.size(), nm = (int32_t)h->mixed_groups.size();
     const int32_t nc = (int32_t)h->cluster_groups.size();
     const int32_t ns = h->num_streamed > 0 ? 1 : 0;
-    const int32_t total = nr + nm + nc + ns + (h->num_mstream > 0 ? 1 : 0);
+    const int32_t nms = h->num_mstream > 0 ? 1 : 0;
+    const int32_t total = nr + nm + nc + ns + nms + (h->num_single > 0 ? 1 : 0);
     if (index < 0 || index >= total) return fail(LPB_EINVAL, "group index out of range");
     std::memset(out, 0, sizeof *out);
+    if (h->num_single > 0 && index == total - 1) {
+        out->kind = 5;
+        out->count = h->num_single;
+        out->threads = lpb::kStreamedThreads;
+        out->persistent = 1;
+        out->smem_bytes = (int64_t)h->single_smem;
+        out->tuned_ms = -1.0f;
+        return LPB_OK;
+    }
     if (index >= nr + nm && index < nr + nm + nc) {
         const lp_batch::ClusterGroup& g = h->cluster_groups[index - nr - nm];
         out->kind = 3;
@@ -1161,8 +1230,8 @@ lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
     if (!h || !plan) return fail(LPB_EINVAL, "handle or plan is NULL");
     plan->num_groups = (int32_t)(h->groups.size() + h->mixed_groups.size() + h->cluster_groups.size()) +
                        (h->num_streamed > 0 ? 1 : 0) + (h->num_mstream > 0 ? 1 : 0) + (h->num_fsmall > 0 ? 1 : 0) +
-                       (h->num_fbig > 0 ? 1 : 0);
-    plan->num_resident = h->num_lps - h->num_streamed - h->num_mstream - h->num_cluster;
+                       (h->num_fbig > 0 ? 1 : 0) + (h->num_single > 0 ? 1 : 0);
+    plan->num_resident = h->num_lps - h->num_streamed - h->num_mstream - h->num_cluster - h->num_single_streamed;
     plan->num_cluster = h->num_cluster;
     plan->num_mixed = h->num_mixed;
     plan->num_fallback = 0;
@@ -1192,7 +1261,7 @@ lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
         plan->internal_error_lp = dg[0] ? dg[2] : -1;
         for (int i = 0; i < 5; ++i) plan->internal_error_detail[i] = dg[0] ? dg[3 + i] : 0;
     }
-    plan->num_streamed = h->num_streamed + h->num_mstream;
+    plan->num_streamed = h->num_streamed + h->num_mstream + h->num_single_streamed;
     plan->num_phase1 = h->num_phase1;
     plan->max_smem_bytes = (int64_t)h->max_smem;
     plan->workspace_bytes = (int64_t)h->streamed_slots * (int64_t)h->slot_bytes +

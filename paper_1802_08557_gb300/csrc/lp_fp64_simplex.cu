@@ -519,6 +519,36 @@ fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* _
     }
 }
 
+// A whole batch in one launch: persistent CTAs take the LPs order[0 ..
+// count) (longest work first) from the atomic `counter` and solve each with
+// the tableau in this CTA's shared memory when it fits (resident[lp] != 0),
+// else in this CTA's global workspace slot -- the same per-LP code as the
+// resident and streamed kernels, so the same results.
+__global__ void __launch_bounds__(kStreamedThreads, 2)
+fp64_single_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order,
+                   const uint8_t* __restrict__ resident, const int32_t count, unsigned char* workspace,
+                   const size_t slot_bytes, int32_t* __restrict__ counter, int32_t* __restrict__ diag)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int next;
+    unsigned char* slot = workspace ? workspace + (size_t)blockIdx.x * slot_bytes : nullptr;
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int idx = next;
+        __syncthreads();
+        if (idx >= count) break;
+        const int lp = order[idx];
+        if (resident[lp])
+            solve_one<false>(B, tol, lp, smem, smem + SmallLayout::total, diag);
+        else if (slot)
+            solve_one<true>(B, tol, lp, smem, slot, diag);
+        else if (threadIdx.x == 0)
+            record_internal_error(diag, 7, lp);  // a plan without a slot for a streamed LP
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 cudaError_t fp64_kernels_prepare() {
@@ -561,6 +591,34 @@ cudaError_t launch_fp64_streamed(const DeviceBatch& B, const Tolerances& tol, co
     cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
     if (err != cudaSuccess) return err;
     fp64_streamed_kernel<<<slots, kStreamedThreads, 0, stream>>>(B, tol, order, count, count_dev, workspace,
+                                                                  slot_bytes, counter, diag);
+    return cudaGetLastError();
+}
+
+// fp64_single_kernel: the largest dynamic shared memory that still lets
+// `per_sm` CTAs share an SM, and how many do at a given size.
+cudaError_t fp64_single_prepare(size_t smem) {
+    return cudaFuncSetAttribute(fp64_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int fp64_single_ctas_per_sm(size_t smem) {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fp64_single_kernel, kStreamedThreads, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return blocks;
+}
+
+cudaError_t launch_fp64_single(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
+                               const uint8_t* resident, int32_t count, int ctas, size_t smem,
+                               unsigned char* workspace, size_t slot_bytes, int32_t* counter, int32_t* diag,
+                               cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
+    if (err != cudaSuccess) return err;
+    fp64_single_kernel<<<ctas, kStreamedThreads, smem, stream>>>(B, tol, order, resident, count, workspace,
                                                                   slot_bytes, counter, diag);
     return cudaGetLastError();
 }

@@ -196,6 +196,12 @@ cudaError_t launch_fp64_streamed(const DeviceBatch& B, const Tolerances& tol, co
                                  int32_t* counter, int32_t* diag, cudaStream_t stream,
                                  const int32_t* count_dev = nullptr);
 // CTAs of the streamed kernel that fit on one SM.
+cudaError_t fp64_single_prepare(size_t smem);
+int fp64_single_ctas_per_sm(size_t smem);
+cudaError_t launch_fp64_single(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
+                               const uint8_t* resident, int32_t count, int ctas, size_t smem,
+                               unsigned char* workspace, size_t slot_bytes, int32_t* counter, int32_t* diag,
+                               cudaStream_t stream);
 int fp64_streamed_ctas_per_sm();
 // Resident kernel over a device-side LP list (persistent CTAs, atomic
 // `counter` zeroed on `stream` before the launch).  `smem` must cover every

@@ -20,7 +20,7 @@ LP_OPTIMAL, LP_INFEASIBLE, LP_UNBOUNDED, LP_ITER_LIMIT, LP_NUMERICAL = 0, 1, 2, 
 LPB_OK, LPB_EINVAL, LPB_ENOMEM, LPB_ECUDA, LPB_ETOOBIG, LPB_ENOTSOLVED = 0, 1, 2, 3, 4, 5
 LPB_HOST, LPB_DEVICE = 0, 1
 LP_PREC_FP64, LP_PREC_FP32_REFINE = 0, 1
-LPB_SCHED_AUTO, LPB_SCHED_STREAMED, LPB_SCHED_CLUSTER = 0, 1, 2
+LPB_SCHED_AUTO, LPB_SCHED_STREAMED, LPB_SCHED_CLUSTER, LPB_SCHED_SINGLE = 0, 1, 2, 3
 LPB_MAX_DIM = 16384
 LPB_EPI_STORE, LPB_EPI_BIAS_RELU, LPB_EPI_BIAS, LPB_EPI_MASK_GRAD = 0, 1, 2, 3
 LPB_GEMM_AUTO, LPB_GEMM_MMA64, LPB_GEMM_MMA128, LPB_GEMM_TC = 0, 1, 2, 3

@@ -99,3 +99,42 @@ def test_lpt_order_and_errors():
             lpb.lp_batch_autotune(s.h, rounds=0)
     finally:
         s.close()
+
+
+def test_single_launch_schedule_gives_identical_results():
+    """LPB_SCHED_SINGLE: the whole uneven batch in one persistent launch (one
+    work queue, longest work first; tableaux up to 110 KB in shared memory,
+    larger ones in the CTA's global workspace slot) -- the same bits as the
+    default plan's many launch groups, large LPs and phase I included, and
+    again on a repeat solve and through a graph replay."""
+    rng = np.random.default_rng(21)
+    lps = [W.uneven_dense(300, lo=8, hi=200, start=40).lp(k) for k in range(300)]
+    for m, n in [(300, 250), (420, 160), (260, 300)]:        # tableaux above 110 KB
+        lps.append((rng.uniform(0, 1, (m, n)), rng.uniform(1, 100, m), rng.uniform(0, 1, n)))
+    A = rng.uniform(-1, 1, (150, 140)); b = rng.uniform(-5, 10, 150); c = rng.uniform(-1, 1, 140)
+    lps.append((A, b, c))                                     # phase I, mid size
+    lps += [W.mixed_sign_dense(50, 40, 40, start=3).lp(k) for k in range(50)]
+    batch = W.pack("single", lps)
+    ref = lpb.BatchSolver(batch, opts=lpb.lpb_default_opts())
+    try:
+        ref.solve()
+        want = ref.results()
+    finally:
+        ref.close()
+    s = lpb.BatchSolver(batch, opts=lpb.lpb_default_opts(schedule=lpb.LPB_SCHED_SINGLE))
+    try:
+        plan = s.plan_info()
+        groups = lpb.lp_batch_groups(s.h)
+        assert plan["num_groups"] == 1 and len(groups) == 1 and groups[0]["kind"] == 5, groups
+        assert groups[0]["count"] == batch.num_lps and plan["num_streamed"] >= 3
+        for run in range(2):
+            s.solve()
+            _same(s.results(), want)
+            assert s.plan_info()["internal_errors"] == 0
+        lpb.lp_batch_solve_graph(s.h)
+        _same(s.results(), want)
+    finally:
+        s.close()
+    with pytest.raises(lpb.LPBError):  # mixed precision has no single-launch form
+        lpb.BatchSolver(batch, opts=lpb.lpb_default_opts(precision=lpb.LP_PREC_FP32_REFINE,
+                                                         schedule=lpb.LPB_SCHED_SINGLE))
