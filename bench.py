@@ -88,6 +88,10 @@ def parse():
     p.add_argument("--warm-train", type=int, default=1_000_000, help="self-solved LPs the network is trained on")
     p.add_argument("--warm-test", type=int, default=100_000, help="test LPs of the warm-start measurement")
     p.add_argument("--hyperbox-dirs", type=int, default=1 << 22, help="directions of the hyperbox measurement")
+    p.add_argument("--profile-case", default=None, choices=["gemm_tc_layer1", "fp64_streamed_uneven"],
+                   help="run one workload a few times for a profiler and exit (no JSON line): the warm-start "
+                        "network's first-layer product on the tcgen05 kernel (1e5 x 320 -> 512, bias + ReLU), or "
+                        "the uneven workload's LPs above one CTA on the streamed FP64 kernel")
     p.add_argument("--precision", default="fp32r", choices=["fp32r", "fp64"],
                    help="headline path: FP32 tableau + FP64 certificate (default) or plain FP64")
     return p.parse_args()
@@ -807,8 +811,45 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """One workload, a few launches, for ncu (see --profile-case)."""
+    import torch
+    from paper_1802_08557_gb300 import build, lpbatch as lpb
+    from paper_1802_08557_gb300 import workloads as W
+    build.build()
+    lpb.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    if args.profile_case == "gemm_tc_layer1":
+        nl = args.warm_test
+        g = torch.Generator(device=dev).manual_seed(0)
+        a = torch.randn((nl, 320), device=dev, generator=g).to(torch.bfloat16)
+        w = (torch.rand((512, 320), device=dev, generator=g) * 0.2 - 0.1).to(torch.bfloat16)
+        bias = torch.zeros(512, dtype=torch.float32, device=dev)
+        h = torch.empty((nl, 512), dtype=torch.bfloat16, device=dev)
+        for _ in range(4):
+            lpb.lp_mlp_gemm_bf16(lpb.LPB_EPI_BIAS_RELU, lpb.LPB_GEMM_TC, nl, 512, 320, a, 320, w, 320, None, 0, bias,
+                                 None, h, 512, None, 0, stream)
+        torch.cuda.synchronize()
+        print(f"gemm_tc_layer1: 4 launches of {nl} x 320 -> 512, faults {lpb.lp_mlp_tc_faults()}")
+    else:
+        ub = W.uneven_dense(args.uneven_lps)
+        um, un = ub.m.astype(np.float64), ub.n.astype(np.float64)
+        big = ub.subset(np.nonzero((um + 2.0) * (un + 1.0) * 8.0 > 227 * 1024)[0])
+        hs = lpb.BatchSolver(big, opts=lpb.lpb_default_opts(precision=lpb.LP_PREC_FP64,
+                                                            schedule=lpb.LPB_SCHED_STREAMED), stream=stream)
+        for _ in range(3):
+            lpb.lp_batch_solve(hs.h, stream)
+        r = hs.results()
+        hs.close()
+        print(f"fp64_streamed_uneven: 3 solves of {big.num_lps} LPs, mean pivots {r['iters'].mean():.1f}")
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
