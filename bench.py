@@ -201,6 +201,12 @@ def cpu_oracle_rate(batch, sample: int, threads: int):
     return rate, dt, len(idx)
 
 
+def oracle_rate_note(rate: float, seconds: float, count: int) -> dict:
+    """The oracle's own rate on the LPs it was compared on (all host threads)."""
+    return {"all_threads": rate, "cores": os.cpu_count() or 1, "unit": "LPs/s",
+            "sample": f"{count} evenly spaced LPs, {seconds:.2f} s wall"}
+
+
 def vs_oracle(status, obj, idx, ores) -> dict:
     """Per-LP agreement of GPU results (status, obj over the whole batch) with
     the oracle's on LPs idx: status mismatches and the distribution of the
@@ -490,9 +496,10 @@ def run_ours(args):
                                         "max_rel_obj_err_on_optimal": float(rel.max()) if rel.size else 0.0}
         if rank == 0:
             idx_s = sample_indices(sb.num_lps, args.oracle_sample)
-            _, _, o_s = cpu_oracle_run(sb, idx_s, os.cpu_count() or 1)
+            r_s, dt_s, o_s = cpu_oracle_run(sb, idx_s, os.cpu_count() or 1)
             support["vs_oracle"] = {lab: vs_oracle(res_s[lab]["status"], res_s[lab]["obj"], idx_s, o_s)
                                     for lab in ("fp64", "fp32r")}
+            support["cpu_oracle"] = oracle_rate_note(r_s, dt_s, len(idx_s))
         support["timing"] = "CUDA events on the solve's stream around K whole solves"
         del sb, res_s
 
@@ -606,10 +613,11 @@ def run_ours(args):
             del bsub, big
         if rank == 0:
             idx_u = sample_indices(ub.num_lps, max(50, args.oracle_sample // 5))
-            _, dt_u, o_u = cpu_oracle_run(ub, idx_u, os.cpu_count() or 1)
+            r_u, dt_u, o_u = cpu_oracle_run(ub, idx_u, os.cpu_count() or 1)
             uneven["vs_oracle"] = {lab: vs_oracle(res_u[lab]["status"], res_u[lab]["obj"], idx_u, o_u)
                                    for lab in ("fp64", "fp32r")}
-            uneven["vs_oracle"]["sample"] = f"{len(idx_u)} evenly spaced LPs (oracle {dt_u:.1f} s)"
+            uneven["vs_oracle"]["sample"] = f"{len(idx_u)} evenly spaced LPs (oracle {dt_u:.2f} s)"
+            uneven["cpu_oracle"] = oracle_rate_note(r_u, dt_u, len(idx_u))
         uneven["timing"] = "CUDA events on the solve's stream around K whole solves (default plan, autotuned plan, graph replay)"
         del ub
 
@@ -685,9 +693,10 @@ def run_ours(args):
         warm_oracle = None
         if rank == 0:
             idx_w = sample_indices(nt_, args.oracle_sample)
-            _, _, o_w = cpu_oracle_run(test_set, idx_w, os.cpu_count() or 1)
+            r_w, dt_w, o_w = cpu_oracle_run(test_set, idx_w, os.cpu_count() or 1)
             warm_oracle = {"warm": vs_oracle(rw["status"], rw["obj"], idx_w, o_w),
-                           "cold_fp64": vs_oracle(rc["status"], rc["obj"], idx_w, o_w)}
+                           "cold_fp64": vs_oracle(rc["status"], rc["obj"], idx_w, o_w),
+                           "cpu_oracle": oracle_rate_note(r_w, dt_w, len(idx_w))}
         warm = {
             "workload": f"shared200x100_test{nt_}",
             "value": nt_ * ws * args.steps / (e_warm * 1e-3), "unit": "LPs/s", "ms_per_step": e_warm / args.steps,
