@@ -290,8 +290,10 @@ __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int
         }
         // ---- B: Step 2.  FP32 screen of this CTA's rows (rows whose operands
         // leave [2^-100, 2^100] are always candidates), cluster minimum, window
-        // max(2^-12, 8 tau) relative + max(2^-20, 8 tau) absolute (wider than
-        // every FP32 rounding error); one candidate in the cluster is the exact
+        // max(2^-12, 8 tau) relative + max(2^-20, 8 tau) absolute (far wider
+        // than the screen's error: operands truncated to FP32 by integer
+        // operations, < 2^-23 relative each, no FP64-pipe conversion, and the
+        // approximate divide); one candidate in the cluster is the exact
         // answer, several get the exact rule on their exact ratios.
         int floc = INT_MAX;
         for (int lr = tid; lr < nrow; lr += nt) {
@@ -305,7 +307,7 @@ __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int
                 const int et = dexp(t), eb = dexp(beta);
                 const bool safe = et >= -100 && et <= 100 && (abskey(beta) == 0 || (eb >= -100 && eb <= 100));
                 if (safe) {
-                    const int fk = fkey(__fdividef(__double2float_rn(beta), __double2float_rn(t)));
+                    const int fk = fkey(__fdividef(f64_to_f32_trunc(beta), f64_to_f32_trunc(t)));
                     code = fk;
                     floc = min(floc, fk);
                 } else {

@@ -355,7 +355,11 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
 
         // ---- Step 2: leaving row (minimum ratio rhs_i / t_ie, t_ie > eps) --
         // FP32 screen: rows with both operands in [2^-100, 2^100] (or rhs 0)
-        // get a float ratio; the others are always candidates.
+        // get a float ratio; the others are always candidates.  The operands
+        // are truncated to FP32 by integer operations (< 2^-23 relative
+        // each): a hardware conversion would take the FP64 pipe, which bounds
+        // this kernel.  The window (far wider than the screen's error) is
+        // set below.
         int floc = INT_MAX;
         for (int i = tid; i < Ract; i += nt) {
             const double t = T[(size_t)i * LD + e];
@@ -367,7 +371,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
                     const int et = dexp(t), eb = dexp(beta);
                     const bool safe = et >= -100 && et <= 100 && (abskey(beta) == 0 || (eb >= -100 && eb <= 100));
                     if (safe) {
-                        const int fk = fkey(__fdividef(__double2float_rn(beta), __double2float_rn(t)));
+                        const int fk = fkey(__fdividef(f64_to_f32_trunc(beta), f64_to_f32_trunc(t)));
                         code = fk;
                         floc = min(floc, fk);
                     } else {
