@@ -27,16 +27,38 @@ __device__ __forceinline__ void record_internal_error(int32_t* diag, int code, i
 
 // Order-preserving map of a (non-NaN) double to a signed 64-bit key:
 // a < b  <=>  okey(a) < okey(b);  -0 and +0 map to the same key.
+// The keys are built from the two 32-bit words of the double: written on its
+// 64-bit pattern, a test of the key can be compiled into an FP64 compare,
+// which GB300 issues to its narrow FP64 pipe at the cost of an FMA.
 __device__ __forceinline__ long long okey(double v) {
-    long long b = __double_as_longlong(v);
-    b = (b == LLONG_MIN) ? 0LL : b;
-    return b ^ ((b >> 63) & LLONG_MAX);
+    int hi = __double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    hi = (hi == INT_MIN && lo == 0u) ? 0 : hi;  // -0 -> +0
+    const int s = hi >> 31;                     // all ones for a negative v
+    return (long long)(((unsigned long long)(unsigned)(hi ^ (s & INT_MAX)) << 32) |
+                       (unsigned long long)(lo ^ (unsigned)s));
+}
+// v < t, given kt = okey(t) (t not NaN), by integer operations; a NaN v
+// counts as below every threshold, so that no check passes on a NaN.
+__device__ __forceinline__ bool below_key(double v, long long kt) {
+    const unsigned ha = (unsigned)__double2hiint(v) & 0x7FFFFFFFu;
+    const bool nan = ha > 0x7FF00000u || (ha == 0x7FF00000u && (unsigned)__double2loint(v) != 0u);
+    return nan || okey(v) < kt;
+}
+// v > t, given kt = okey(t) (t not NaN), by integer operations; false for a NaN v.
+__device__ __forceinline__ bool above_key(double v, long long kt) {
+    const unsigned ha = (unsigned)__double2hiint(v) & 0x7FFFFFFFu;
+    const bool nan = ha > 0x7FF00000u || (ha == 0x7FF00000u && (unsigned)__double2loint(v) != 0u);
+    return !nan && okey(v) > kt;
 }
 __device__ __forceinline__ double kval(long long k) {
     return __longlong_as_double(k ^ ((k >> 63) & LLONG_MAX));
 }
 // Key of |v| (the plain bit pattern with the sign cleared).
-__device__ __forceinline__ long long abskey(double v) { return __double_as_longlong(v) & LLONG_MAX; }
+__device__ __forceinline__ long long abskey(double v) {
+    return (long long)(((unsigned long long)((unsigned)__double2hiint(v) & 0x7FFFFFFFu) << 32) |
+                       (unsigned long long)(unsigned)__double2loint(v));
+}
 
 __device__ __forceinline__ long long warp_min_i64(long long v) {
     const int hi = (int)(v >> 32);
@@ -80,6 +102,65 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) 
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// ---- mbarriers and bulk asynchronous copies (global -> this CTA's shared
+// memory), for the streamed kernel's staged update ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Makes initialised mbarriers visible to the asynchronous proxy.
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// `bytes` (a multiple of 16) from 16-byte aligned global `src` to 16-byte
+// aligned shared `dst`; completion counted on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Wait for the phase of `bar` with the given parity; false after `cycles`
+// clock cycles (the copy did not complete).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long cycles) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > cycles) return false;
+    return true;
+}
+// Orders this thread's earlier generic-proxy accesses of shared memory before
+// later asynchronous-proxy writes to it (reuse of a staging buffer).
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Orders this thread's earlier generic-proxy writes of global memory before
+// later asynchronous-proxy reads of it (bulk copies of rows it updated).
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 
 // Block-wide reductions over per-warp `redux` results.  Each call writes
 // one slot per warp, waits at a barrier, reads every slot, and waits at a

@@ -65,6 +65,47 @@ __device__ __forceinline__ unsigned long long step1_window(long long kmin, long 
     return (unsigned long long)wb << sh;
 }
 
+// ---- Staged update of the streamed kernel ----------------------------------
+// The rank-1 update of a tableau in global memory is bound by the bytes it
+// keeps in flight.  Each warp streams its share of the rows through a ring of
+// kStageDepth chunks of kStageChunkPairs column pairs in shared memory, filled
+// by bulk asynchronous copies (cp.async.bulk, completion on one mbarrier per
+// chunk) that one lane issues kStageDepth chunks ahead; the pivot row and the
+// pivot column are read from shared-memory copies.  The FMA of every element
+// is the one of the plain loop, so the results are the same bit for bit.
+constexpr int kStageChunkPairs = 128;  // 2 KB per chunk: 4 pairs per lane
+constexpr int kStageDepth = 2;
+constexpr long long kStageWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+
+// A CTA's shared memory for the staged update: a flag word, the mbarriers and
+// rings of every warp, then the pivot-column copy (R doubles) and the
+// pivot-row copy (LD doubles) of the LP being solved.
+struct StageLayout {
+    size_t flag, bars, rings, colE, prow, total;
+};
+__host__ __device__ inline StageLayout stage_layout(int nwarps, int R, int LD) {
+    StageLayout S;
+    size_t o = 0;
+    S.flag = o;  o += 16;
+    S.bars = o;  o += (size_t)nwarps * kStageDepth * 8;
+    o = (o + 127) & ~size_t(127);
+    S.rings = o; o += (size_t)nwarps * kStageDepth * kStageChunkPairs * 16;
+    S.colE = o;  o += align16((size_t)R * 8);
+    S.prow = o;  o += align16((size_t)LD * 8);
+    S.total = o;
+    return S;
+}
+
+// The staged path of one LP (on = false: the plain loop).
+struct Staging {
+    bool on;
+    uint64_t* bar;      // this warp's kStageDepth mbarriers
+    double2* ring;      // this warp's kStageDepth chunks
+    double* prow;       // copy of the scaled pivot row
+    unsigned phase;     // bit s: parity of the next completion of chunk s (warp-uniform)
+    int* fail;          // shared: 1 a copy did not complete (LP abandoned); 2 one may still be in flight
+};
+
 struct Tab {
     double* T;        // R x LD, row-major; column 0 = right-hand side
     double* colE;     // copy of the pivot column
@@ -72,6 +113,90 @@ struct Tab {
     int* row_var;     // basic variable of each constraint row
     int LD;
 };
+
+// Phase B of Step 3 for a tableau in global memory, through the staging
+// rings: chunk c covers row ii = c / cpr (skipping the pivot row l) and pairs
+// [p0, p0 + len) of it; warp w takes chunks w, w + nw, ...  The pivot row is
+// read from st.prow, column e from tb.colE (shared memory on this path).
+// The pair beyond an odd Cact is padding (updated, never read).  A copy that
+// does not complete within kStageWaitCycles abandons the update: *st.fail is
+// set (the caller reports the LP as numerical) after the warp has waited,
+// bounded again, for its other copies.
+__device__ __noinline__ unsigned staged_update(const Staging st, const Tab tb, int Ract, int Cact, int l, int e) {
+    unsigned phase = st.phase;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int LD = tb.LD;
+    const int Cp = (Cact + 1) >> 1;
+    const int cpr = (Cp + kStageChunkPairs - 1) / kStageChunkPairs;
+    const int total = (Ract - 1) * cpr;
+    const double2* P2 = reinterpret_cast<const double2*>(st.prow);
+    auto chunk = [&](int c, int& r, int& p0, int& len) {
+        const int ii = c / cpr;
+        const int piece = c - ii * cpr;
+        r = ii + (ii >= l ? 1 : 0);
+        p0 = piece * kStageChunkPairs;
+        len = min(kStageChunkPairs, Cp - p0);
+    };
+    auto issue = [&](int c, int s) {  // lane 0
+        int r, p0, len;
+        chunk(c, r, p0, len);
+        const unsigned bytes = (unsigned)len * 16u;
+        mbar_expect_tx(&st.bar[s], bytes);
+        bulk_load(st.ring + s * kStageChunkPairs, tb.T + (size_t)r * LD + 2 * p0, bytes, &st.bar[s]);
+    };
+    unsigned pending = 0;  // chunks issued and not yet waited for (warp-uniform)
+    for (int s = 0; s < kStageDepth; ++s) {
+        const int c = warp + s * nw;
+        if (c < total) {
+            if (lane == 0) issue(c, s);
+            pending |= 1u << s;
+        }
+    }
+    bool ok = true;
+    for (int it = 0;; ++it) {
+        const int c = warp + it * nw;
+        if (c >= total) break;
+        const int s = it % kStageDepth;
+        ok = __all_sync(kFull, mbar_wait_bounded(&st.bar[s], (phase >> s) & 1u, kStageWaitCycles));
+        if (!ok) break;
+        phase ^= 1u << s;
+        pending &= ~(1u << s);
+        int r, p0, len;
+        chunk(c, r, p0, len);
+        const double cr = -tb.colE[r];
+        const double2* src = st.ring + s * kStageChunkPairs;
+        double2* dst = reinterpret_cast<double2*>(tb.T + (size_t)r * LD) + p0;
+        for (int q = lane; q < len; q += 32) {
+            const double2 old = src[q];
+            const double2 p = P2[p0 + q];
+            const int j = 2 * (p0 + q);
+            double2 v;
+            v.x = __fma_rn(cr, p.x, (j == e) ? 0.0 : old.x);
+            v.y = __fma_rn(cr, p.y, (j + 1 == e) ? 0.0 : old.y);
+            dst[q] = v;
+        }
+        __syncwarp();
+        const int cn = c + kStageDepth * nw;
+        if (cn < total) {
+            if (lane == 0) {
+                fence_proxy_async_shared();  // the warp's reads of chunk s before the copy over it
+                issue(cn, s);
+            }
+            pending |= 1u << s;
+        }
+    }
+    if (!ok) {
+        // let the copies still in flight land before the rings are reused
+        bool drained = true;
+        for (int s = 0; s < kStageDepth; ++s)
+            if (pending & (1u << s)) {
+                drained = mbar_wait_bounded(&st.bar[s], (phase >> s) & 1u, kStageWaitCycles) && drained;
+                phase ^= 1u << s;
+            }
+        if (lane == 0) atomicMax(st.fail, drained ? 1 : 2);
+    }
+    return phase;
+}
 
 // Step 3 (Section 3.1, Listing 1) on the condensed tableau: divide pivot row
 // l by PE = colE[l], then t_ij <- fma(-t_ie, r_j, t_ij) for every other active
@@ -86,16 +211,19 @@ struct Tab {
 // 16-byte loads and stores -- the same FMA for every element, so the same
 // results; the pair beyond an odd Cact is padding (updated, never read).
 template <bool kPairs = false>
-__device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e) {
+__device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e, Staging* st = nullptr) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int LD = tb.LD;
     double* T = tb.T;
     const double* colE = tb.colE;
     const double pe = colE[l];
     double* Tl = T + (size_t)l * LD;
+    const bool staged = kPairs && st != nullptr && st->on;
     for (int j = tid; j < Cact; j += nt) {
         const double v = (j == e) ? 1.0 : Tl[j];
-        Tl[j] = __ddiv_rn(v, pe);
+        const double q = __ddiv_rn(v, pe);
+        Tl[j] = q;
+        if (staged) st->prow[j] = q;
     }
     if (tid == 0) {
         const int ev = tb.col_var[e];
@@ -104,6 +232,12 @@ __device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e) 
     }
     __syncthreads();
     const int left = tb.col_var[e];
+    if (staged) {
+        st->phase = staged_update(*st, tb, Ract, Cact, l, e);
+        fence_proxy_async_global();  // this thread's stores before later bulk reads of them
+        __syncthreads();
+        return left;
+    }
     if (kPairs) {
         const int Cp = (Cact + 1) >> 1;
         const int total = (Ract - 1) * Cp;
@@ -149,7 +283,8 @@ __device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e) 
 
 // A retired artificial (it just left the basis and may never re-enter) sits
 // in column e: move the last live column into its place and shrink.
-__device__ __forceinline__ void retire_column(Tab& tb, int Ract, int e, int& Cvar) {
+// `fence`: the tableau is read by bulk copies later (staged streamed update).
+__device__ __forceinline__ void retire_column(Tab& tb, int Ract, int e, int& Cvar, bool fence = false) {
     const int tid = threadIdx.x, nt = blockDim.x;
     if (e != Cvar) {
         for (int r = tid; r < Ract; r += nt) {
@@ -159,15 +294,19 @@ __device__ __forceinline__ void retire_column(Tab& tb, int Ract, int e, int& Cva
         if (tid == 0) tb.col_var[e] = tb.col_var[Cvar];
     }
     --Cvar;
+    if (fence) fence_proxy_async_global();
     __syncthreads();
 }
 
 // One LP, Steps 1-3 until it halts.  `small` is shared memory
 // (SmallLayout); `big` is shared memory (resident) or a global workspace slot
-// (streamed), laid out by big_layout.
+// (streamed), laid out by big_layout.  `stage` (streamed only, may be null):
+// `stage_bytes` of this CTA's shared memory for the staged update, used when
+// the LP's stage_layout fits.
 template <bool kStreamed>
 __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances& tol, const int lp,
-                                          unsigned char* small, unsigned char* big, int32_t* diag)
+                                          unsigned char* small, unsigned char* big, int32_t* diag,
+                                          unsigned char* stage = nullptr, size_t stage_bytes = 0)
 {
     const int m = B.m[lp];
     const int n = B.n[lp];
@@ -217,6 +356,31 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
     const int LD = L.LD;
     double* T = tb.T;  // the tableau is written through several pointers: no restrict
     int Cvar = n + k;  // live variable columns 1..Cvar
+    Staging stg{};
+    stg.on = false;
+    if (kStreamed && stage != nullptr) {
+        if (tid == 0) *reinterpret_cast<int*>(stage) = 0;  // the flag word (read after the barriers below)
+        const StageLayout S = stage_layout(nw, L.R, L.LD);
+        if (S.total <= stage_bytes) {
+            stg.on = true;
+            stg.fail = reinterpret_cast<int*>(stage + S.flag);
+            stg.bar = reinterpret_cast<uint64_t*>(stage + S.bars) + warp * kStageDepth;
+            stg.ring = reinterpret_cast<double2*>(stage + S.rings) + (size_t)warp * kStageDepth * kStageChunkPairs;
+            stg.prow = reinterpret_cast<double*>(stage + S.prow);
+            stg.phase = 0;
+            tb.colE = reinterpret_cast<double*>(stage + S.colE);  // the pivot column in shared memory
+            if (lane == 0) {
+                for (int q = 0; q < kStageDepth; ++q) mbar_init(&stg.bar[q], 1);
+                mbar_init_fence();
+            }
+        }
+    }
+    // the barriers are invalidated before their memory can serve another LP
+    // (unless a copy may still be in flight: the kernel then stops)
+    auto release_staging = [&]() {
+        if (stg.on && lane == 0 && *stg.fail != 2)
+            for (int q = 0; q < kStageDepth; ++q) mbar_inval(&stg.bar[q]);
+    };
 
     for (int j = tid; j <= Cvar; j += nt)
         tb.col_var[j] = (j == 0) ? -1 : (j <= n ? j - 1 : n + neg[j - 1 - n]);
@@ -281,6 +445,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         __syncthreads();
     }
 
+    if (stg.on) fence_proxy_async_global();  // the build's stores before bulk reads of them
     const long long key_neg_eps_opt = okey(-tol.eps_opt);
     const long long key_eps_piv = okey(tol.eps_piv);
     const int max_iters = tol.max_iters > 0 ? tol.max_iters : 50 * (m + n);
@@ -323,9 +488,10 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
                 const int e = (int)(sel & 0xffffu);
                 for (int r = tid; r < m + 1; r += nt) tb.colE[r] = T[(size_t)r * LD + e];
                 __syncthreads();
-                const int left = pivot<kStreamed>(tb, m + 1, Cvar + 1, i, e);
+                const int left = pivot<kStreamed>(tb, m + 1, Cvar + 1, i, e, &stg);
                 ++iters;
-                if (left >= nm) retire_column(tb, m + 1, e, Cvar);
+                if (stg.on && *stg.fail) { status = kNumerical; break; }
+                if (left >= nm) retire_column(tb, m + 1, e, Cvar, stg.on);
             }
             phase = 2;
             continue;
@@ -423,9 +589,14 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         if (iters >= max_iters) { status = kIterLimit; break; }
 
         // ---- Step 3: pivot ---------------------------------------------------
-        const int left = pivot<kStreamed>(tb, Ract, Cvar + 1, l, e);
+        const int left = pivot<kStreamed>(tb, Ract, Cvar + 1, l, e, &stg);
         ++iters;
-        if (left >= nm) retire_column(tb, Ract, e, Cvar);
+        if (stg.on && *stg.fail) {
+            if (tid == 0) record_internal_error(diag, 8, lp, iters);  // a bulk copy did not complete
+            status = kNumerical;
+            break;
+        }
+        if (left >= nm) retire_column(tb, Ract, e, Cvar, stg.on);
     }
 
     // ---- labels must name variables (self-check before they index global
@@ -442,6 +613,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
                 B.status[lp] = kNumerical;
                 B.iters[lp] = iters;
             }
+            release_staging();
             return;
         }
     }
@@ -466,6 +638,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         B.iters[lp] = iters;
         B.obj[lp] = T[(size_t)m * LD];
     }
+    release_staging();
 }
 
 __global__ void __launch_bounds__(kMaxThreads, 2)
@@ -503,13 +676,20 @@ fp64_resident_queue_kernel(const DeviceBatch B, const Tolerances tol, const int3
     }
 }
 
+// Dynamic shared memory of fp64_streamed_kernel: the staged update's rings and
+// copies (stage_layout), enough for R + LD up to ~1,900 doubles; larger LPs
+// take the plain loop.
+constexpr size_t kStreamStageBytes = 80 * 1024;
+
 __global__ void __launch_bounds__(kStreamedThreads, 2)
 fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order,
                      const int32_t count, const int32_t* __restrict__ count_dev, unsigned char* workspace,
-                     const size_t slot_bytes, int32_t* __restrict__ counter, int32_t* __restrict__ diag)
+                     const size_t slot_bytes, int32_t* __restrict__ counter, int32_t* __restrict__ diag,
+                     const size_t stage_bytes)
 {
     __shared__ __align__(16) unsigned char small[SmallLayout::total];
     __shared__ int next;
+    extern __shared__ __align__(128) unsigned char stage[];
     unsigned char* big = workspace + (size_t)blockIdx.x * slot_bytes;
     const int n_items = count_dev ? min(*count_dev, count) : count;
     for (;;) {
@@ -518,8 +698,10 @@ fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* _
         const int idx = next;
         __syncthreads();
         if (idx >= n_items) break;
-        solve_one<true>(B, tol, order[idx], small, big, diag);
+        solve_one<true>(B, tol, order[idx], small, big, diag, stage_bytes ? stage : nullptr, stage_bytes);
         __syncthreads();
+        // a bulk copy that may still be in flight into the rings: take no more LPs
+        if (stage_bytes && *reinterpret_cast<volatile int*>(stage) == 2) break;
     }
 }
 
@@ -531,7 +713,8 @@ fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* _
 __global__ void __launch_bounds__(kStreamedThreads, 2)
 fp64_single_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order,
                    const uint8_t* __restrict__ resident, const int32_t count, unsigned char* workspace,
-                   const size_t slot_bytes, int32_t* __restrict__ counter, int32_t* __restrict__ diag)
+                   const size_t slot_bytes, int32_t* __restrict__ counter, int32_t* __restrict__ diag,
+                   const size_t smem_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int next;
@@ -543,12 +726,17 @@ fp64_single_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __r
         __syncthreads();
         if (idx >= count) break;
         const int lp = order[idx];
-        if (resident[lp])
+        if (resident[lp]) {
             solve_one<false>(B, tol, lp, smem, smem + SmallLayout::total, diag);
-        else if (slot)
-            solve_one<true>(B, tol, lp, smem, slot, diag);
-        else if (threadIdx.x == 0)
+        } else if (slot) {
+            // the CTA's shared memory beyond the reduction scratch stages the update
+            unsigned char* stage = smem + SmallLayout::total;
+            solve_one<true>(B, tol, lp, smem, slot, diag, stage, smem_bytes - SmallLayout::total);
+            __syncthreads();
+            if (*reinterpret_cast<volatile int*>(stage) == 2) break;  // a copy may still be in flight
+        } else if (threadIdx.x == 0) {
             record_internal_error(diag, 7, lp);  // a plan without a slot for a streamed LP
+        }
         __syncthreads();
     }
 }
@@ -581,9 +769,16 @@ cudaError_t launch_fp64_resident_queue(const DeviceBatch& B, const Tolerances& t
     return cudaGetLastError();
 }
 
+cudaError_t fp64_streamed_prepare() {
+    return cudaFuncSetAttribute(fp64_streamed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kStreamStageBytes);
+}
+
 int fp64_streamed_ctas_per_sm() {
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fp64_streamed_kernel, kStreamedThreads, 0) != cudaSuccess)
+    if (fp64_streamed_prepare() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fp64_streamed_kernel, kStreamedThreads,
+                                                      kStreamStageBytes) != cudaSuccess)
         return 1;
     return blocks > 0 ? blocks : 1;
 }
@@ -594,8 +789,9 @@ cudaError_t launch_fp64_streamed(const DeviceBatch& B, const Tolerances& tol, co
     if (count <= 0) return cudaSuccess;
     cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
     if (err != cudaSuccess) return err;
-    fp64_streamed_kernel<<<slots, kStreamedThreads, 0, stream>>>(B, tol, order, count, count_dev, workspace,
-                                                                  slot_bytes, counter, diag);
+    if ((err = fp64_streamed_prepare()) != cudaSuccess) return err;
+    fp64_streamed_kernel<<<slots, kStreamedThreads, kStreamStageBytes, stream>>>(
+        B, tol, order, count, count_dev, workspace, slot_bytes, counter, diag, kStreamStageBytes);
     return cudaGetLastError();
 }
 
@@ -623,7 +819,7 @@ cudaError_t launch_fp64_single(const DeviceBatch& B, const Tolerances& tol, cons
     cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
     if (err != cudaSuccess) return err;
     fp64_single_kernel<<<ctas, kStreamedThreads, smem, stream>>>(B, tol, order, resident, count, workspace,
-                                                                  slot_bytes, counter, diag);
+                                                                  slot_bytes, counter, diag, smem);
     return cudaGetLastError();
 }
 

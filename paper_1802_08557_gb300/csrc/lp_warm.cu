@@ -111,6 +111,12 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
     for (int j = tid; j < n; j += nt) ck = max(ck, abskey(cv[j]));
     const double tol_p = a.cert_tol * __longlong_as_double(-red.min_i64(-bk));
     const double tol_d = a.cert_tol * __longlong_as_double(-red.min_i64(-ck));
+    // thresholds of the checks as order keys: the checks compare by integer
+    // operations (an FP64 compare takes the FP64 pipe, which bounds this
+    // kernel); a NaN never passes
+    const long long k_neg_tol_p = okey(-tol_p), k_tol_p = okey(tol_p), k_neg_tol_d = okey(-tol_d);
+    const long long k_eps_piv = okey(a.eps_piv), k_zero = 0;
+    const long long k_neg_eps_opt = okey(-a.eps_opt), k_huge = okey(1e300);
 
     // 1. predicted rows, ascending
     int k = 0;
@@ -132,7 +138,7 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
         ++round;
         // ---- 2. restricted tableau: rows R (slack basis), columns 1..n structurals
         unsigned negb = 0, dummy;
-        for (int r = tid; r < k; r += nt) negb += (bv[rows[r]] < 0.0) ? 1u : 0u;
+        for (int r = tid; r < k; r += nt) negb += below_key(bv[rows[r]], k_zero) ? 1u : 0u;
         red.count_min(negb, 0u, negb, dummy);
         if (negb) { ok = false; break; }
         for (int j = tid; j <= n; j += nt) col_var[j] = j - 1;  // column j holds structural j-1 (0: RHS)
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
             long long loc = LLONG_MAX;
             for (int j = 1 + tid; j <= n; j += nt) loc = min(loc, okey(To[j]));
             const long long dmin = red.min_i64(loc);
-            if (!(kval(dmin) < -a.eps_opt)) { status = 0; break; }
+            if (!(dmin < k_neg_eps_opt)) { status = 0; break; }
             unsigned esel = 0xFFFFFFFFu;
             for (int j = 1 + tid; j <= n; j += nt)
                 if (okey(To[j]) == dmin) esel = min(esel, ((unsigned)col_var[j] << 16) | (unsigned)j);
@@ -169,22 +175,66 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
             const int e = (int)(esel & 0xFFFFu);
             if (e < 1 || e > n) { status = 4; break; }
             // Step 2: minimum ratio over rows with t_re > eps_piv; exact ties to
-            // the lowest row (each ratio divided once, its key kept for the tie pass)
-            long long rl = LLONG_MAX;
+            // the lowest row.  FP32 screen first (operands truncated to FP32
+            // by integer operations, rows with an operand outside [2^-100,
+            // 2^100] always candidates, window 2^-12 relative + 2^-20
+            // absolute: far wider than the screen's error); exact FP64
+            // ratios only when more than one row survives.  The row is the
+            // plain rule's in every case; the FP64 divides it saves are most
+            // of this kernel's FP64-pipe time besides the update.
+            int floc = INT_MAX;
             for (int r = tid; r <= k; r += nt) {
                 const double t = T[(size_t)r * LD + e];
                 colE[r] = t;
-                const long long key = (r < k && t > a.eps_piv) ? okey(__ddiv_rn(T[(size_t)r * LD], t)) : LLONG_MAX;
-                rkey[r] = key;
-                rl = min(rl, key);
+                long long code = LLONG_MAX;  // not eligible
+                if (r < k && above_key(t, k_eps_piv)) {
+                    const double beta = T[(size_t)r * LD];
+                    const int et = dexp(t), eb = dexp(beta);
+                    if (et >= -100 && et <= 100 && (abskey(beta) == 0 || (eb >= -100 && eb <= 100))) {
+                        const int fk = fkey(__fdividef(f64_to_f32_trunc(beta), f64_to_f32_trunc(t)));
+                        code = fk;
+                        floc = min(floc, fk);
+                    } else {
+                        code = LLONG_MIN;  // unscreened: always a candidate
+                    }
+                }
+                rkey[r] = code;
             }
-            const long long rmin = red.min_i64(rl);
-            if (rmin == LLONG_MAX) { status = 2; e_unb = e; break; }
-            unsigned lsel = 0xFFFFFFFFu;
-            for (int r = tid; r < k; r += nt)
-                if (rkey[r] == rmin) lsel = min(lsel, (unsigned)r);
-            const int l = (int)red.min_u32(lsel);
-            if (l < 0 || l >= k || !(fabs(colE[l]) < 1e300)) { status = 4; break; }
+            const int fmin = red.min_i32(floc);  // barrier: rkey, colE complete
+            long long fwin = LLONG_MIN;
+            if (fmin != INT_MAX) {
+                const float fm = fval(fmin);
+                fwin = fkey(fm + __fmaf_rn(0x1p-12f, fabsf(fm), 0x1p-20f));
+            }
+            unsigned lcnt = 0, lsel = 0xFFFFFFFFu;
+            for (int r = tid; r < k; r += nt) {
+                const long long code = rkey[r];
+                if (code == LLONG_MIN || (code != LLONG_MAX && code <= fwin)) {
+                    ++lcnt;
+                    lsel = min(lsel, (unsigned)r);
+                }
+            }
+            red.count_min(lcnt, lsel, lcnt, lsel);
+            if (lcnt == 0) { status = 2; e_unb = e; break; }
+            if (lcnt > 1) {
+                // several candidates: their exact ratios, the exact rule
+                long long rl = LLONG_MAX;
+                for (int r = tid; r < k; r += nt) {
+                    const long long code = rkey[r];
+                    long long rk = LLONG_MAX;
+                    if (code == LLONG_MIN || (code != LLONG_MAX && code <= fwin))
+                        rk = okey(__ddiv_rn(T[(size_t)r * LD], colE[r]));
+                    rkey[r] = rk;
+                    rl = min(rl, rk);
+                }
+                const long long rmin = red.min_i64(rl);
+                unsigned sel = 0xFFFFFFFFu;
+                for (int r = tid; r < k; r += nt)
+                    if (rkey[r] == rmin) sel = min(sel, (unsigned)r);
+                lsel = red.min_u32(sel);
+            }
+            const int l = (int)lsel;
+            if (l < 0 || l >= k || abskey(colE[l]) >= k_huge) { status = 4; break; }
             if (iters >= a.max_iters) { status = 3; break; }
             // Step 3: pivot row times one reciprocal (the restricted LP only
             // proposes the rows; its optimum is checked on the full LP below),
@@ -246,7 +296,7 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
                     const int v = row_var[r];
                     if ((unsigned)v < (unsigned)n) s = __fma_rn(-A[(size_t)i * n + v], T[(size_t)r * LD + e_unb], s);
                 }
-                const bool bound = s > tol_p;
+                const bool bound = above_key(s, k_tol_p);
                 inR[i] = bound ? 2 : 0;  // 2: to be added
                 add += bound ? 1u : 0u;
             }
@@ -261,7 +311,7 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
                     const int v = row_var[r];
                     if ((unsigned)v < (unsigned)n) s = __fma_rn(-A[(size_t)i * n + v], xv[v], s);
                 }
-                const bool viol = s < -tol_p;
+                const bool viol = below_key(s, k_neg_tol_p);
                 if (!inR[i]) {
                     inR[i] = viol ? 2 : 0;
                     add += viol ? 1u : 0u;
@@ -269,11 +319,11 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
                     bad += viol ? 1u : 0u;  // a restricted row must hold already
                 }
             }
-            for (int r = tid; r < k; r += nt) bad += (yv[r] < -tol_d) ? 1u : 0u;
+            for (int r = tid; r < k; r += nt) bad += below_key(yv[r], k_neg_tol_d) ? 1u : 0u;
             for (int j = tid; j < n; j += nt) {
                 double d = -cv[j];
                 for (int r = 0; r < k; ++r) d = __fma_rn(A[(size_t)rows[r] * n + j], yv[r], d);
-                bad += (d < -tol_d) ? 1u : 0u;
+                bad += below_key(d, k_neg_tol_d) ? 1u : 0u;
             }
             unsigned tot_add;
             red.count_min(add, 0u, tot_add, first);

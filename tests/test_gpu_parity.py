@@ -268,6 +268,26 @@ def test_large_lps_take_the_cluster_or_streamed_path(schedule):
     assert bitwise == n
 
 
+def test_streamed_tableaux_beyond_the_staging_buffer():
+    """The streamed kernel stages its update through shared memory when the
+    LP's pivot row and column fit beside the rings (R + LD up to ~1,900
+    doubles), else it runs the plain loop: an LP on each side of that limit
+    (one with phase I and a retired artificial column), and tall and wide
+    shapes whose chunks end mid-row, against the oracle bit for bit."""
+    rng = np.random.default_rng(21)
+    lps = []
+    A = rng.uniform(0, 1, (400, 1700)); lps.append((A, rng.uniform(1, 100, 400), rng.uniform(0, 1, 1700)))  # plain
+    A = rng.uniform(0, 1, (300, 1300)); b = rng.uniform(1, 100, 300); b[::37] *= -0.01
+    lps.append((A, b, rng.uniform(0, 1, 1300)))                                     # staged, phase I
+    A = rng.uniform(0, 1, (900, 130)); lps.append((A, rng.uniform(1, 100, 900), rng.uniform(0, 1, 130)))
+    A = rng.uniform(0, 1, (140, 257)); lps.append((A, rng.uniform(1, 100, 140), rng.uniform(0, 1, 257)))
+    batch = W.pack("staging", lps)
+    g, r, n, bitwise = _check(batch, opts=lpb.lpb_default_opts(schedule=lpb.LPB_SCHED_STREAMED))
+    assert g["plan"]["num_streamed"] == batch.num_lps
+    assert bitwise == n
+    assert int(g["status"][0]) == 0 and int(g["iters"][0]) > 0
+
+
 def test_cluster_kernel_matches_streamed_bitwise():
     """Mixed-sign 260 x 260 LPs (phase I, infeasible and unbounded ones among
     them) on thread-block clusters and in the global workspace: identical."""
