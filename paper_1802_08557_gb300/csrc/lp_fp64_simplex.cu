@@ -73,8 +73,8 @@ __device__ __forceinline__ unsigned long long step1_window(long long kmin, long 
 // chunk) that one lane issues kStageDepth chunks ahead; the pivot row and the
 // pivot column are read from shared-memory copies.  The FMA of every element
 // is the one of the plain loop, so the results are the same bit for bit.
-constexpr int kStageChunkPairs = 128;  // 2 KB per chunk: 4 pairs per lane
-constexpr int kStageDepth = 2;
+constexpr int kStageChunkPairs = 96;  // 1.5 KB per chunk: 3 pairs per lane
+constexpr int kStageDepth = 3;
 constexpr long long kStageWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
 // A CTA's shared memory for the staged update: a flag word, the mbarriers and
@@ -677,9 +677,9 @@ fp64_resident_queue_kernel(const DeviceBatch B, const Tolerances tol, const int3
 }
 
 // Dynamic shared memory of fp64_streamed_kernel: the staged update's rings and
-// copies (stage_layout), enough for R + LD up to ~1,900 doubles; larger LPs
+// copies (stage_layout), enough for R + LD up to ~2,000 doubles; larger LPs
 // take the plain loop.
-constexpr size_t kStreamStageBytes = 80 * 1024;
+constexpr size_t kStreamStageBytes = 88 * 1024;
 
 __global__ void __launch_bounds__(kStreamedThreads, 2)
 fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order,

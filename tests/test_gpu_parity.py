@@ -270,7 +270,7 @@ def test_large_lps_take_the_cluster_or_streamed_path(schedule):
 
 def test_streamed_tableaux_beyond_the_staging_buffer():
     """The streamed kernel stages its update through shared memory when the
-    LP's pivot row and column fit beside the rings (R + LD up to ~1,900
+    LP's pivot row and column fit beside the rings (R + LD up to ~2,000
     doubles), else it runs the plain loop: an LP on each side of that limit
     (one with phase I and a retired artificial column), and tall and wide
     shapes whose chunks end mid-row, against the oracle bit for bit."""
