@@ -78,33 +78,31 @@ constexpr int kStageDepth = 3;
 constexpr long long kStageWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
 // A CTA's shared memory for the staged update: a flag word, the mbarriers and
-// rings of every warp, then the pivot-column copy (R doubles) and the
-// pivot-row copy (LD doubles) of the LP being solved.
-struct StageLayout {
-    size_t flag, bars, rings, colE, prow, total;
-};
-__host__ __device__ inline StageLayout stage_layout(int nwarps, int R, int LD) {
-    StageLayout S;
-    size_t o = 0;
-    S.flag = o;  o += 16;
-    S.bars = o;  o += (size_t)nwarps * kStageDepth * 8;
-    o = (o + 127) & ~size_t(127);
-    S.rings = o; o += (size_t)nwarps * kStageDepth * kStageChunkPairs * 16;
-    S.colE = o;  o += align16((size_t)R * 8);
-    S.prow = o;  o += align16((size_t)LD * 8);
-    S.total = o;
-    return S;
+// rings of every warp, the pivot-row copy (LD doubles), then the pivot-column
+// copy (R doubles) of the LP being solved.  Everything but the column copy
+// sits at offsets that depend only on the number of warps.
+__host__ __device__ inline size_t stage_rings(int nwarps) {
+    return (16 + (size_t)nwarps * kStageDepth * 8 + 127) & ~size_t(127);
+}
+__host__ __device__ inline size_t stage_prow(int nwarps) {
+    return stage_rings(nwarps) + (size_t)nwarps * kStageDepth * kStageChunkPairs * 16;
+}
+__host__ __device__ inline size_t stage_colE(int nwarps, int LD) { return stage_prow(nwarps) + align16((size_t)LD * 8); }
+__host__ __device__ inline size_t stage_total(int nwarps, int R, int LD) {
+    return stage_colE(nwarps, LD) + align16((size_t)R * 8);
 }
 
-// The staged path of one LP (on = false: the plain loop).
+// The staged path of one LP: `base` of the staging area (null: the plain
+// loop) and the parities of the warp's chunk mbarriers (bit s: parity of the
+// next completion of chunk s, warp-uniform).  The flag word at `base`: 1 a
+// copy did not complete (LP abandoned); 2 one may still be in flight.
 struct Staging {
-    bool on;
-    uint64_t* bar;      // this warp's kStageDepth mbarriers
-    double2* ring;      // this warp's kStageDepth chunks
-    double* prow;       // copy of the scaled pivot row
-    unsigned phase;     // bit s: parity of the next completion of chunk s (warp-uniform)
-    int* fail;          // shared: 1 a copy did not complete (LP abandoned); 2 one may still be in flight
+    unsigned char* base;
+    unsigned phase;
 };
+__device__ __forceinline__ uint64_t* stage_bars(unsigned char* base) {
+    return reinterpret_cast<uint64_t*>(base + 16) + (threadIdx.x >> 5) * kStageDepth;
+}
 
 struct Tab {
     double* T;        // R x LD, row-major; column 0 = right-hand side
@@ -117,19 +115,21 @@ struct Tab {
 // Phase B of Step 3 for a tableau in global memory, through the staging
 // rings: chunk c covers row ii = c / cpr (skipping the pivot row l) and pairs
 // [p0, p0 + len) of it; warp w takes chunks w, w + nw, ...  The pivot row is
-// read from st.prow, column e from tb.colE (shared memory on this path).
+// read from the staging area's copy, column e from tb.colE (shared memory on this path).
 // The pair beyond an odd Cact is padding (updated, never read).  A copy that
-// does not complete within kStageWaitCycles abandons the update: *st.fail is
-// set (the caller reports the LP as numerical) after the warp has waited,
+// does not complete within kStageWaitCycles abandons the update: the flag
+// word is set (the caller reports the LP as numerical) after the warp has waited,
 // bounded again, for its other copies.
 __device__ __noinline__ unsigned staged_update(const Staging st, const Tab tb, int Ract, int Cact, int l, int e) {
     unsigned phase = st.phase;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int LD = tb.LD;
+    uint64_t* bar = stage_bars(st.base);
+    double2* ring = reinterpret_cast<double2*>(st.base + stage_rings(nw)) + (size_t)warp * kStageDepth * kStageChunkPairs;
     const int Cp = (Cact + 1) >> 1;
     const int cpr = (Cp + kStageChunkPairs - 1) / kStageChunkPairs;
     const int total = (Ract - 1) * cpr;
-    const double2* P2 = reinterpret_cast<const double2*>(st.prow);
+    const double2* P2 = reinterpret_cast<const double2*>(st.base + stage_prow(nw));
     auto chunk = [&](int c, int& r, int& p0, int& len) {
         const int ii = c / cpr;
         const int piece = c - ii * cpr;
@@ -141,8 +141,8 @@ __device__ __noinline__ unsigned staged_update(const Staging st, const Tab tb, i
         int r, p0, len;
         chunk(c, r, p0, len);
         const unsigned bytes = (unsigned)len * 16u;
-        mbar_expect_tx(&st.bar[s], bytes);
-        bulk_load(st.ring + s * kStageChunkPairs, tb.T + (size_t)r * LD + 2 * p0, bytes, &st.bar[s]);
+        mbar_expect_tx(&bar[s], bytes);
+        bulk_load(ring + s * kStageChunkPairs, tb.T + (size_t)r * LD + 2 * p0, bytes, &bar[s]);
     };
     unsigned pending = 0;  // chunks issued and not yet waited for (warp-uniform)
     for (int s = 0; s < kStageDepth; ++s) {
@@ -157,14 +157,14 @@ __device__ __noinline__ unsigned staged_update(const Staging st, const Tab tb, i
         const int c = warp + it * nw;
         if (c >= total) break;
         const int s = it % kStageDepth;
-        ok = __all_sync(kFull, mbar_wait_bounded(&st.bar[s], (phase >> s) & 1u, kStageWaitCycles));
+        ok = __all_sync(kFull, mbar_wait_bounded(&bar[s], (phase >> s) & 1u, kStageWaitCycles));
         if (!ok) break;
         phase ^= 1u << s;
         pending &= ~(1u << s);
         int r, p0, len;
         chunk(c, r, p0, len);
         const double cr = -tb.colE[r];
-        const double2* src = st.ring + s * kStageChunkPairs;
+        const double2* src = ring + s * kStageChunkPairs;
         double2* dst = reinterpret_cast<double2*>(tb.T + (size_t)r * LD) + p0;
         for (int q = lane; q < len; q += 32) {
             const double2 old = src[q];
@@ -190,10 +190,10 @@ __device__ __noinline__ unsigned staged_update(const Staging st, const Tab tb, i
         bool drained = true;
         for (int s = 0; s < kStageDepth; ++s)
             if (pending & (1u << s)) {
-                drained = mbar_wait_bounded(&st.bar[s], (phase >> s) & 1u, kStageWaitCycles) && drained;
+                drained = mbar_wait_bounded(&bar[s], (phase >> s) & 1u, kStageWaitCycles) && drained;
                 phase ^= 1u << s;
             }
-        if (lane == 0) atomicMax(st.fail, drained ? 1 : 2);
+        if (lane == 0) atomicMax(reinterpret_cast<int*>(st.base), drained ? 1 : 2);
     }
     return phase;
 }
@@ -218,12 +218,13 @@ __device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e, 
     const double* colE = tb.colE;
     const double pe = colE[l];
     double* Tl = T + (size_t)l * LD;
-    const bool staged = kPairs && st != nullptr && st->on;
+    const bool staged = kPairs && st != nullptr && st->base != nullptr;
+    double* prow = staged ? reinterpret_cast<double*>(st->base + stage_prow(nt >> 5)) : nullptr;
     for (int j = tid; j < Cact; j += nt) {
         const double v = (j == e) ? 1.0 : Tl[j];
         const double q = __ddiv_rn(v, pe);
         Tl[j] = q;
-        if (staged) st->prow[j] = q;
+        if (staged) prow[j] = q;
     }
     if (tid == 0) {
         const int ev = tb.col_var[e];
@@ -302,7 +303,7 @@ __device__ __forceinline__ void retire_column(Tab& tb, int Ract, int e, int& Cva
 // (SmallLayout); `big` is shared memory (resident) or a global workspace slot
 // (streamed), laid out by big_layout.  `stage` (streamed only, may be null):
 // `stage_bytes` of this CTA's shared memory for the staged update, used when
-// the LP's stage_layout fits.
+// the LP's stage_total fits.
 template <bool kStreamed>
 __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances& tol, const int lp,
                                           unsigned char* small, unsigned char* big, int32_t* diag,
@@ -356,30 +357,24 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
     const int LD = L.LD;
     double* T = tb.T;  // the tableau is written through several pointers: no restrict
     int Cvar = n + k;  // live variable columns 1..Cvar
-    Staging stg{};
-    stg.on = false;
+    Staging stg{nullptr, 0u};
     if (kStreamed && stage != nullptr) {
         if (tid == 0) *reinterpret_cast<int*>(stage) = 0;  // the flag word (read after the barriers below)
-        const StageLayout S = stage_layout(nw, L.R, L.LD);
-        if (S.total <= stage_bytes) {
-            stg.on = true;
-            stg.fail = reinterpret_cast<int*>(stage + S.flag);
-            stg.bar = reinterpret_cast<uint64_t*>(stage + S.bars) + warp * kStageDepth;
-            stg.ring = reinterpret_cast<double2*>(stage + S.rings) + (size_t)warp * kStageDepth * kStageChunkPairs;
-            stg.prow = reinterpret_cast<double*>(stage + S.prow);
-            stg.phase = 0;
-            tb.colE = reinterpret_cast<double*>(stage + S.colE);  // the pivot column in shared memory
+        if (stage_total(nw, L.R, L.LD) <= stage_bytes) {
+            stg.base = stage;
+            tb.colE = reinterpret_cast<double*>(stage + stage_colE(nw, L.LD));  // pivot column in shared memory
             if (lane == 0) {
-                for (int q = 0; q < kStageDepth; ++q) mbar_init(&stg.bar[q], 1);
+                for (int q = 0; q < kStageDepth; ++q) mbar_init(&stage_bars(stage)[q], 1);
                 mbar_init_fence();
             }
         }
     }
+    const bool staged = kStreamed && stg.base != nullptr;
     // the barriers are invalidated before their memory can serve another LP
     // (unless a copy may still be in flight: the kernel then stops)
     auto release_staging = [&]() {
-        if (stg.on && lane == 0 && *stg.fail != 2)
-            for (int q = 0; q < kStageDepth; ++q) mbar_inval(&stg.bar[q]);
+        if (staged && lane == 0 && *reinterpret_cast<volatile int*>(stage) != 2)
+            for (int q = 0; q < kStageDepth; ++q) mbar_inval(&stage_bars(stage)[q]);
     };
 
     for (int j = tid; j <= Cvar; j += nt)
@@ -445,7 +440,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         __syncthreads();
     }
 
-    if (stg.on) fence_proxy_async_global();  // the build's stores before bulk reads of them
+    if (staged) fence_proxy_async_global();  // the build's stores before bulk reads of them
     const long long key_neg_eps_opt = okey(-tol.eps_opt);
     const long long key_eps_piv = okey(tol.eps_piv);
     const int max_iters = tol.max_iters > 0 ? tol.max_iters : 50 * (m + n);
@@ -490,8 +485,8 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
                 __syncthreads();
                 const int left = pivot<kStreamed>(tb, m + 1, Cvar + 1, i, e, &stg);
                 ++iters;
-                if (stg.on && *stg.fail) { status = kNumerical; break; }
-                if (left >= nm) retire_column(tb, m + 1, e, Cvar, stg.on);
+                if (staged && *reinterpret_cast<volatile int*>(stage)) { status = kNumerical; break; }
+                if (left >= nm) retire_column(tb, m + 1, e, Cvar, staged);
             }
             phase = 2;
             continue;
@@ -591,12 +586,12 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         // ---- Step 3: pivot ---------------------------------------------------
         const int left = pivot<kStreamed>(tb, Ract, Cvar + 1, l, e, &stg);
         ++iters;
-        if (stg.on && *stg.fail) {
+        if (staged && *reinterpret_cast<volatile int*>(stage)) {
             if (tid == 0) record_internal_error(diag, 8, lp, iters);  // a bulk copy did not complete
             status = kNumerical;
             break;
         }
-        if (left >= nm) retire_column(tb, Ract, e, Cvar, stg.on);
+        if (left >= nm) retire_column(tb, Ract, e, Cvar, staged);
     }
 
     // ---- labels must name variables (self-check before they index global
@@ -677,7 +672,7 @@ fp64_resident_queue_kernel(const DeviceBatch B, const Tolerances tol, const int3
 }
 
 // Dynamic shared memory of fp64_streamed_kernel: the staged update's rings and
-// copies (stage_layout), enough for R + LD up to ~2,000 doubles; larger LPs
+// copies (stage_total), enough for R + LD up to ~2,000 doubles; larger LPs
 // take the plain loop.
 constexpr size_t kStreamStageBytes = 88 * 1024;
 
