@@ -54,9 +54,9 @@ HBM_PEAK_GBS, BF16_PEAK_TFLOPS, PEAKS_SOURCE = _measured_peaks()
 # DRAM bytes per LP (read + write) from ncu captures of the kernels as they are
 # now, for the roofline's `traffic` (scaled to a launch by the LPs it solves):
 # profiles/mixed_warp_kernel__dense50x50_20k__ncu.md (k = 0 group, 15629 LPs:
-# 349.4 MB + 12.4 MB) and profiles/hyperbox_tile_kernel__dirs1M_dim28__ncu.md
+# 350.7 MB + 12.6 MB) and profiles/hyperbox_tile_kernel__dirs1M_dim28__ncu.md
 # (2^20 LPs in R^28: 234.9 MB + 7.6 MB).
-MIXED_DRAM_BYTES_PER_LP = (349.375232e6 + 12.406528e6) / 15629
+MIXED_DRAM_BYTES_PER_LP = (350.654208e6 + 12.641024e6) / 15629
 HYPERBOX_DRAM_BYTES_PER_LP_DIM28 = (234.9e6 + 7.6e6) / (1 << 20)
 L2_BYTES = 129 * 1024 * 1024
 
