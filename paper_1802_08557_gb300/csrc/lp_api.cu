@@ -757,7 +757,11 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
             (err = cudaMemcpyAsync(h->d_resident, single_resident.data(), (size_t)num_lps, cudaMemcpyHostToDevice, s)))
             return bail_cuda(err, "plan upload");
         int sms = 0;
-        h->single_smem = (std::max(h->single_smem, lpb::SmallLayout::total) + 1023) / 1024 * 1024;
+        h->single_smem = std::max(h->single_smem, lpb::SmallLayout::total);
+        // streamed LPs stage their update in the CTA's shared memory beyond the reduction scratch
+        if (h->num_single_streamed > 0)
+            h->single_smem = std::max(h->single_smem, lpb::SmallLayout::total + lpb::kStreamStageBytes);
+        h->single_smem = (h->single_smem + 1023) / 1024 * 1024;
         if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device)) ||
             (err = lpb::fp64_single_prepare(h->single_smem)))
             return bail_cuda(err, "single launch set-up");

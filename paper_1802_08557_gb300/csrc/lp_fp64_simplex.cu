@@ -671,10 +671,6 @@ fp64_resident_queue_kernel(const DeviceBatch B, const Tolerances tol, const int3
     }
 }
 
-// Dynamic shared memory of fp64_streamed_kernel: the staged update's rings and
-// copies (stage_total), enough for R + LD up to ~2,000 doubles; larger LPs
-// take the plain loop.
-constexpr size_t kStreamStageBytes = 88 * 1024;
 
 __global__ void __launch_bounds__(kStreamedThreads, 2)
 fp64_streamed_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order,

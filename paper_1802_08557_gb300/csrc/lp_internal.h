@@ -182,6 +182,12 @@ cudaError_t launch_mixed(const DeviceBatch& B, const Tolerances& tol, const Mixe
 
 // Launchers (lp_fp64_simplex.cu).
 constexpr int kStreamedThreads = 512;
+// Shared memory of a streamed FP64 LP's staged rank-1 update (the rings of
+// bulk-copied tableau chunks and the pivot row and column copies): the
+// streamed kernel's dynamic shared memory, and the least the single-launch
+// kernel gets when its batch has streamed LPs.  Enough for R + LD up to
+// ~2,000 doubles; larger LPs take the plain update loop.
+constexpr size_t kStreamStageBytes = 88 * 1024;
 cudaError_t fp64_kernels_prepare();
 // diag: 8 int32 internal-consistency record (see record_internal_error), or null.
 cudaError_t launch_fp64_resident(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,

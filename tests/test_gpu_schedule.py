@@ -101,6 +101,17 @@ def test_lpt_order_and_errors():
         s.close()
 
 
+def gpu_solve_opts(batch, opts):
+    s = lpb.BatchSolver(batch, opts=opts)
+    try:
+        s.solve()
+        r = s.results()
+        assert s.plan_info()["internal_errors"] == 0
+        return r
+    finally:
+        s.close()
+
+
 def test_single_launch_schedule_gives_identical_results():
     """LPB_SCHED_SINGLE: the whole uneven batch in one persistent launch (one
     work queue, longest work first; tableaux up to 110 KB in shared memory,
@@ -135,6 +146,12 @@ def test_single_launch_schedule_gives_identical_results():
         _same(s.results(), want)
     finally:
         s.close()
+    # a batch of streamed LPs only: the single launch still gets the shared
+    # memory to stage their update, and matches the streamed kernel bit for bit
+    big = W.pack("single_big", lps[300:303])
+    a = gpu_solve_opts(big, lpb.lpb_default_opts(schedule=lpb.LPB_SCHED_STREAMED))
+    b = gpu_solve_opts(big, lpb.lpb_default_opts(schedule=lpb.LPB_SCHED_SINGLE))
+    _same(b, a)
     with pytest.raises(lpb.LPBError):  # mixed precision has no single-launch form
         lpb.BatchSolver(batch, opts=lpb.lpb_default_opts(precision=lpb.LP_PREC_FP32_REFINE,
                                                          schedule=lpb.LPB_SCHED_SINGLE))
