@@ -3,7 +3,7 @@
 // K-major), FP32 accumulation in tensor memory, the fused epilogues of
 // lp_mlp_gemm.cuh.  No counterpart in the paper.
 //
-// Persistent CTAs of 6 warps, one per SM, each taking 128 x 128 output tiles
+// Persistent CTAs of 10 warps, one per SM, each taking 128 x 128 output tiles
 // tile = blockIdx.x, blockIdx.x + gridDim.x, ... (columns of a row of tiles
 // consecutive, so neighbouring CTAs share A's rows in L2):
 //  - warp 0, one lane: TMA producer.  Tiles of 128 rows x 64 K-elements of A
@@ -15,10 +15,13 @@
 //    stage into one of two 128-column FP32 accumulators in tensor memory
 //    (tile i uses accumulator i % 2), a tcgen05.commit per stage to free it
 //    and one per tile to hand the accumulator to the epilogue.
-//  - warps 2..5: epilogue.  Warp w reads accumulator lanes 32(w%4) .. +31
-//    (its rows) with tcgen05.ld, releases the accumulator to the MMA warp, and
-//    applies the epilogue with 16-byte stores -- while the MMAs of the next
-//    tile run in the other accumulator.
+//  - warps 2..9: epilogue.  Warp w reads accumulator lanes 32(w%4) .. +31
+//    (its rows; a warp may only reach its own quarter of the lanes) and
+//    columns 64((w-2)/4) .. +63 with tcgen05.ld, releases the accumulator to
+//    the MMA warp, and applies the epilogue with 16-byte stores -- while the
+//    MMAs of the next tile run in the other accumulator.  Two warps per lane
+//    quarter halve each warp's share of a tile: the epilogue, not the tensor
+//    pipe, sets the pace of these K <= 512 products.
 // Rows and columns past M, N and K are zero-filled by the TMA unit and not
 // stored.  Every wait is bounded (about two seconds of clock) and also ends
 // when another role of the CTA has given up: the CTA then counts a fault,
@@ -43,16 +46,19 @@
 namespace lpb {
 namespace {
 
-constexpr int kTcM = 128, kTcN = 128, kTcK = 64, kTcStages = 5, kTcThreads = 192;
+constexpr int kTcM = 128, kTcN = 128, kTcK = 64, kTcStages = 4;
+constexpr int kTcEpiWarps = 8, kTcThreads = 64 + 32 * kTcEpiWarps;
+constexpr int kTcEpiCols = kTcN / 2;  // columns of a tile per epilogue warp
 constexpr uint32_t kTileBytes = kTcM * kTcK * 2;  // 16 KB per operand tile (also for B: kTcN == kTcM)
-// per epilogue warp: 32 rows of up to 256 bytes (128 BF16 or 64 FP32 values),
-// padded to 272 bytes so that a lane's 32-byte row piece and a row's 16-byte
-// chunks fall on distinct banks; then the tile's 128 bias values
+// per epilogue warp: 32 rows of up to 256 bytes (its 64 columns as FP32, or
+// as BF16 in the first 128), padded to 272 bytes so that a lane's row piece
+// and a row's 16-byte chunks fall on distinct banks; then its 64 bias values
 constexpr uint32_t kStageRow = 272, kStageWarp = 32 * kStageRow;
-constexpr size_t kTcSmem = 1024 /* alignment slack */ + 2 * kTcStages * (size_t)kTileBytes + 4 * kStageWarp +
-                           4 * 128 * 4 + 256;
+constexpr size_t kTcSmem = 1024 /* alignment slack */ + 2 * kTcStages * (size_t)kTileBytes +
+                           kTcEpiWarps * kStageWarp + kTcEpiWarps * kTcEpiCols * 4 + 256;
+static_assert(kTcSmem <= 227 * 1024, "shared memory of the tcgen05 product");
 constexpr long long kTcWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
-constexpr int kTcChunks = kTcN / 16;
+constexpr int kTcChunks = kTcEpiCols / 16;  // 16-column chunks per epilogue warp
 
 __device__ int g_tc_faults;  // CTAs that gave up on a wait (read by lp_mlp_tc_faults)
 
@@ -132,9 +138,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // 128-byte swizzle atoms need 1024-byte alignment
     const uint32_t a_tiles = base, b_tiles = base + kTcStages * kTileBytes;
-    const uint32_t stage_out = base + 2 * kTcStages * kTileBytes;  // epilogue staging, 4 x kStageWarp
-    const uint32_t bias_s = stage_out + 4 * kStageWarp;            // 4 x 128 floats (one slot per warp)
-    const uint32_t bars = bias_s + 4 * 128 * 4;
+    const uint32_t stage_out = base + 2 * kTcStages * kTileBytes;     // epilogue staging, one area per warp
+    const uint32_t bias_s = stage_out + kTcEpiWarps * kStageWarp;     // kTcEpiCols floats per epilogue warp
+    const uint32_t bars = bias_s + kTcEpiWarps * kTcEpiCols * 4;
     // barriers: full[S], empty[S], acc_full[2], acc_empty[2], mma_done
     auto full = [&](int s) { return bars + 8u * s; };
     auto empty = [&](int s) { return bars + 8u * (kTcStages + s); };
@@ -156,7 +162,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full(b), 1);
-            mbar_init(acc_empty(b), 4);  // one arrival per epilogue warp
+            mbar_init(acc_empty(b), kTcEpiWarps);  // one arrival per epilogue warp
         }
         mbar_init(mma_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -232,10 +238,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
         __syncwarp();
     } else {
-        // epilogue: warp w owns accumulator lanes (rows) 32*(w%4) .. +31
-        const int q = warp & 3;
-        uint8_t* my_stage = smem_raw + (stage_out - raw) + (size_t)q * kStageWarp;
-        float* my_bias = reinterpret_cast<float*>(smem_raw + (bias_s - raw)) + q * 128;
+        // epilogue: warp w owns accumulator lanes (rows) 32*(w%4) .. +31 and
+        // columns cb .. cb + 63 of the tile
+        const int q = warp & 3, ew = warp - 2;
+        const int cb = (ew >> 2) * kTcEpiCols;
+        uint8_t* my_stage = smem_raw + (stage_out - raw) + (size_t)ew * kStageWarp;
+        float* my_bias = reinterpret_cast<float*>(smem_raw + (bias_s - raw)) + ew * kTcEpiCols;
         // the fast path: BF16 rows (and FP32 rows of C) through the warp's
         // staging area, written out as whole contiguous rows; 16-byte aligned
         // rows needed (ldc a multiple of 4, ldh of 8, aligned bases)
@@ -252,7 +260,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             if (ok) {
 #pragma unroll
                 for (int c = 0; c < kTcChunks; ++c)
-                    tmem_ld16(tmem + (uint32_t)(b * kTcN) + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 16), v[c]);
+                    tmem_ld16(tmem + (uint32_t)(b * kTcN) + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb + c * 16), v[c]);
                 tmem_wait();
 #pragma unroll
                 for (int c = 0; c < kTcChunks; ++c)
@@ -266,8 +274,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const int row0 = m0 + q * 32, row = row0 + lane;
             const bool full_tile = vec && n0 + kTcN <= g.N && row0 + 32 <= g.M;
             if (full_tile && (kEpi == kEpiBias || kEpi == kEpiBiasReLU)) {
-                // the tile's bias columns, once per warp
-                reinterpret_cast<float4*>(my_bias)[lane] = reinterpret_cast<const float4*>(g.bias + n0)[lane];
+                // the warp's bias columns
+                if (lane < kTcEpiCols / 4)
+                    reinterpret_cast<float4*>(my_bias)[lane] = reinterpret_cast<const float4*>(g.bias + n0 + cb)[lane];
                 __syncwarp();
             }
             if (!ok) {
@@ -291,7 +300,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         }
                     }
                     if (kEpi == kEpiMaskGrad) {
-                        const float* pr = g.pre + (size_t)row * g.ldc + n0 + c * 16;
+                        const float* pr = g.pre + (size_t)row * g.ldc + n0 + cb + c * 16;
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const float4 p4 = reinterpret_cast<const float4*>(pr)[u];
@@ -302,32 +311,27 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         }
                     }
                 }
-                // FP32 rows of C through the staging area, 64 columns at a time
+                // FP32 rows of C (the warp's 64 columns = 256 bytes) through the staging area
                 if (g.C) {
 #pragma unroll
-                    for (int half = 0; half < 2; ++half) {
+                    for (int c = 0; c < kTcChunks; ++c) {
+                        float4* dst = reinterpret_cast<float4*>(my_stage + lane * kStageRow + c * 64);
 #pragma unroll
-                        for (int c = 0; c < kTcChunks / 2; ++c) {
-                            float4* dst = reinterpret_cast<float4*>(my_stage + lane * kStageRow + c * 64);
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int cc = half * (kTcChunks / 2) + c;
-                                dst[u] = make_float4(f[cc][4 * u], f[cc][4 * u + 1], f[cc][4 * u + 2], f[cc][4 * u + 3]);
-                            }
-                        }
-                        __syncwarp();
-                        // a row is 16 chunks of 16 bytes: 2 rows per warp store
-#pragma unroll 4
-                        for (int r = 0; r < 32; r += 2) {
-                            const int rr = r + (lane >> 4), ch = lane & 15;
-                            const uint4 val = *reinterpret_cast<const uint4*>(my_stage + rr * kStageRow + ch * 16);
-                            *reinterpret_cast<uint4*>(g.C + (size_t)(row0 + rr) * g.ldc + n0 + half * 64 + ch * 4) = val;
-                        }
-                        __syncwarp();
+                        for (int u = 0; u < 4; ++u)
+                            dst[u] = make_float4(f[c][4 * u], f[c][4 * u + 1], f[c][4 * u + 2], f[c][4 * u + 3]);
                     }
+                    __syncwarp();
+                    // a row is 16 chunks of 16 bytes: 2 rows per warp store
+#pragma unroll 4
+                    for (int r = 0; r < 32; r += 2) {
+                        const int rr = r + (lane >> 4), ch = lane & 15;
+                        const uint4 val = *reinterpret_cast<const uint4*>(my_stage + rr * kStageRow + ch * 16);
+                        *reinterpret_cast<uint4*>(g.C + (size_t)(row0 + rr) * g.ldc + n0 + cb + ch * 4) = val;
+                    }
+                    __syncwarp();
                 }
                 if (kEpi == kEpiBiasReLU || kEpi == kEpiMaskGrad) {
-                    // BF16 rows of h through the staging area (128 columns = 256 bytes)
+                    // BF16 rows of h (the warp's 64 columns = 128 bytes) through the staging area
 #pragma unroll
                     for (int c = 0; c < kTcChunks; ++c) {
                         __nv_bfloat16 hv[16];
@@ -339,15 +343,16 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         dst[1] = *reinterpret_cast<const uint4*>(&hv[8]);
                         if (g.hbfT) {
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) g.hbfT[(size_t)(n0 + c * 16 + j) * g.ldt + row] = hv[j];
+                            for (int j = 0; j < 16; ++j) g.hbfT[(size_t)(n0 + cb + c * 16 + j) * g.ldt + row] = hv[j];
                         }
                     }
                     __syncwarp();
+                    // a row is 8 chunks of 16 bytes: 4 rows per warp store
 #pragma unroll 4
-                    for (int r = 0; r < 32; r += 2) {
-                        const int rr = r + (lane >> 4), ch = lane & 15;
+                    for (int r = 0; r < 32; r += 4) {
+                        const int rr = r + (lane >> 3), ch = lane & 7;
                         const uint4 val = *reinterpret_cast<const uint4*>(my_stage + rr * kStageRow + ch * 16);
-                        *reinterpret_cast<uint4*>(g.hbf + (size_t)(row0 + rr) * g.ldh + n0 + ch * 8) = val;
+                        *reinterpret_cast<uint4*>(g.hbf + (size_t)(row0 + rr) * g.ldh + n0 + cb + ch * 8) = val;
                     }
                     __syncwarp();
                 }
@@ -355,7 +360,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 // partial tile or unaligned rows: element by element
 #pragma unroll
                 for (int c = 0; c < kTcChunks; ++c) {
-                    const int col0 = n0 + c * 16;
+                    const int col0 = n0 + cb + c * 16;
                     if (vec && col0 + 16 <= g.N) {
                         epilogue16<kEpi>(g, row, col0, f[c]);
                     } else {
