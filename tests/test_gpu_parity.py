@@ -225,6 +225,37 @@ def test_tie_window_settings(tau):
     assert bitwise == n
 
 
+@pytest.mark.parametrize("tau", [0.0, 1e-3])
+def test_streamed_staged_update_extreme_values_and_ties(tau):
+    """The streamed kernel (staged update, shared-memory pivot column) on LPs
+    that take its rare paths: right-hand sides and entries outside [2^-100,
+    2^100] (unscreened rows), integer data with exact ties in Steps 1 and 2,
+    degenerate and phase-I LPs, infeasible and unbounded ones -- with and
+    without a tie window -- against the oracle bit for bit."""
+    rng = np.random.default_rng(131)
+    lps = []
+    for t in range(24):
+        m, n = int(rng.integers(20, 70)), int(rng.integers(20, 70))
+        A = rng.uniform(-1, 1, (m, n))
+        b = rng.uniform(-0.5, 2, m)
+        c = rng.uniform(-1, 1, n)
+        kind = t % 4
+        if kind == 0:
+            b = b * [1e35, 1e-35, 1e200, 1e-200][(t // 4) % 4]
+        elif kind == 1:
+            A = A * [1e35, 1e-35, 1e120, 1e-120][(t // 4) % 4]
+        elif kind == 2:
+            A, b, c = np.round(A * 3), np.round(b * 3), np.round(c * 3)  # exact ties
+        else:
+            b[: m // 2] = 0.0  # degenerate
+        lps.append((A, b, c))
+    batch = W.pack("streamed_extreme", lps)
+    g, r, n, bitwise = _check(batch, opts=lpb.lpb_default_opts(tau=tau, schedule=lpb.LPB_SCHED_STREAMED))
+    assert g["plan"]["num_streamed"] == batch.num_lps
+    assert len(set(r["status"].tolist())) >= 3  # optimal, infeasible and unbounded among them
+    assert bitwise == n
+
+
 def test_streamed_kernel_matches_resident_bitwise():
     """The same LPs through the global-workspace kernel and the shared-memory
     kernel give identical results (same per-LP code, different storage)."""
