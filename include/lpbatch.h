@@ -226,6 +226,9 @@ typedef struct {
     int32_t num_warm_rounds;   /* last lp_batch_solve_warm: restricted LPs solved    */
     int32_t num_cluster;       /* LPs solved on a thread-block cluster (tableau split
                                   over the CTAs' shared memory)                   */
+    int32_t num_warm_retried;  /* last lp_batch_solve_warm: LPs whose restricted LP
+                                  outgrew the first pass's 16 rows and went to the
+                                  second pass (up to 32 rows)                     */
     int64_t max_smem_bytes;    /* largest shared-memory footprint of a launch        */
     int64_t workspace_bytes;   /* global workspace of the streamed LPs (and of the
                                   streamed FP64 re-solve of large mixed LPs)      */
@@ -487,11 +490,14 @@ lpb_err lp_mlp_tc_faults(int32_t *count);
  * (up to 8 rounds).  A certified LP is reported LP_OPTIMAL with that x, the
  * duals y (0 off the restricted rows), obj = c^T x and iters = the restricted
  * pivots; every other LP is solved cold by the FP64 path (same results as
- * lp_batch_solve with LP_PREC_FP64).  Requirements: all LPs of one size m x n,
+ * lp_batch_solve with LP_PREC_FP64).  The restricted LP holds at most 16 rows
+ * in a first pass (a smaller tableau: more LPs per SM); an LP whose rows
+ * outgrow that is tried again in a second pass with up to 32 rows before it
+ * goes to the cold solve.  Requirements: all LPs of one size m x n,
  * a network with m + n inputs (b then c) and m outputs on the batch's device,
  * and every LP's FP64 tableau within one CTA's shared memory (LPB_ETOOBIG
  * otherwise).  Asynchronous like lp_batch_solve; lp_batch_plan_info reports
- * num_warm_certified, num_warm_rounds and num_fallback. */
+ * num_warm_certified, num_warm_rounds, num_warm_retried and num_fallback. */
 lpb_err lp_batch_solve_warm(lp_batch *h, lp_mlp *net, float threshold, void *stream);
 
 /* Training data from a batch of equal-size LPs (device arrays):

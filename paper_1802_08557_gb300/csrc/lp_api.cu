@@ -215,7 +215,9 @@ struct lp_batch {
     float* warm_x = nullptr;       // features [num_lps x (m+n)]
     float* warm_logits = nullptr;  // [num_lps x m]
     int32_t* warm_q = nullptr;     // LPs for the cold FP64 solve
-    int32_t* warm_stats = nullptr; // [0] queue length, [1] certified, [2] rounds, [3] queue counter
+    int32_t* warm_q2 = nullptr;    // LPs whose restricted LP outgrew the first pass's row cap
+    int32_t* warm_stats = nullptr; // [0] queue length, [1] certified, [2] rounds, [3] queue counter,
+                                   // [4] second-pass queue length
     bool last_warm = false;
     // per launch group: LP count and work counter of the persistent form
     int32_t* group_len = nullptr;
@@ -1092,30 +1094,41 @@ lpb_err lp_batch_solve_warm(lp_batch* h, lp_mlp* net, float threshold, void* str
     const int32_t N = h->num_lps;
     if (!h->warm_x) {
         if ((err = alloc(h, &h->warm_x, (size_t)N * (m + n), s)) || (err = alloc(h, &h->warm_logits, (size_t)N * m, s)) ||
-            (err = alloc(h, &h->warm_q, (size_t)N, s)) || (err = alloc(h, &h->warm_stats, 4, s)) ||
+            (err = alloc(h, &h->warm_q, (size_t)N, s)) || (err = alloc(h, &h->warm_q2, (size_t)N, s)) ||
+            (err = alloc(h, &h->warm_stats, 8, s)) ||
             (err = lpb::fp64_kernels_prepare())) {
             h->warm_x = nullptr;
             return cuda_fail(err, "warm-start buffers");
         }
     }
-    // restricted rows at most (a cap of 16 measured 8% faster on the 200 x 100
-    // family, ~6 active rows, through occupancy; 32 keeps families with more
-    // active rows certified)
-    const int kmax = std::min(m, 32);
+    // restricted rows at most: a first pass with a cap of 16 (the shared
+    // memory of a smaller tableau puts more LPs on an SM: 200 x 100 family,
+    // ~6 active rows, 3.96 against 4.82 ms per 1e5 LPs with a cap of 32), then
+    // a second pass with a cap of 32 over the LPs whose rows outgrew the
+    // first; the cold solve gets what neither certifies
+    const int kmax1 = std::min(m, 16), kmax2 = std::min(m, 32);
+    const bool two_pass = kmax2 > kmax1;
     const float logit_thr = (float)std::log((double)threshold / (1.0 - (double)threshold));
     int sms = 0;
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device))) return cuda_fail(err, "device query");
     const size_t cold_smem = (h->cold_smem + 1023) / 1024 * 1024;
     const int ctas = sms * lpb::fp64_resident_queue_ctas_per_sm(h->cold_threads, cold_smem);
     if ((err = cudaMemsetAsync(h->diag, 0, 8 * sizeof(int32_t), s)) ||
-        (err = cudaMemsetAsync(h->warm_stats, 0, 4 * sizeof(int32_t), s)) ||
+        (err = cudaMemsetAsync(h->warm_stats, 0, 8 * sizeof(int32_t), s)) ||
         (err = lpb::launch_warm_features(h->d, N, m, n, h->warm_x, s)))
         return cuda_fail(err, "warm-start features");
     lpb_err r = lp_mlp_forward(net, h->warm_x, N, h->warm_logits, stream);
     if (r != LPB_OK) return r;
-    if ((err = lpb::launch_warm(h->d, h->warm_logits, N, m, n, kmax, /*max_rounds=*/8, /*max_iters=*/50 * (kmax + n),
+    if ((err = lpb::launch_warm(h->d, h->warm_logits, N, m, n, kmax1, /*max_rounds=*/8, /*max_iters=*/50 * (kmax1 + n),
                                 logit_thr, h->tol.eps_opt, h->tol.eps_piv, /*cert_tol=*/1e-9, h->warm_q,
-                                h->warm_stats, N, h->warm_stats + 1, h->warm_stats + 2, h->diag, s)) ||
+                                h->warm_stats, N, nullptr, nullptr, two_pass ? h->warm_q2 : nullptr,
+                                two_pass ? h->warm_stats + 4 : nullptr, h->warm_stats + 1, h->warm_stats + 2, h->diag,
+                                s)) ||
+        (two_pass &&
+         (err = lpb::launch_warm(h->d, h->warm_logits, N, m, n, kmax2, /*max_rounds=*/8,
+                                 /*max_iters=*/50 * (kmax2 + n), logit_thr, h->tol.eps_opt, h->tol.eps_piv,
+                                 /*cert_tol=*/1e-9, h->warm_q, h->warm_stats, N, h->warm_q2, h->warm_stats + 4,
+                                 nullptr, nullptr, h->warm_stats + 1, h->warm_stats + 2, h->diag, s))) ||
         (err = lpb::launch_fp64_resident_queue(h->d, h->tol, h->warm_q, h->warm_stats, N, N, h->warm_stats + 3,
                                                h->diag, ctas, h->cold_threads, cold_smem, s)))
         return cuda_fail(err, "warm solve");
@@ -1241,13 +1254,14 @@ lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
     plan->num_fallback = 0;
     plan->num_warm_certified = 0;
     plan->num_warm_rounds = 0;
+    plan->num_warm_retried = 0;
     plan->internal_errors = 0;
     plan->internal_error_code = 0;
     plan->internal_error_lp = -1;
     for (int i = 0; i < 5; ++i) plan->internal_error_detail[i] = 0;
     if (h->solved) {
         DeviceGuard guard(h->device);
-        int32_t fb = 0, fbig = 0, dg[8] = {0, 0, -1, 0, 0, 0, 0, 0}, ws[4] = {0, 0, 0, 0};
+        int32_t fb = 0, fbig = 0, dg[8] = {0, 0, -1, 0, 0, 0, 0, 0}, ws[5] = {0, 0, 0, 0, 0};
         cudaError_t err = cudaSuccess;
         if (h->last_warm)
             err = cudaMemcpyAsync(ws, h->warm_stats, sizeof ws, cudaMemcpyDeviceToHost, h->last_stream);
@@ -1260,6 +1274,7 @@ lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
         plan->num_fallback = h->last_warm ? ws[0] : fb + fbig;
         plan->num_warm_certified = h->last_warm ? ws[1] : 0;
         plan->num_warm_rounds = h->last_warm ? ws[2] : 0;
+        plan->num_warm_retried = h->last_warm ? ws[4] : 0;
         plan->internal_errors = dg[0];
         plan->internal_error_code = dg[0] ? dg[1] : 0;
         plan->internal_error_lp = dg[0] ? dg[2] : -1;

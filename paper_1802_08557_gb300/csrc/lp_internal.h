@@ -288,6 +288,7 @@ cudaError_t launch_warm_features(const DeviceBatch& B, int32_t num_lps, int32_t 
 cudaError_t launch_warm(const DeviceBatch& B, const float* logits, int32_t num_lps, int32_t m, int32_t n,
                         int32_t kmax, int32_t max_rounds, int32_t max_iters, float threshold, double eps_opt,
                         double eps_piv, double cert_tol, int32_t* fb_queue, int32_t* fb_len, int32_t fb_cap,
+                        const int32_t* queue, const int32_t* queue_len, int32_t* ov_queue, int32_t* ov_len,
                         int32_t* certified, int32_t* rounds, int32_t* diag, cudaStream_t s);
 cudaError_t launch_warm_labels(const DeviceBatch& B, int32_t num_lps, int32_t m, float* labels, cudaStream_t s);
 // Input and output widths and the device of a warm-start network.

@@ -16,9 +16,11 @@
 //  4. rows the optimum violates are added to R and step 2 runs again
 //     (constraint generation: the simplex continues from the proposal until
 //     the restricted optimum is feasible); an unbounded restricted LP adds the
-//     rows that bound its ray.  After max_rounds rounds, with R full, with
-//     b_R < 0, or when a check fails, the LP goes to the queue of the cold FP64
-//     solve, which decides it.
+//     rows that bound its ray.  With R outgrowing kmax rows the LP goes to the
+//     overflow queue when one is given (the host runs a second pass with a
+//     larger kmax over it); after max_rounds rounds, with b_R < 0, when a
+//     check fails, or overflowing without that queue, it goes to the queue of
+//     the cold FP64 solve, which decides it.
 // Tolerances: tol_p = cert_tol * max(1, max|b|), tol_d = cert_tol * max(1, max|c|).
 
 #include <algorithm>
@@ -41,6 +43,10 @@ struct WarmArgs {
     int32_t* fb_queue;
     int32_t* fb_len;
     int32_t fb_cap;
+    const int32_t* queue;      // non-null: solve the LPs queue[0 .. *queue_len) (else LP = CTA index)
+    const int32_t* queue_len;
+    int32_t* ov_queue;         // non-null: LPs whose restricted LP outgrows kmax rows go here
+    int32_t* ov_len;           //   (capacity fb_cap) instead of to the cold queue
     int32_t* certified;    // count of LPs certified here
     int32_t* rounds;       // total restricted solves
     int32_t* diag;
@@ -80,10 +86,9 @@ __host__ __device__ inline WarmLayout warm_layout(int m, int n, int kmax) {
     return L;
 }
 
-__global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
+// One LP of the warm solve (the whole CTA).
+__device__ __forceinline__ void warm_one(const WarmArgs& a, const int lp) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lp = blockIdx.x;
-    if (lp >= a.num_lps) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     Reducer red{reinterpret_cast<long long*>(smem + SmallLayout::red64),
                 reinterpret_cast<unsigned*>(smem + SmallLayout::red32), nt >> 5, tid >> 5, tid & 31};
@@ -131,6 +136,7 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
     }
     __syncthreads();
     bool ok = k <= kmax;
+    bool overflow = !ok;  // the rows outgrew kmax (the only failure a larger kmax can cure)
     int iters = 0, round = 0;
     bool certified = false;
     while (ok && !certified) {
@@ -356,7 +362,11 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
             }
         }
         // ---- 4. grow R by the marked rows (ascending), if there is room
-        if (k + (int)add > kmax) { ok = false; break; }
+        if (k + (int)add > kmax) {
+            ok = false;
+            overflow = true;
+            break;
+        }
         for (int i0 = 0; i0 < m; i0 += nt) {
             const int i = i0 + tid;
             const bool sel = (i < m) && (inR[i] == 2);
@@ -382,9 +392,25 @@ __global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
         }
         if (tid == 0) atomicAdd(a.certified, 1);
     } else if (tid == 0) {
-        const int pos = atomicAdd(a.fb_len, 1);
-        if (pos < a.fb_cap) a.fb_queue[pos] = lp;
+        const bool retry = overflow && a.ov_queue != nullptr;
+        const int pos = atomicAdd(retry ? a.ov_len : a.fb_len, 1);
+        if (pos < a.fb_cap) (retry ? a.ov_queue : a.fb_queue)[pos] = lp;
         else record_internal_error(a.diag, 4, lp);
+    }
+}
+
+// One CTA per LP of the batch, or (a.queue) persistent CTAs over the LPs of a
+// device-side queue, whose length only the device knows.
+__global__ void __launch_bounds__(kWarmThreads) warm_kernel(const WarmArgs a) {
+    const int count = a.queue ? min(*a.queue_len, a.fb_cap) : min(a.num_lps, (int)blockIdx.x + 1);
+    for (int qi = blockIdx.x; qi < count; qi += gridDim.x) {
+        const int lp = a.queue ? a.queue[qi] : qi;
+        if ((unsigned)lp >= (unsigned)a.num_lps) {
+            if (threadIdx.x == 0) record_internal_error(a.diag, 9, lp);
+            continue;
+        }
+        warm_one(a, lp);
+        __syncthreads();  // the next LP reuses the shared memory
     }
 }
 
@@ -419,9 +445,11 @@ cudaError_t launch_warm_features(const DeviceBatch& B, int32_t num_lps, int32_t 
 cudaError_t launch_warm(const DeviceBatch& B, const float* logits, int32_t num_lps, int32_t m, int32_t n,
                         int32_t kmax, int32_t max_rounds, int32_t max_iters, float threshold, double eps_opt,
                         double eps_piv, double cert_tol, int32_t* fb_queue, int32_t* fb_len, int32_t fb_cap,
+                        const int32_t* queue, const int32_t* queue_len, int32_t* ov_queue, int32_t* ov_len,
                         int32_t* certified, int32_t* rounds, int32_t* diag, cudaStream_t s) {
     if (num_lps <= 0) return cudaSuccess;
     WarmArgs a{};
+    a.queue = queue; a.queue_len = queue_len; a.ov_queue = ov_queue; a.ov_len = ov_len;
     a.B = B; a.logits = logits; a.num_lps = num_lps; a.m = m; a.n = n; a.kmax = kmax;
     a.max_rounds = max_rounds; a.max_iters = max_iters; a.threshold = threshold;
     a.eps_opt = eps_opt; a.eps_piv = eps_piv; a.cert_tol = cert_tol;
@@ -430,7 +458,16 @@ cudaError_t launch_warm(const DeviceBatch& B, const float* logits, int32_t num_l
     const size_t smem = warm_smem_bytes(m, n, kmax);
     cudaError_t err = cudaFuncSetAttribute(warm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    warm_kernel<<<num_lps, kWarmThreads, smem, s>>>(a);
+    int grid = num_lps;
+    if (queue) {
+        // one wave of persistent CTAs over the queue
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((err = cudaGetDevice(&dev)) || (err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+            (err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warm_kernel, kWarmThreads, smem)))
+            return err;
+        grid = std::min<int>(num_lps, sms * std::max(1, per_sm));
+    }
+    warm_kernel<<<grid, kWarmThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

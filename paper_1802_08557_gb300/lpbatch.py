@@ -86,6 +86,7 @@ class LPBatchPlan(ctypes.Structure):
         ("num_warm_certified", ctypes.c_int32),
         ("num_warm_rounds", ctypes.c_int32),
         ("num_cluster", ctypes.c_int32),
+        ("num_warm_retried", ctypes.c_int32),
         ("max_smem_bytes", ctypes.c_int64),
         ("workspace_bytes", ctypes.c_int64),
     ]

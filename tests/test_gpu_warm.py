@@ -90,6 +90,27 @@ def test_trained_network_certifies_what_an_untrained_one_cannot(trained, test_ba
     np.testing.assert_array_equal(r0["status"], _cold(test_batch)["status"])
 
 
+@pytest.mark.parametrize("threshold", [0.2, 0.01])
+def test_second_pass_for_rows_beyond_the_first_cap(trained, test_batch, threshold):
+    """The first pass holds at most 16 restricted rows; an LP whose rows
+    outgrow that (a low threshold proposes more rows) goes to the second pass
+    with up to 32, and only then to the cold solve.  Every status equals the
+    cold FP64 solve's, optimal objectives within 1e-9; the counts add up."""
+    net, _ = trained
+    batch = test_batch.subset(np.arange(1500))
+    r, plan = WS.solve_warm(batch, net, threshold=threshold)
+    assert plan["internal_errors"] == 0
+    assert plan["num_warm_certified"] + plan["num_fallback"] == batch.num_lps
+    assert 0 <= plan["num_warm_retried"] <= batch.num_lps
+    if threshold < 0.1:
+        assert plan["num_warm_retried"] > 0, plan  # many proposals above 16 rows
+    c = _cold(batch)
+    np.testing.assert_array_equal(r["status"], c["status"])
+    opt = c["status"] == 0
+    rel = np.abs(r["obj"][opt] - c["obj"][opt]) / np.maximum(1.0, np.abs(c["obj"][opt]))
+    assert rel.max() <= 1e-9
+
+
 def test_fallback_lps_are_the_cold_fp64_results(trained, test_batch):
     """With an untrained network nothing is certified: every LP is answered by
     the cold FP64 solve, bit for bit."""
