@@ -14,8 +14,10 @@
 //    variable plus the right-hand side (column 0).  A pivot swaps the labels of
 //    the entering column and the leaving row.  Basic columns of the paper's
 //    full tableau are unit vectors and carry no information;
-//  - the tableau lives in shared memory for the whole solve; global memory is
-//    touched only to read A, b, c and write the results;
+//  - the tableau lives in shared memory for the whole solve (global memory is
+//    touched only to read A, b, c and write the results), or, above one CTA's
+//    shared memory, in a global workspace slot whose rank-1 update streams
+//    through shared-memory rings filled by bulk asynchronous copies;
 //  - reductions are warp `redux` instructions on 64-bit order-preserving
 //    integer keys of the FP64 values (exact, no FP64-pipe compares);
 //  - phase I runs in the same kernel (the paper launches twice, Section 5);
