@@ -575,6 +575,22 @@ def run_ours(args):
             "results_identical_to_default_plan": bool(all(np.array_equal(r1[k], res_u["fp64"][k])
                                                           for k in ("status", "iters", "obj", "x", "y")))}
         hs1.close()
+        # the same for mixed precision: one persistent launch of the mixed
+        # per-LP code, then the FP64 re-solves of the uncertified LPs
+        hs2 = lpb.BatchSolver(ub, opts=lpb.lpb_default_opts(precision=lpb.LP_PREC_FP32_REFINE,
+                                                             schedule=lpb.LPB_SCHED_SINGLE), stream=stream)
+        ms_single2 = ev_time(lambda: lpb.lp_batch_solve(hs2.h, stream))
+        ms_single2_graph = ev_time(lambda: lpb.lp_batch_solve_graph(hs2.h, stream))
+        r2 = hs2.results()
+        uneven["fp32r_single_launch"] = {
+            "ms": ms_single2, "ms_graph": ms_single2_graph,
+            "launches_per_solve": hs2.plan_info()["num_groups"],
+            "what": "one launch of the mixed per-LP code plus the FP64 re-solve launches",
+            "default_plan_launches_per_solve": uneven["fp32r"]["groups"],
+            "value": ub.num_lps * ws / (min(ms_single2, ms_single2_graph) * 1e-3),
+            "results_identical_to_default_plan": bool(all(np.array_equal(r2[k], res_u["fp32r"][k])
+                                                          for k in ("status", "iters", "obj", "x", "y")))}
+        hs2.close()
         uneven["value"] = max(uneven["fp64"]["value"], uneven["fp32r"]["value"])
         opt_u = res_u["fp64"]["status"] == 0
         rel_u = (np.abs(res_u["fp32r"]["obj"][opt_u] - res_u["fp64"]["obj"][opt_u])

@@ -95,11 +95,13 @@ typedef struct {
  * STREAMED: global workspace for every LP (FP32_REFINE: the FP32 tableau of
  * every LP).  CLUSTER: as AUTO, but an FP64 tableau above one CTA is split by
  * rows over the shared memory of a thread-block cluster of 2-16 CTAs (the
- * smallest that holds it; all CTAs take the same decisions).  SINGLE
- * (LP_PREC_FP64 only): the whole batch in one persistent launch -- 512-thread
- * CTAs take the LPs, longest work first, from one work queue and keep each
- * tableau in their shared memory when it fits 110 KB, else in their global
- * workspace slot.  Results are bit-identical under every schedule. */
+ * smallest that holds it; all CTAs take the same decisions).  SINGLE: the
+ * whole batch in one persistent launch -- CTAs (512 threads for LP_PREC_FP64,
+ * 256 for LP_PREC_FP32_REFINE) take the LPs, longest work first, from one work
+ * queue and keep each tableau in their shared memory when it fits 110 KB,
+ * else in their global workspace slot; with LP_PREC_FP32_REFINE the FP64
+ * re-solves of uncertified LPs follow as separate launches (they need the
+ * whole pass's queues).  Results are bit-identical under every schedule. */
 enum { LPB_SCHED_AUTO = 0, LPB_SCHED_STREAMED = 1, LPB_SCHED_CLUSTER = 2, LPB_SCHED_SINGLE = 3 };
 
 typedef struct lp_batch lp_batch;   /* opaque; owned by the library */
@@ -261,8 +263,8 @@ lpb_err lp_batch_autotune(lp_batch *h, int32_t rounds, void *stream);
 typedef struct {
     int32_t kind;        /* 0 mixed precision, 1 FP64 shared-memory resident, 2 FP64 streamed,
                             3 FP64 on a thread-block cluster, 4 mixed precision
-                            with the FP32 tableau in a global workspace, 5 FP64
-                            single launch (LPB_SCHED_SINGLE) */
+                            with the FP32 tableau in a global workspace, 5 single
+                            launch (LPB_SCHED_SINGLE, FP64 or mixed) */
     int32_t count;       /* LPs in the group                                  */
     int32_t threads;     /* threads per CTA                                   */
     int32_t persistent;  /* 1: persistent CTAs over a work queue              */

@@ -281,6 +281,14 @@ lpb::FallbackQueues fallback_queues(const lp_batch* h) {
     return lpb::FallbackQueues{h->fb_queue, h->fb_len, h->num_fsmall, h->fbig_queue, h->fbig_len, h->num_fbig};
 }
 
+// CTAs of a group's persistent form on `sms` SMs: CTAs per SM x SMs, at most
+// one per LP.
+void size_persistent(Group& g, int kind, int sms) {
+    const int per_sm = kind == 0 ? lpb::mixed_queue_ctas_per_sm(g.threads, g.smem)
+                                 : lpb::fp64_resident_queue_ctas_per_sm(g.threads, g.smem);
+    g.ctas = (int32_t)std::min<int64_t>((int64_t)sms * per_sm, g.count);
+}
+
 // One launch group on stream ls: kind 0 mixed precision, 1 FP64 resident;
 // one CTA per LP, or persistent CTAs over the group's work queue.
 cudaError_t launch_group(lp_batch* h, int kind, const Group& g, cudaStream_t ls) {
@@ -330,7 +338,11 @@ lpb_err enqueue_solve(lp_batch* h, cudaStream_t s, bool timing) {
             used[lane] = true;
         }
         const Job& j = jobs[i];
-        if (j.kind == 5) {
+        if (j.kind == 5 && h->num_mixed > 0) {
+            err = lpb::launch_mixed_single(h->d, h->tol, h->mp, h->d_order + h->single_offset, h->d_resident,
+                                           h->num_single, h->single_ctas, h->single_smem, h->single_workspace,
+                                           h->single_slot_bytes, h->single_counter, fallback_queues(h), h->diag, ls);
+        } else if (j.kind == 5) {
             err = lpb::launch_fp64_single(h->d, h->tol, h->d_order + h->single_offset, h->d_resident, h->num_single,
                                           h->single_ctas, h->single_smem, h->single_workspace, h->single_slot_bytes,
                                           h->single_counter, h->diag, ls);
@@ -440,8 +452,6 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
     if (o.schedule != LPB_SCHED_AUTO && o.schedule != LPB_SCHED_STREAMED && o.schedule != LPB_SCHED_CLUSTER &&
         o.schedule != LPB_SCHED_SINGLE)
         return fail(LPB_EINVAL, "unknown schedule");
-    if (o.schedule == LPB_SCHED_SINGLE && o.precision != LP_PREC_FP64)
-        return fail(LPB_EINVAL, "LPB_SCHED_SINGLE is for LP_PREC_FP64");
     if (!(o.eps_opt >= 0) || !(o.eps_piv >= 0) || !(o.eps_feas >= 0) || !(o.tau >= 0))
         return fail(LPB_EINVAL, "tolerances must be >= 0");
 
@@ -590,6 +600,22 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
                 fbig_lps.push_back(k);
             }
             const size_t mneed = lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]);
+            if (o.schedule == LPB_SCHED_SINGLE) {
+                // one launch for all: the LP's area in shared memory up to
+                // kMixedSingleSmemCap (two CTAs per SM), else in this CTA's
+                // global workspace slot
+                if (single_resident.empty()) single_resident.assign((size_t)num_lps, 0);
+                single.push_back(k);
+                if (mneed <= lpb::kMixedSingleSmemCap) {
+                    single_resident[k] = 1;
+                    h->single_smem = std::max(h->single_smem, mneed);
+                } else {
+                    ++h->num_single_streamed;
+                    h->single_slot_bytes = std::max(
+                        h->single_slot_bytes, (lpb::mixed_layout(hm[k], hn[k], hk[k]).total + 255) & ~size_t(255));
+                }
+                continue;
+            }
             if (o.schedule != LPB_SCHED_STREAMED && mneed <= queue_smem_cap) {
                 const int threads = mixed_threads(hm[k], hn[k], hk[k], o.block_threads);
                 // shared memory rounded to 1 KiB for the one-warp form (it sets
@@ -743,6 +769,7 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
     lpt(single);
     h->single_offset = (int64_t)order.size();
     h->num_single = (int32_t)single.size();
+    if (o.precision == LP_PREC_FP32_REFINE) h->num_mixed += h->num_single;
     order.insert(order.end(), single.begin(), single.end());
     lpt(streamed);
     h->streamed_offset = (int64_t)order.size();
@@ -759,15 +786,18 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
             (err = cudaMemcpyAsync(h->d_resident, single_resident.data(), (size_t)num_lps, cudaMemcpyHostToDevice, s)))
             return bail_cuda(err, "plan upload");
         int sms = 0;
+        const bool mixed = o.precision == LP_PREC_FP32_REFINE;
+        // (each LP's footprint above includes the reduction scratch its area follows)
         h->single_smem = std::max(h->single_smem, lpb::SmallLayout::total);
-        // streamed LPs stage their update in the CTA's shared memory beyond the reduction scratch
-        if (h->num_single_streamed > 0)
+        // FP64 streamed LPs stage their update in the CTA's shared memory beyond the reduction scratch
+        if (!mixed && h->num_single_streamed > 0)
             h->single_smem = std::max(h->single_smem, lpb::SmallLayout::total + lpb::kStreamStageBytes);
         h->single_smem = (h->single_smem + 1023) / 1024 * 1024;
         if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device)) ||
-            (err = lpb::fp64_single_prepare(h->single_smem)))
+            (err = mixed ? lpb::mixed_single_prepare(h->single_smem) : lpb::fp64_single_prepare(h->single_smem)))
             return bail_cuda(err, "single launch set-up");
-        const int per_sm = std::max(1, lpb::fp64_single_ctas_per_sm(h->single_smem));
+        const int per_sm = std::max(1, mixed ? lpb::mixed_single_ctas_per_sm(h->single_smem)
+                                             : lpb::fp64_single_ctas_per_sm(h->single_smem));
         int64_t ctas = std::min<int64_t>((int64_t)sms * per_sm, h->num_single);
         if (h->num_single_streamed > 0) {
             h->single_slot_bytes = (h->single_slot_bytes + 255) & ~size_t(255);
@@ -776,6 +806,7 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
                 return bail_cuda(err, "single-launch workspace allocation");
         }
         h->single_ctas = (int32_t)ctas;
+        h->max_smem = std::max(h->max_smem, h->single_smem);
         if ((err = alloc(h, &h->single_counter, 1, s))) return bail_cuda(err, "single-launch counter");
     }
     if (h->num_streamed > 0) {
@@ -962,11 +993,7 @@ lpb_err lp_batch_autotune(lp_batch* h, int32_t rounds, void* stream) {
                     Group t = g;
                     t.threads = threads;
                     t.persistent = persistent;
-                    if (persistent) {
-                        const int per_sm = kind == 0 ? lpb::mixed_queue_ctas_per_sm(threads, t.smem)
-                                                     : lpb::fp64_resident_queue_ctas_per_sm(threads, t.smem);
-                        t.ctas = (int32_t)std::min<int64_t>((int64_t)sms * per_sm, t.count);
-                    }
+                    if (persistent) size_persistent(t, kind, sms);
                     float ms = 0.0f;
                     cudaError_t e = time_group(kind, t, ms);
                     if (e != cudaSuccess) return e;
@@ -1010,9 +1037,7 @@ lpb_err lp_batch_set_group_form(lp_batch* h, int32_t index, int32_t threads, int
         int sms = 0;
         cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
         if (err) return cuda_fail(err, "device query");
-        const int per_sm = kind == 0 ? lpb::mixed_queue_ctas_per_sm(threads, g.smem)
-                                     : lpb::fp64_resident_queue_ctas_per_sm(threads, g.smem);
-        g.ctas = (int32_t)std::min<int64_t>((int64_t)sms * per_sm, g.count);
+        size_persistent(g, kind, sms);
     }
     if (h->graph_exec) {
         cudaGraphExecDestroy(h->graph_exec);
@@ -1033,7 +1058,7 @@ lpb_err lp_batch_group_info(lp_batch* h, int32_t index, lp_batch_group* out) {
     if (h->num_single > 0 && index == total - 1) {
         out->kind = 5;
         out->count = h->num_single;
-        out->threads = lpb::kStreamedThreads;
+        out->threads = h->num_mixed > 0 ? lpb::kMixedSingleThreads : lpb::kStreamedThreads;
         out->persistent = 1;
         out->smem_bytes = (int64_t)h->single_smem;
         out->tuned_ms = -1.0f;
@@ -1285,7 +1310,8 @@ lpb_err lp_batch_plan_info(lp_batch* h, lp_batch_plan* plan) {
     plan->max_smem_bytes = (int64_t)h->max_smem;
     plan->workspace_bytes = (int64_t)h->streamed_slots * (int64_t)h->slot_bytes +
                             (int64_t)h->mstream_slots * (int64_t)h->mslot_bytes +
-                            (int64_t)h->fbig_slots * (int64_t)h->fbig_slot_bytes;
+                            (int64_t)h->fbig_slots * (int64_t)h->fbig_slot_bytes +
+                            (h->single_workspace ? (int64_t)h->single_ctas * (int64_t)h->single_slot_bytes : 0);
     return LPB_OK;
 }
 

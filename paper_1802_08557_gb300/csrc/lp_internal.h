@@ -273,6 +273,17 @@ int mixed_queue_ctas_per_sm(int threads, size_t smem);
 // `slot_bytes` bytes (at least mixed_layout(m, n, k).total of every listed LP,
 // a multiple of 256).  Results are bit-identical to the shared-memory kernels.
 constexpr int kMixedStreamedThreads = 512;
+// LPB_SCHED_SINGLE with mixed precision: one persistent launch of CTAs of this
+// many threads (two per SM), each LP's area in shared memory up to
+// kMixedSingleSmemCap, else in the CTA's global workspace slot.
+constexpr int kMixedSingleThreads = 256;
+constexpr size_t kMixedSingleSmemCap = 110 * 1024;
+cudaError_t mixed_single_prepare(size_t smem);
+int mixed_single_ctas_per_sm(size_t smem);
+cudaError_t launch_mixed_single(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
+                                const int32_t* order, const uint8_t* resident, int32_t count, int ctas, size_t smem,
+                                unsigned char* workspace, size_t slot_bytes, int32_t* counter,
+                                const FallbackQueues& fq, int32_t* diag, cudaStream_t stream);
 cudaError_t launch_mixed_streamed(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
                                   const int32_t* order, int32_t count, int slots, unsigned char* workspace,
                                   size_t slot_bytes, int32_t* counter, const FallbackQueues& fq, int32_t* diag,

@@ -1,5 +1,6 @@
 // lp_mixed_streamed.cu -- mixed-precision simplex for LPs whose FP32 tableau
-// exceeds one CTA's shared memory: the same per-LP code as the shared-memory
+// exceeds one CTA's shared memory (and the single-launch form, which also
+// takes such LPs): the same per-LP code as the shared-memory
 // kernels (mixed_solve: FP32 Steps 1-3 of Section 3, FP64 certificate), with
 // the LP's area (certificate vectors, labels, FP32 tableau) in a global
 // workspace slot instead.  Persistent CTAs take LPs from an atomic counter;
@@ -39,7 +40,68 @@ mixed_streamed_kernel(const DeviceBatch B, const Tolerances tol, const MixedPara
     }
 }
 
+// A whole mixed-precision batch in one launch (LPB_SCHED_SINGLE): persistent
+// CTAs take the LPs order[0 .. count) (longest work first) from the atomic
+// `counter` and solve each with its area in this CTA's shared memory when it
+// fits (resident[lp] != 0), else in this CTA's global workspace slot -- the
+// per-LP code of the other mixed kernels, so the same results.  The FP64
+// re-solves of the LPs it does not certify stay separate launches: they need
+// the whole pass's queues.
+__global__ void __launch_bounds__(kMixedSingleThreads, 2)
+mixed_single_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp,
+                    const int32_t* __restrict__ order, const uint8_t* __restrict__ resident, const int32_t count,
+                    unsigned char* workspace, const size_t slot_bytes, int32_t* __restrict__ counter,
+                    const FallbackQueues fq, int32_t* __restrict__ diag)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int next;
+    unsigned char* slot = workspace ? workspace + (size_t)blockIdx.x * slot_bytes : nullptr;
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int idx = next;
+        __syncthreads();
+        if (idx >= count) break;
+        const int lp = order[idx];
+        BlockGroup g(reinterpret_cast<long long*>(smem + SmallLayout::red64),
+                     reinterpret_cast<unsigned*>(smem + SmallLayout::red32));
+        if (resident[lp])
+            mixed_solve_lp(g, B, tol, mp, lp, smem + SmallLayout::total, fq, diag);
+        else if (slot)
+            mixed_solve_lp(g, B, tol, mp, lp, slot, fq, diag);
+        else if (threadIdx.x == 0)
+            record_internal_error(diag, 7, lp);  // a plan without a slot for a streamed LP
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+cudaError_t mixed_single_prepare(size_t smem) {
+    return cudaFuncSetAttribute(mixed_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int mixed_single_ctas_per_sm(size_t smem) {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, mixed_single_kernel, kMixedSingleThreads, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return blocks;
+}
+
+cudaError_t launch_mixed_single(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
+                                const int32_t* order, const uint8_t* resident, int32_t count, int ctas, size_t smem,
+                                unsigned char* workspace, size_t slot_bytes, int32_t* counter,
+                                const FallbackQueues& fq, int32_t* diag, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
+    if (err != cudaSuccess) return err;
+    mixed_single_kernel<<<ctas, kMixedSingleThreads, smem, stream>>>(B, tol, mp, order, resident, count, workspace,
+                                                                      slot_bytes, counter, fq, diag);
+    return cudaGetLastError();
+}
 
 int mixed_streamed_ctas_per_sm() {
     int blocks = 0;

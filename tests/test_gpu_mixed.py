@@ -175,7 +175,7 @@ def test_mixed_large_lps_and_their_fp64_streamed_re_solve():
             if t in (2, 6):
                 A[::7] = -A[::7]
         if t % 2 == 1:
-            A[0, 0] = 2.0 ** 61  # outside the FP32 range: straight to the FP64 re-solve
+            A[0, 0] = 2.0 ** 61  # above the FP32 pass's 2^60 bound: straight to the FP64 re-solve
         forced.append(t % 2 == 1)
         lps.append((A, b, c))
     batch = W.pack("large_mixed", lps)

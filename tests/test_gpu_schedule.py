@@ -152,6 +152,46 @@ def test_single_launch_schedule_gives_identical_results():
     a = gpu_solve_opts(big, lpb.lpb_default_opts(schedule=lpb.LPB_SCHED_STREAMED))
     b = gpu_solve_opts(big, lpb.lpb_default_opts(schedule=lpb.LPB_SCHED_SINGLE))
     _same(b, a)
-    with pytest.raises(lpb.LPBError):  # mixed precision has no single-launch form
-        lpb.BatchSolver(batch, opts=lpb.lpb_default_opts(precision=lpb.LP_PREC_FP32_REFINE,
+
+
+def test_mixed_single_launch_gives_identical_results():
+    """LPB_SCHED_SINGLE with mixed precision: one persistent launch of the
+    mixed per-LP code (each LP's area in shared memory up to 110 KB, else in
+    the CTA's global slot), then the FP64 re-solves -- the same bits as the
+    default mixed plan, with LPs whose FP32 tableau is resident in one plan and
+    streamed in the other, phase I, infeasible and unbounded LPs, and LPs the
+    certificate hands to the FP64 re-solve; again on a repeat solve and
+    through a graph replay."""
+    rng = np.random.default_rng(23)
+    lps = [W.uneven_dense(300, lo=8, hi=200, start=41).lp(k) for k in range(300)]
+    for m, n in [(300, 250), (180, 170), (200, 190)]:        # FP32 areas above 110 KB
+        lps.append((rng.uniform(0, 1, (m, n)), rng.uniform(1, 100, m), rng.uniform(0, 1, n)))
+    A = rng.uniform(0, 1, (60, 50)); A[0, 0] = 2.0 ** 61      # above the FP32 pass's 2^60 bound: FP64 re-solve
+    lps.append((A, rng.uniform(1, 100, 60), rng.uniform(0, 1, 50)))
+    lps += [W.mixed_sign_dense(80, 40, 40, start=5).lp(k) for k in range(80)]
+    batch = W.pack("single_mixed", lps)
+    opts = lpb.lpb_default_opts(precision=lpb.LP_PREC_FP32_REFINE)
+    ref = lpb.BatchSolver(batch, opts=opts)
+    try:
+        ref.solve()
+        want = ref.results()
+        want_plan = ref.plan_info()
+    finally:
+        ref.close()
+    s = lpb.BatchSolver(batch, opts=lpb.lpb_default_opts(precision=lpb.LP_PREC_FP32_REFINE,
                                                          schedule=lpb.LPB_SCHED_SINGLE))
+    try:
+        groups = lpb.lp_batch_groups(s.h)
+        assert len(groups) == 1 and groups[0]["kind"] == 5 and groups[0]["count"] == batch.num_lps, groups
+        for run in range(2):
+            s.solve()
+            got = s.results()
+            _same(got, want)
+            plan = s.plan_info()
+            assert plan["internal_errors"] == 0 and plan["num_mixed"] == batch.num_lps
+            assert plan["num_fallback"] == want_plan["num_fallback"] >= 1
+        assert len(set(want["status"].tolist())) == 3
+        lpb.lp_batch_solve_graph(s.h)
+        _same(s.results(), want)
+    finally:
+        s.close()
