@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "lp_internal.h"
 #include "lpbatch.h"
 
@@ -45,14 +47,58 @@ lpb_err fail(lpb_err e, const std::string& msg) { return lpb::api_fail(e, msg); 
 
 lpb_err cuda_fail(cudaError_t err, const char* what) { return lpb::api_cuda_fail(err, what); }
 
-// One stream-ordered memory pool per device that keeps freed memory cached,
-// so that create/destroy cycles do not return memory to the driver.
+// Identity of the calling thread's current CUDA context (0 if there is none
+// or the driver cannot say).  The per-device pool cache below holds a pool of
+// one context and starts over when it changes: after cudaDeviceReset, or with
+// another context current, the pool it held is gone or not ours.
+unsigned long long context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(p);
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return 0;
+    if (!ctx) {
+        // no context yet: the runtime's first call makes its primary context
+        // current; do that now, so that what is cached belongs to it
+        cudaFree(nullptr);
+        if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    }
+    unsigned long long id = 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// One stream-ordered memory pool per device and context that keeps freed
+// memory cached, so that create/destroy cycles do not return memory to the
+// driver.  A changed context (cudaDeviceReset, or another context current)
+// gets a pool of its own; the old one is forgotten, not destroyed (it went
+// with its context, or belongs to one that is not current).
+struct DeviceCache {
+    unsigned long long ctx = 0;
+    cudaMemPool_t pool = nullptr;
+};
+std::mutex g_cache_mu;
+std::map<int, DeviceCache> g_cache;
+
 cudaError_t device_pool(int dev, cudaMemPool_t* out) {
-    static std::mutex mu;
-    static std::map<int, cudaMemPool_t> pools;
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = pools.find(dev);
-    if (it != pools.end()) { *out = it->second; return cudaSuccess; }
+    const unsigned long long ctx = context_id();
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    DeviceCache& c = g_cache[dev];
+    if (c.pool && c.ctx == ctx) { *out = c.pool; return cudaSuccess; }
     cudaMemPoolProps props;
     std::memset(&props, 0, sizeof props);
     props.allocType = cudaMemAllocationTypePinned;
@@ -64,7 +110,8 @@ cudaError_t device_pool(int dev, cudaMemPool_t* out) {
     uint64_t keep = UINT64_MAX;
     err = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     if (err != cudaSuccess) return err;
-    pools[dev] = pool;
+    c.pool = pool;
+    c.ctx = ctx;
     *out = pool;
     return cudaSuccess;
 }

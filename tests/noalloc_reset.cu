@@ -1,4 +1,5 @@
-// noalloc_reset.cu -- lp_solve_uniform_noalloc across a cudaDeviceReset.
+// noalloc_reset.cu -- lp_solve_uniform_noalloc (and the library's cached
+// memory pool) across a cudaDeviceReset.
 //
 // Built by tests/test_zz_no_alloc.py from this file and the library's own
 // object files, so that this program and the library share one CUDA runtime
@@ -11,6 +12,10 @@
 //     module (with its static scratch array) are gone.
 //  4. The inputs are allocated and copied again, and lp_solve_uniform_noalloc
 //     is called again in the new context: bit-identical again.
+//  5. The regular path and lp_solve_host (host arrays, 3 ranges) run before
+//     and after the reset too: the library keeps a stream-ordered memory pool
+//     per device and context, and must not use the old context's pool in the
+//     new one.
 //
 // Prints "noalloc reset ok" and exits 0 on success; any mismatch or error
 // exits non-zero with a message.
@@ -92,6 +97,35 @@ bool noalloc_solve(const DeviceData& d, int N, int m, int n, Results& r) {
     return true;
 }
 
+bool regular_solve(const DeviceData& d, int N, int m, int n, size_t a_len, Results& r) {
+    lp_batch* h = nullptr;
+    lpb_err e = lp_batch_create(&h, N, std::vector<int32_t>(N, m).data(), std::vector<int32_t>(N, n).data(), nullptr,
+                                d.A, (int64_t)a_len, nullptr, d.b, (int64_t)N * m, nullptr, d.c, (int64_t)N * n,
+                                LPB_DEVICE, nullptr, nullptr);
+    if (e == LPB_OK) e = lp_batch_solve(h, nullptr);
+    if (e == LPB_OK)
+        e = lp_batch_results(h, r.status.data(), r.iters.data(), r.obj.data(), r.x.data(), r.y.data(), LPB_HOST);
+    if (h) lp_batch_destroy(h);
+    if (e != LPB_OK) {
+        std::fprintf(stderr, "regular path: %s (%s)\n", lpb_strerror(e), lpb_last_error());
+        return false;
+    }
+    return true;
+}
+
+bool host_solve(const std::vector<double>& A, const std::vector<double>& b, const std::vector<double>& c, int N,
+                int m, int n, Results& r) {
+    const lpb_err e = lp_solve_host(N, std::vector<int32_t>(N, m).data(), std::vector<int32_t>(N, n).data(), nullptr,
+                                    A.data(), (int64_t)A.size(), nullptr, b.data(), (int64_t)b.size(), nullptr,
+                                    c.data(), (int64_t)c.size(), nullptr, 3, r.status.data(), r.iters.data(),
+                                    r.obj.data(), r.x.data(), r.y.data());
+    if (e != LPB_OK) {
+        std::fprintf(stderr, "lp_solve_host: %s (%s)\n", lpb_strerror(e), lpb_last_error());
+        return false;
+    }
+    return true;
+}
+
 bool same(const Results& a, const Results& b, const char* what) {
     const bool ok = a.status == b.status && a.iters == b.iters &&
                     std::memcmp(a.obj.data(), b.obj.data(), a.obj.size() * 8) == 0 &&
@@ -112,19 +146,9 @@ bool run() {
     DeviceData d;
     if (!upload(d, A, b, c, N, m, n)) return false;
     Results ref(N, m, n);
-    lp_batch* h = nullptr;
-    lpb_err e = lp_batch_create(&h, N, std::vector<int32_t>(N, m).data(), std::vector<int32_t>(N, n).data(), nullptr,
-                                d.A, (int64_t)A.size(), nullptr, d.b, (int64_t)b.size(), nullptr, d.c,
-                                (int64_t)c.size(), LPB_DEVICE, nullptr, nullptr);
-    if (e == LPB_OK) e = lp_batch_solve(h, nullptr);
-    if (e == LPB_OK)
-        e = lp_batch_results(h, ref.status.data(), ref.iters.data(), ref.obj.data(), ref.x.data(), ref.y.data(),
-                             LPB_HOST);
-    if (e != LPB_OK) {
-        std::fprintf(stderr, "regular path: %s (%s)\n", lpb_strerror(e), lpb_last_error());
-        return false;
-    }
-    lp_batch_destroy(h);
+    if (!regular_solve(d, N, m, n, A.size(), ref)) return false;
+    Results r0(N, m, n);
+    if (!host_solve(A, b, c, N, m, n, r0) || !same(ref, r0, "lp_solve_host before the reset")) return false;
     int phase1 = 0, statuses[5] = {0, 0, 0, 0, 0};
     for (int k = 0; k < N; ++k) {
         phase1 += (k % 4 == 0);
@@ -140,6 +164,9 @@ bool run() {
     if (!upload(d2, A, b, c, N, m, n)) return false;
     Results r2(N, m, n);
     if (!noalloc_solve(d2, N, m, n, r2) || !same(ref, r2, "after the reset")) return false;
+    Results r3(N, m, n), r4(N, m, n);
+    if (!regular_solve(d2, N, m, n, A.size(), r3) || !same(ref, r3, "regular path after the reset")) return false;
+    if (!host_solve(A, b, c, N, m, n, r4) || !same(ref, r4, "lp_solve_host after the reset")) return false;
     std::printf("noalloc reset ok: %d LPs of %dx%d (%d with phase I; optimal %d, infeasible %d, unbounded %d)\n", N,
                 m, n, phase1, statuses[0], statuses[1], statuses[2]);
     return true;

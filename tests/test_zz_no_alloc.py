@@ -101,7 +101,9 @@ def test_noalloc_after_device_reset(lib, tmp_path):
     the library's objects, so both share one CUDA runtime) solves with the
     regular path, with this entry point, resets the device and solves again
     with this entry point in the new context: both calls bit-identical to the
-    regular path.  No torch in that process, so nothing else holds the
+    regular path.  The regular path and lp_solve_host run on both sides of the
+    reset too (the library's cached memory pool must start over in the new
+    context).  No torch in that process, so nothing else holds the
     context."""
     from paper_1802_08557_gb300 import build
     nvcc = build.nvcc()
