@@ -281,6 +281,7 @@ struct lp_batch {
     // LPB_SCHED_SINGLE: every LP in one persistent launch over order[single_offset ...)
     int64_t single_offset = 0;
     int32_t num_single = 0, num_single_streamed = 0, single_ctas = 0;
+    int32_t single_warp_from = 0;      // mixed: order[single_offset + single_warp_from ...) one LP per warp
     size_t single_smem = 0, single_slot_bytes = 0;
     uint8_t* d_resident = nullptr;     // per LP: 1 = tableau in shared memory
     unsigned char* single_workspace = nullptr;
@@ -387,8 +388,9 @@ lpb_err enqueue_solve(lp_batch* h, cudaStream_t s, bool timing) {
         const Job& j = jobs[i];
         if (j.kind == 5 && h->num_mixed > 0) {
             err = lpb::launch_mixed_single(h->d, h->tol, h->mp, h->d_order + h->single_offset, h->d_resident,
-                                           h->num_single, h->single_ctas, h->single_smem, h->single_workspace,
-                                           h->single_slot_bytes, h->single_counter, fallback_queues(h), h->diag, ls);
+                                           h->num_single, h->single_warp_from, h->single_ctas, h->single_smem,
+                                           h->single_workspace, h->single_slot_bytes, h->single_counter,
+                                           fallback_queues(h), h->diag, ls);
         } else if (j.kind == 5) {
             err = lpb::launch_fp64_single(h->d, h->tol, h->d_order + h->single_offset, h->d_resident, h->num_single,
                                           h->single_ctas, h->single_smem, h->single_workspace, h->single_slot_bytes,
@@ -619,6 +621,7 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
     std::vector<int32_t> mstream;                         // mixed precision, tableau in global memory
     std::vector<int32_t> fbig_lps;                        // mixed LPs whose FP64 re-solve exceeds one CTA
     std::vector<int32_t> single;                          // LPB_SCHED_SINGLE: every LP
+    std::vector<int32_t> single_warp;                     // ... (mixed) the ones solved one per warp
     std::vector<uint8_t> single_resident;                 // ... per LP: 1 = in shared memory
     const size_t queue_smem_cap = lpb::kMaxSmemPerBlock - 1024;
     h->uniform_m = hm[0];
@@ -648,10 +651,19 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
             }
             const size_t mneed = lpb::mixed_smem_bytes(hm[k], hn[k], hk[k]);
             if (o.schedule == LPB_SCHED_SINGLE) {
-                // one launch for all: the LP's area in shared memory up to
-                // kMixedSingleSmemCap (two CTAs per SM), else in this CTA's
-                // global workspace slot
+                // one launch for all: an LP the default plan gives one warp
+                // and whose area fits a warp's share of the CTA in warp mode
+                // (listed last); the others one per CTA, the LP's area in
+                // shared memory up to kMixedSingleSmemCap (two CTAs per SM),
+                // else in this CTA's global workspace slot
                 if (single_resident.empty()) single_resident.assign((size_t)num_lps, 0);
+                if (mixed_threads(hm[k], hn[k], hk[k], o.block_threads) == 32 &&
+                    lpb::mixed_layout(hm[k], hn[k], hk[k]).total <= lpb::kMixedSingleWarpArea) {
+                    single_resident[k] = 1;
+                    single_warp.push_back(k);
+                    h->single_smem = std::max(h->single_smem, lpb::kMixedSingleSmemCap);  // every warp's area
+                    continue;
+                }
                 single.push_back(k);
                 if (mneed <= lpb::kMixedSingleSmemCap) {
                     single_resident[k] = 1;
@@ -814,6 +826,9 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
             return bail_cuda(err, "mixed streamed workspace allocation");
     }
     lpt(single);
+    lpt(single_warp);
+    h->single_warp_from = (int32_t)single.size();
+    single.insert(single.end(), single_warp.begin(), single_warp.end());
     h->single_offset = (int64_t)order.size();
     h->num_single = (int32_t)single.size();
     if (o.precision == LP_PREC_FP32_REFINE) h->num_mixed += h->num_single;

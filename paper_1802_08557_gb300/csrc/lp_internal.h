@@ -274,16 +274,23 @@ int mixed_queue_ctas_per_sm(int threads, size_t smem);
 // a multiple of 256).  Results are bit-identical to the shared-memory kernels.
 constexpr int kMixedStreamedThreads = 512;
 // LPB_SCHED_SINGLE with mixed precision: one persistent launch of CTAs of this
-// many threads (two per SM), each LP's area in shared memory up to
-// kMixedSingleSmemCap, else in the CTA's global workspace slot.
+// many threads (two per SM).  order[0 .. warp_from) are solved one per CTA,
+// each LP's area in shared memory up to kMixedSingleSmemCap (resident[lp]),
+// else in the CTA's global workspace slot; order[warp_from .. count) -- LPs
+// the default plan gives one warp, with an area of at most
+// kMixedSingleWarpArea -- one per warp, warp w of a CTA working in
+// smem + w * kMixedSingleWarpArea (the CTA's shared memory is then
+// kMixedSingleSmemCap).
 constexpr int kMixedSingleThreads = 256;
 constexpr size_t kMixedSingleSmemCap = 110 * 1024;
+constexpr size_t kMixedSingleWarpArea = kMixedSingleSmemCap / (kMixedSingleThreads / 32);
+static_assert(kMixedSingleWarpArea % 128 == 0, "warp areas of the single launch must stay 128-byte aligned");
 cudaError_t mixed_single_prepare(size_t smem);
 int mixed_single_ctas_per_sm(size_t smem);
 cudaError_t launch_mixed_single(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
-                                const int32_t* order, const uint8_t* resident, int32_t count, int ctas, size_t smem,
-                                unsigned char* workspace, size_t slot_bytes, int32_t* counter,
-                                const FallbackQueues& fq, int32_t* diag, cudaStream_t stream);
+                                const int32_t* order, const uint8_t* resident, int32_t count, int32_t warp_from,
+                                int ctas, size_t smem, unsigned char* workspace, size_t slot_bytes,
+                                int32_t* counter, const FallbackQueues& fq, int32_t* diag, cudaStream_t stream);
 cudaError_t launch_mixed_streamed(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
                                   const int32_t* order, int32_t count, int slots, unsigned char* workspace,
                                   size_t slot_bytes, int32_t* counter, const FallbackQueues& fq, int32_t* diag,

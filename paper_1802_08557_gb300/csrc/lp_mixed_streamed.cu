@@ -41,27 +41,36 @@ mixed_streamed_kernel(const DeviceBatch B, const Tolerances tol, const MixedPara
 }
 
 // A whole mixed-precision batch in one launch (LPB_SCHED_SINGLE): persistent
-// CTAs take the LPs order[0 .. count) (longest work first) from the atomic
-// `counter` and solve each with its area in this CTA's shared memory when it
-// fits (resident[lp] != 0), else in this CTA's global workspace slot -- the
-// per-LP code of the other mixed kernels, so the same results.  The FP64
-// re-solves of the LPs it does not certify stay separate launches: they need
-// the whole pass's queues.
+// CTAs take the LPs order[0 .. count) (longest work first within each part)
+// from the atomic `counter`.  Block mode, order[0 .. warp_from): the CTA
+// solves each LP with its area in the CTA's shared memory when it fits
+// (resident[lp] != 0), else in this CTA's global workspace slot.  Warp mode,
+// from the first index >= warp_from a CTA draws: every warp takes its own
+// LPs (the small ones, listed last), warp w working in
+// smem + w * kMixedSingleWarpArea, claiming its next LP before it solves the
+// current one.  The per-LP code is that of the other mixed kernels, so the
+// same results.  The FP64 re-solves of the LPs it does not certify stay
+// separate launches: they need the whole pass's queues.
 __global__ void __launch_bounds__(kMixedSingleThreads, 2)
 mixed_single_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams mp,
                     const int32_t* __restrict__ order, const uint8_t* __restrict__ resident, const int32_t count,
-                    unsigned char* workspace, const size_t slot_bytes, int32_t* __restrict__ counter,
-                    const FallbackQueues fq, int32_t* __restrict__ diag)
+                    const int32_t warp_from, unsigned char* workspace, const size_t slot_bytes,
+                    int32_t* __restrict__ counter, const FallbackQueues fq, int32_t* __restrict__ diag)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int next;
     unsigned char* slot = workspace ? workspace + (size_t)blockIdx.x * slot_bytes : nullptr;
+    int first = count;
     for (;;) {
         if (threadIdx.x == 0) next = atomicAdd(counter, 1);
         __syncthreads();
         const int idx = next;
         __syncthreads();
-        if (idx >= count) break;
+        if (idx >= count) return;
+        if (idx >= warp_from) {
+            first = idx;
+            break;
+        }
         const int lp = order[idx];
         BlockGroup g(reinterpret_cast<long long*>(smem + SmallLayout::red64),
                      reinterpret_cast<unsigned*>(smem + SmallLayout::red32));
@@ -72,6 +81,17 @@ mixed_single_kernel(const DeviceBatch B, const Tolerances tol, const MixedParams
         else if (threadIdx.x == 0)
             record_internal_error(diag, 7, lp);  // a plan without a slot for a streamed LP
         __syncthreads();
+    }
+    // warp mode (every thread of the CTA got here with the same `first`)
+    const int w = (int)(threadIdx.x >> 5);
+    const bool leader = (threadIdx.x & 31) == 0;
+    unsigned char* area = smem + (size_t)w * kMixedSingleWarpArea;
+    int idx = (w == 0) ? first : __shfl_sync(0xffffffffu, leader ? atomicAdd(counter, 1) : 0, 0);
+    while (idx < count) {
+        const int nxt = leader ? atomicAdd(counter, 1) : 0;
+        WarpGroup g;
+        mixed_solve_lp(g, B, tol, mp, order[idx], area, fq, diag);
+        idx = __shfl_sync(0xffffffffu, nxt, 0);
     }
 }
 
@@ -92,14 +112,16 @@ int mixed_single_ctas_per_sm(size_t smem) {
 }
 
 cudaError_t launch_mixed_single(const DeviceBatch& B, const Tolerances& tol, const MixedParams& mp,
-                                const int32_t* order, const uint8_t* resident, int32_t count, int ctas, size_t smem,
-                                unsigned char* workspace, size_t slot_bytes, int32_t* counter,
-                                const FallbackQueues& fq, int32_t* diag, cudaStream_t stream) {
+                                const int32_t* order, const uint8_t* resident, int32_t count, int32_t warp_from,
+                                int ctas, size_t smem, unsigned char* workspace, size_t slot_bytes,
+                                int32_t* counter, const FallbackQueues& fq, int32_t* diag, cudaStream_t stream) {
     if (count <= 0) return cudaSuccess;
+    // warp mode needs every warp's area
+    if (warp_from < count && smem < kMixedSingleSmemCap) return cudaErrorInvalidValue;
     cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int32_t), stream);
     if (err != cudaSuccess) return err;
-    mixed_single_kernel<<<ctas, kMixedSingleThreads, smem, stream>>>(B, tol, mp, order, resident, count, workspace,
-                                                                      slot_bytes, counter, fq, diag);
+    mixed_single_kernel<<<ctas, kMixedSingleThreads, smem, stream>>>(B, tol, mp, order, resident, count, warp_from,
+                                                                      workspace, slot_bytes, counter, fq, diag);
     return cudaGetLastError();
 }
 
