@@ -99,9 +99,11 @@ typedef struct {
  * whole batch in one persistent launch -- CTAs (512 threads for LP_PREC_FP64,
  * 256 for LP_PREC_FP32_REFINE) take the LPs, longest work first, from one work
  * queue and keep each tableau in their shared memory when it fits 110 KB,
- * else in their global workspace slot; with LP_PREC_FP32_REFINE the FP64
- * re-solves of uncertified LPs follow as separate launches (they need the
- * whole pass's queues).  Results are bit-identical under every schedule. */
+ * else in their global workspace slot; with LP_PREC_FP32_REFINE the LPs that
+ * AUTO solves on one warp come last and are solved one per warp (each warp
+ * of a CTA takes its own from the queue), and the FP64 re-solves of
+ * uncertified LPs follow as separate launches (they need the whole pass's
+ * queues).  Results are bit-identical under every schedule. */
 enum { LPB_SCHED_AUTO = 0, LPB_SCHED_STREAMED = 1, LPB_SCHED_CLUSTER = 2, LPB_SCHED_SINGLE = 3 };
 
 typedef struct lp_batch lp_batch;   /* opaque; owned by the library */
