@@ -778,7 +778,7 @@ def run_ours(args):
 
         e2e_step()
         torch.cuda.synchronize()
-        e2e_steps = max(3, args.steps)
+        e2e_steps = max(10, args.steps)
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
