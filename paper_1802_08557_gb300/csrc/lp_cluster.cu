@@ -410,7 +410,7 @@ __device__ __forceinline__ void build_and_solve(cg::cluster_group& cl, const int
         ++iters;
     }
 
-    // ---- labels must name variables (replicated: the same verdict everywhere)
+    // ---- labels must name variables (replicated: the same decision everywhere)
     {
         unsigned badl = 0, dummy;
         const unsigned nvar = (unsigned)(nm + k);
