@@ -8,7 +8,8 @@
 // consecutive, so neighbouring CTAs share A's rows in L2):
 //  - warp 0, one lane: TMA producer.  Tiles of 128 rows x 64 K-elements of A
 //    and of B (128 bytes per row, 128-byte swizzle) are copied by
-//    cp.async.bulk.tensor into a ring of kTcStages stages that runs across
+//    cp.async.bulk.tensor into a ring of 4 stages (5 when the product writes
+//    BF16 outputs only, whose epilogue staging is half as wide) that runs across
 //    output tiles; each stage's full barrier counts the bytes in, its empty
 //    barrier is armed by the MMAs that read it.
 //  - warp 1, one lane: MMA issuer.  Four tcgen05.mma (128 x 128 x 16) per
@@ -46,17 +47,27 @@
 namespace lpb {
 namespace {
 
-constexpr int kTcM = 128, kTcN = 128, kTcK = 64, kTcStages = 4;
+constexpr int kTcM = 128, kTcN = 128, kTcK = 64;
 constexpr int kTcEpiWarps = 8, kTcThreads = 64 + 32 * kTcEpiWarps;
 constexpr int kTcEpiCols = kTcN / 2;  // columns of a tile per epilogue warp
 constexpr uint32_t kTileBytes = kTcM * kTcK * 2;  // 16 KB per operand tile (also for B: kTcN == kTcM)
-// per epilogue warp: 32 rows of up to 256 bytes (its 64 columns as FP32, or
-// as BF16 in the first 128), padded to 272 bytes so that a lane's row piece
-// and a row's 16-byte chunks fall on distinct banks; then its 64 bias values
-constexpr uint32_t kStageRow = 272, kStageWarp = 32 * kStageRow;
-constexpr size_t kTcSmem = 1024 /* alignment slack */ + 2 * kTcStages * (size_t)kTileBytes +
-                           kTcEpiWarps * kStageWarp + kTcEpiWarps * kTcEpiCols * 4 + 256;
-static_assert(kTcSmem <= 227 * 1024, "shared memory of the tcgen05 product");
+// Ring depth and epilogue staging, per form.  Per epilogue warp: 32 rows of
+// its 64 columns, padded so that a lane's row piece and a row's 16-byte
+// chunks fall on distinct banks, then its 64 bias values.  kWide (an FP32
+// output C): rows of 256 bytes (272 with padding), 4 stages.  Otherwise
+// (BF16 outputs only): rows of 128 bytes (144), which leaves room for a
+// fifth stage -- the operand stream is bound by the latency of the TMA loads,
+// so more bytes in flight is what speeds it.
+template <bool kWide>
+struct TcForm {
+    static constexpr int kStages = kWide ? 4 : 5;
+    static constexpr uint32_t kStageRow = kWide ? 272 : 144, kStageWarp = 32 * kStageRow;
+    static constexpr size_t kSmem = 1024 /* alignment slack */ + 2 * kStages * (size_t)kTileBytes +
+                                    kTcEpiWarps * kStageWarp + kTcEpiWarps * kTcEpiCols * 4 +
+                                    256 /* barriers */;
+    static_assert(kSmem <= 227 * 1024, "shared memory of the tcgen05 product");
+    static_assert(8 * (2 * kStages + 5) <= 256, "barrier area");
+};
 constexpr long long kTcWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int kTcChunks = kTcEpiCols / 16;  // 16-column chunks per epilogue warp
 
@@ -129,9 +140,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
 }
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-template <int kEpi>
+template <int kEpi, bool kWide>
 __global__ void __launch_bounds__(kTcThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs g) {
+    constexpr int kTcStages = TcForm<kWide>::kStages;
+    constexpr uint32_t kStageRow = TcForm<kWide>::kStageRow, kStageWarp = TcForm<kWide>::kStageWarp;
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_fault;
     __shared__ uint32_t s_tmem;
@@ -312,7 +325,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     }
                 }
                 // FP32 rows of C (the warp's 64 columns = 256 bytes) through the staging area
-                if (g.C) {
+                if (kWide && g.C) {
 #pragma unroll
                     for (int c = 0; c < kTcChunks; ++c) {
                         float4* dst = reinterpret_cast<float4*>(my_stage + lane * kStageRow + c * 64);
@@ -419,15 +432,17 @@ bool make_map(CUtensorMap* map, const void* base, int rows, int k, int ld) {
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int kEpi>
+template <int kEpi, bool kWide>
 cudaError_t launch_tc(const GemmArgs& g, cudaStream_t s) {
     static_assert(tc::valid_m128_n(kTcN), "instruction shape");
+    constexpr size_t kTcSmem = TcForm<kWide>::kSmem;
     CUtensorMap ma, mb;
     if (!make_map(&ma, g.A, g.M, g.K, g.lda) || !make_map(&mb, g.B, g.N, g.K, g.ldb)) return cudaErrorNotSupported;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(gemm_tc_kernel<kEpi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+        attr = cudaFuncSetAttribute(gemm_tc_kernel<kEpi, kWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kTcSmem);
     });
     if (attr != cudaSuccess) return attr;
     int dev = 0, sms = 0;
@@ -436,8 +451,14 @@ cudaError_t launch_tc(const GemmArgs& g, cudaStream_t s) {
     if (err) return err;
     const int64_t tiles = (int64_t)((g.N + kTcN - 1) / kTcN) * ((g.M + kTcM - 1) / kTcM);
     const int grid = (int)std::min<int64_t>(tiles, sms);  // one persistent CTA per SM
-    gemm_tc_kernel<kEpi><<<grid, kTcThreads, kTcSmem, s>>>(ma, mb, g);
+    gemm_tc_kernel<kEpi, kWide><<<grid, kTcThreads, kTcSmem, s>>>(ma, mb, g);
     return cudaGetLastError();
+}
+
+// the wide form (FP32 staging, 4 stages) when the product writes C
+template <int kEpi>
+cudaError_t launch_tc(const GemmArgs& g, cudaStream_t s) {
+    return g.C ? launch_tc<kEpi, true>(g, s) : launch_tc<kEpi, false>(g, s);
 }
 
 }  // namespace

@@ -205,6 +205,14 @@ def test_tcgen05_product_aligned_rows_and_tail_tiles():
             hn = h.float().cpu().numpy()
             np.testing.assert_array_equal(hn, omlp.bf16_round(own.astype(np.float32)))
             np.testing.assert_array_equal(hT.float().cpu().numpy(), hn.T)
+        if epi == lpb.LPB_EPI_BIAS_RELU:
+            # the inference form (no FP32 output, no transposed copy: narrower
+            # epilogue staging and a deeper operand ring) writes the same h
+            h2 = torch.full((M, N), -3072.0, dtype=torch.bfloat16, device="cuda")
+            lpb.lp_mlp_gemm_bf16(epi, lpb.LPB_GEMM_TC, M, N, K, _bf16_dev(A), K, _bf16_dev(B), K, None, 0,
+                                 _dev(bias), None, h2, N, None, 0)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(h2.float().cpu().numpy(), hn)
     assert lpb.lp_mlp_tc_faults() == 0
 
 
