@@ -9,12 +9,14 @@
 // stream; lp_batch_results copies the outputs.
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda.h>
@@ -180,6 +182,13 @@ int pick_threads(int m, int n, int k, int requested) {
 // tableau size.  32 selects the one-warp-per-LP variant (no block barriers):
 // measured best up to 70x70 tableaux (50x50: 16.3 ms per 1e5 LPs against
 // 19.7 ms at 64 threads), 128 best at 100x100.
+// Rows with b_i < 0 (each gets an artificial variable in phase I).
+int32_t count_negative(const double* b, int32_t m) {
+    int32_t cnt = 0;
+    for (int32_t i = 0; i < m; ++i) cnt += b[i] < 0.0 ? 1 : 0;
+    return cnt;
+}
+
 int mixed_threads(int m, int n, int k, int requested) {
     if (requested > 0) return pick_threads(m, n, k, requested);
     const int64_t e = (int64_t)(m + 1 + (k > 0)) * (n + k + 1);
@@ -473,19 +482,20 @@ const char* lpb_strerror(lpb_err e) {
 
 const char* lpb_last_error(void) { return g_last_error.c_str(); }
 
-// lp_batch_create, with two more parameters for lp_solve_host: `copied`
+// lp_batch_create, with three more parameters for lp_solve_host: `copied`
 // (optional) is recorded on the stream right after the copies of A, b and c;
 // with `defer_check` (host inputs only) the call returns without waiting for
 // the stream, leaving the count of non-finite inputs in h->d_bad for the
 // caller to read after its solve (the check zeroes every such entry, so the
 // solve sees finite data).  Without it the call waits for the check and fails
-// on a non-finite entry.
+// on a non-finite entry.  `phase1_rows` (host inputs only, optional): every
+// LP's count of rows with b_i < 0, already counted by the caller.
 static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, const int32_t* n,
                             const int64_t* a_off, const double* A, int64_t a_len,
                             const int64_t* b_off, const double* b, int64_t b_len,
                             const int64_t* c_off, const double* c, int64_t c_len,
                             int32_t ptr_kind, const lp_batch_opts* opts, void* stream, cudaEvent_t copied,
-                            bool defer_check) {
+                            bool defer_check, const int32_t* phase1_rows = nullptr) {
     g_last_error.clear();
     if (!out) return fail(LPB_EINVAL, "out is NULL");
     if (defer_check && ptr_kind != LPB_HOST) return fail(LPB_EINVAL, "a deferred input check needs host inputs");
@@ -598,11 +608,10 @@ static lpb_err create_batch(lp_batch** out, int32_t num_lps, const int32_t* m, c
         // upload of the plan, so that no host call of this function waits for
         // a kernel (a kernel queued behind another stream's large grid can
         // wait for most of that grid)
-        for (int32_t k = 0; k < num_lps; ++k) {
-            const double* bk = b + hb[k];
-            int32_t cnt = 0;
-            for (int32_t i = 0; i < hm[k]; ++i) cnt += bk[i] < 0.0 ? 1 : 0;
-            hk[k] = cnt;
+        if (phase1_rows) {
+            std::copy(phase1_rows, phase1_rows + num_lps, hk.begin());
+        } else {
+            for (int32_t k = 0; k < num_lps; ++k) hk[k] = count_negative(b + hb[k], hm[k]);
         }
     } else {
         if ((err = cudaMemcpyAsync(hk.data(), dk, nl * 4, cudaMemcpyDeviceToHost, s)) ||
@@ -1489,6 +1498,28 @@ lpb_err lp_solve_host(int32_t num_lps, const int32_t* m, const int32_t* n,
     lpb_err e = LPB_OK;
     int64_t px = 0, py = 0;
     for (int32_t i = 0; i <= chunks; ++i) k0s[i] = (int32_t)((int64_t)num_lps * i / chunks);
+    // The phase-I row counts of ranges 1.. are taken by a helper thread while
+    // range 0 is created: each create would otherwise read its range's b on
+    // the host path that issues the copies (~0.3 ms per 12,500 LPs of 50 rows
+    // on the GPU machine's host).
+    std::vector<int32_t> phase1(chunks > 1 ? (size_t)num_lps : 0);
+    std::atomic<int32_t> counted{0};  // ranges 1 .. counted-1 are done
+    std::thread counter;
+    bool helper = false;
+    if (chunks > 1) {
+        counted.store(1, std::memory_order_relaxed);
+        try {
+            counter = std::thread([&] {
+                for (int32_t i = 1; i < chunks; ++i) {
+                    for (int32_t k = k0s[i]; k < k0s[i + 1]; ++k) phase1[k] = count_negative(b + hb[k], m[k]);
+                    counted.store(i + 1, std::memory_order_release);
+                }
+            });
+            helper = true;
+        } catch (...) {
+            helper = false;  // no thread: every create counts its own range
+        }
+    }
     // Every chunk is created and its solve enqueued without waiting for the
     // device: the copies run back to back (chunk i+1's copy waits for chunk
     // i's, so the first chunk has the bandwidth to itself), each solve starts
@@ -1519,10 +1550,14 @@ lpb_err lp_solve_host(int32_t num_lps, const int32_t* m, const int32_t* n,
             e = cuda_fail(err, "stream creation");
             break;
         }
+        if (helper && i > 0)
+            while (counted.load(std::memory_order_acquire) <= i) std::this_thread::yield();
         e = create_batch(&hs[i], k1 - k0, m + k0, n + k0, sa.data(), A + alo, ahi - alo, sb.data(), b + blo,
-                         bhi - blo, sc.data(), c + clo, chi - clo, LPB_HOST, opts, streams[i], copied[i], true);
+                         bhi - blo, sc.data(), c + clo, chi - clo, LPB_HOST, opts, streams[i], copied[i], true,
+                         helper && i > 0 ? phase1.data() + k0 : nullptr);
         if (e == LPB_OK) e = lp_batch_solve(hs[i], streams[i]);
     }
+    if (helper) counter.join();
     // the input checks (each read waits for its chunk's solve); results only
     // when every chunk's inputs were finite
     for (int32_t i = 0; i < chunks && e == LPB_OK; ++i) {
