@@ -87,6 +87,31 @@ def test_graph_solve_replays_the_plain_solve():
         s.close()
 
 
+@pytest.mark.parametrize("kind", ["all_one_warp", "none_one_warp"])
+def test_mixed_single_launch_warp_mode_bounds(kind):
+    """The mixed single launch with every LP in warp mode (small LPs only:
+    each CTA switches at its first draw) and with none (every LP above the
+    one-warp size): the same bits as the default plan."""
+    if kind == "all_one_warp":
+        lps = [W.uneven_dense(400, lo=4, hi=40, start=61).lp(k) for k in range(400)]
+        lps += [W.mixed_sign_dense(60, 30, 30, start=8).lp(k) for k in range(60)]
+    else:
+        rng = np.random.default_rng(62)
+        lps = [(rng.uniform(0, 1, (m, n)), rng.uniform(1, 100, m), rng.uniform(0, 1, n))
+               for m, n in [(130, 90), (100, 120), (160, 70), (95, 95), (140, 140), (300, 250)] * 4]
+    batch = W.pack("single_" + kind, lps)
+    want = gpu_solve_opts(batch, lpb.lpb_default_opts(precision=lpb.LP_PREC_FP32_REFINE))
+    s = lpb.BatchSolver(batch, opts=lpb.lpb_default_opts(precision=lpb.LP_PREC_FP32_REFINE,
+                                                         schedule=lpb.LPB_SCHED_SINGLE))
+    try:
+        for _ in range(2):
+            s.solve()
+            _same(s.results(), want)
+            assert s.plan_info()["internal_errors"] == 0
+    finally:
+        s.close()
+
+
 def test_lpt_order_and_errors():
     batch = W.uneven_dense(200, lo=8, hi=150, start=11)
     s = lpb.BatchSolver(batch)
