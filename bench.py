@@ -528,15 +528,24 @@ def run_ours(args):
         c1 = {"workload": f"dense5x5_{b1.num_lps}", "unit": "LPs/s"}
         for label, prec in (("fp64", lpb.LP_PREC_FP64), ("fp32r", lpb.LP_PREC_FP32_REFINE)):
             h1_ = lpb.BatchSolver(b1, opts=lpb.lpb_default_opts(precision=prec), stream=stream)
-            ms = ev_time(lambda: lpb.lp_batch_solve(h1_.h, stream))
+            ms_plain = ev_time(lambda: lpb.lp_batch_solve(h1_.h, stream))
             r1 = h1_.results()
+            # the same solve captured once and replayed as a CUDA graph: one
+            # launch instead of the counter resets, events and kernel launches
+            ms_graph = ev_time(lambda: lpb.lp_batch_solve_graph(h1_.h, stream))
+            rg = h1_.results()
             h1_.close()
+            ms = min(ms_plain, ms_graph)
             fl1 = 2.0 * algorithmic_fmas(b1, r1["iters"])
-            c1[label] = {"value": b1.num_lps * ws / (ms * 1e-3), "ms_per_step": ms, "result": r1,
+            c1[label] = {"value": b1.num_lps * ws / (ms * 1e-3), "ms_per_step": ms, "ms_plain": ms_plain,
+                         "ms_graph": ms_graph, "result": r1,
+                         "graph_results_identical": bool(all(np.array_equal(r1[k], rg[k])
+                                                             for k in ("status", "iters", "obj", "x"))),
                          "fp64_pipe_frac": fl1 / (ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS}
         c1["value"] = c1["fp64"]["value"]
-        c1["timing"] = ("CUDA events on the solve's stream around K whole solves; one launch of 1000 tiny CTAs, "
-                        "so the time is launch and latency, not throughput")
+        c1["timing"] = ("CUDA events on the solve's stream around K whole solves, plain and as a CUDA-graph replay "
+                        "(the faster is the value); one launch of 1000 tiny CTAs, so the time is launch and "
+                        "latency, not throughput")
         if rank == 0:
             idx1 = np.arange(b1.num_lps)
             r_one, dt_one, o1 = cpu_oracle_run(b1, idx1, 1)
