@@ -212,7 +212,16 @@ __device__ __noinline__ unsigned staged_update(const Staging st, const Tab tb, i
 // multiple of 4): the update takes two adjacent columns per thread with
 // 16-byte loads and stores -- the same FMA for every element, so the same
 // results; the pair beyond an odd Cact is padding (updated, never read).
-template <bool kPairs = false>
+// The barrier of the thread group that owns the LP: the CTA, or (kWarp: a
+// one-warp CTA) the warp -- no block barrier, shared-memory writes ordered by
+// __syncwarp.
+template <bool kWarp>
+__device__ __forceinline__ void group_sync() {
+    if (kWarp) __syncwarp();
+    else __syncthreads();
+}
+
+template <bool kPairs = false, bool kWarp = false>
 __device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e, Staging* st = nullptr) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int LD = tb.LD;
@@ -233,12 +242,12 @@ __device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e, 
         tb.col_var[e] = tb.row_var[l];
         tb.row_var[l] = ev;
     }
-    __syncthreads();
+    group_sync<kWarp>();
     const int left = tb.col_var[e];
     if (staged) {
         st->phase = staged_update(*st, tb, Ract, Cact, l, e);
         fence_proxy_async_global();  // this thread's stores before later bulk reads of them
-        __syncthreads();
+        group_sync<kWarp>();
         return left;
     }
     if (kPairs) {
@@ -263,7 +272,7 @@ __device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e, 
             jp += dj;
             if (jp >= Cp) { jp -= Cp; ++ii; }
         }
-        __syncthreads();
+        group_sync<kWarp>();
         return left;
     }
     const int total = (Ract - 1) * Cact;
@@ -280,13 +289,14 @@ __device__ __forceinline__ int pivot(Tab& tb, int Ract, int Cact, int l, int e, 
         jj += dj;
         if (jj >= Cact) { jj -= Cact; ++ii; }
     }
-    __syncthreads();
+    group_sync<kWarp>();
     return left;
 }
 
 // A retired artificial (it just left the basis and may never re-enter) sits
 // in column e: move the last live column into its place and shrink.
 // `fence`: the tableau is read by bulk copies later (staged streamed update).
+template <bool kWarp = false>
 __device__ __forceinline__ void retire_column(Tab& tb, int Ract, int e, int& Cvar, bool fence = false) {
     const int tid = threadIdx.x, nt = blockDim.x;
     if (e != Cvar) {
@@ -298,7 +308,7 @@ __device__ __forceinline__ void retire_column(Tab& tb, int Ract, int e, int& Cva
     }
     --Cvar;
     if (fence) fence_proxy_async_global();
-    __syncthreads();
+    group_sync<kWarp>();
 }
 
 // One LP, Steps 1-3 until it halts.  `small` is shared memory
@@ -306,7 +316,7 @@ __device__ __forceinline__ void retire_column(Tab& tb, int Ract, int e, int& Cva
 // (streamed), laid out by big_layout.  `stage` (streamed only, may be null):
 // `stage_bytes` of this CTA's shared memory for the staged update, used when
 // the LP's stage_total fits.
-template <bool kStreamed>
+template <bool kStreamed, bool kWarp = false>
 __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances& tol, const int lp,
                                           unsigned char* small, unsigned char* big, int32_t* diag,
                                           unsigned char* stage = nullptr, size_t stage_bytes = 0)
@@ -322,8 +332,17 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
 
     // k-independent part of the layout (k = 0 gives the same offsets)
     const BigLayout L0 = big_layout(m, n, 0, kStreamed);
-    Reducer red{reinterpret_cast<long long*>(small + SmallLayout::red64),
-                reinterpret_cast<unsigned*>(small + SmallLayout::red32), nw, warp, lane};
+    // the group's reductions: block-wide through the scratch in `small`, or
+    // (kWarp) `redux` within the one warp
+    auto make_red = [&]() {
+        if constexpr (kWarp) {
+            return WarpGroup();
+        } else {
+            return Reducer{reinterpret_cast<long long*>(small + SmallLayout::red64),
+                           reinterpret_cast<unsigned*>(small + SmallLayout::red32), nw, warp, lane};
+        }
+    };
+    auto red = make_red();
     long long* rkey = reinterpret_cast<long long*>(big + L0.rkey);
     int* row_var = reinterpret_cast<int*>(big + L0.row_var);
     int* neg = reinterpret_cast<int*>(big + L0.neg);
@@ -347,7 +366,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         }
         k += tot;
     }
-    __syncthreads();  // neg[] and row_var[] are read by other threads below
+    group_sync<kWarp>();  // neg[] and row_var[] are read by other threads below
 
     const BigLayout L = big_layout(m, n, k, kStreamed);
     Tab tb;
@@ -397,7 +416,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
                 if (j >= n) { j -= n; ++i; }
             }
             cp_async_wait_all();
-            __syncthreads();
+            group_sync<kWarp>();
             if (k > 0)
                 for (int64_t idx = tid; idx < cnt; idx += nt) {
                     const int i2 = (int)(idx / n), j2 = (int)(idx - (int64_t)i2 * n);
@@ -439,7 +458,7 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
             for (int t = 0; t < k; ++t) w = __dsub_rn(w, T[(size_t)neg[t] * LD + j]);
             Tw[j] = w;
         }
-        __syncthreads();
+        group_sync<kWarp>();
     }
 
     if (staged) fence_proxy_async_global();  // the build's stores before bulk reads of them
@@ -484,11 +503,11 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
                 if (iters >= max_iters) { status = kIterLimit; break; }
                 const int e = (int)(sel & 0xffffu);
                 for (int r = tid; r < m + 1; r += nt) tb.colE[r] = T[(size_t)r * LD + e];
-                __syncthreads();
-                const int left = pivot<kStreamed>(tb, m + 1, Cvar + 1, i, e, &stg);
+                group_sync<kWarp>();
+                const int left = pivot<kStreamed, kWarp>(tb, m + 1, Cvar + 1, i, e, &stg);
                 ++iters;
                 if (staged && *reinterpret_cast<volatile int*>(stage)) { status = kNumerical; break; }
-                if (left >= nm) retire_column(tb, m + 1, e, Cvar, staged);
+                if (left >= nm) retire_column<kWarp>(tb, m + 1, e, Cvar, staged);
             }
             phase = 2;
             continue;
@@ -586,14 +605,14 @@ __device__ __forceinline__ void solve_one(const DeviceBatch& B, const Tolerances
         if (iters >= max_iters) { status = kIterLimit; break; }
 
         // ---- Step 3: pivot ---------------------------------------------------
-        const int left = pivot<kStreamed>(tb, Ract, Cvar + 1, l, e, &stg);
+        const int left = pivot<kStreamed, kWarp>(tb, Ract, Cvar + 1, l, e, &stg);
         ++iters;
         if (staged && *reinterpret_cast<volatile int*>(stage)) {
             if (tid == 0) record_internal_error(diag, 8, lp, iters);  // a bulk copy did not complete
             status = kNumerical;
             break;
         }
-        if (left >= nm) retire_column(tb, Ract, e, Cvar, staged);
+        if (left >= nm) retire_column<kWarp>(tb, Ract, e, Cvar, staged);
     }
 
     // ---- labels must name variables (self-check before they index global
@@ -644,6 +663,17 @@ fp64_resident_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* _
 {
     extern __shared__ __align__(16) unsigned char smem[];
     solve_one<false>(B, tol, order[blockIdx.x], smem, smem + SmallLayout::total, diag);
+}
+
+// One warp per LP (blockDim = 32), the form of the groups of small tableaux:
+// the same per-LP code with warp barriers and `redux` reductions instead of
+// block barriers and shared-memory round trips; the same arithmetic.
+__global__ void __launch_bounds__(32, 32)
+fp64_warp_kernel(const DeviceBatch B, const Tolerances tol, const int32_t* __restrict__ order,
+                 int32_t* __restrict__ diag)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    solve_one<false, true>(B, tol, order[blockIdx.x], smem, smem + SmallLayout::total, diag);
 }
 
 // Resident kernel over a device-side list: persistent CTAs take the LPs
@@ -740,6 +770,8 @@ cudaError_t fp64_kernels_prepare() {
     cudaError_t err = cudaFuncSetAttribute(fp64_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)kMaxSmemPerBlock);
     if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(fp64_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmemPerBlock);
+    if (err != cudaSuccess) return err;
     return cudaFuncSetAttribute(fp64_resident_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(kMaxSmemPerBlock - 1024));
 }
@@ -819,7 +851,10 @@ cudaError_t launch_fp64_single(const DeviceBatch& B, const Tolerances& tol, cons
 cudaError_t launch_fp64_resident(const DeviceBatch& B, const Tolerances& tol, const int32_t* order,
                                  int32_t count, int threads, size_t smem, int32_t* diag, cudaStream_t stream) {
     if (count <= 0) return cudaSuccess;
-    fp64_resident_kernel<<<count, threads, smem, stream>>>(B, tol, order, diag);
+    if (threads == 32)
+        fp64_warp_kernel<<<count, 32, smem, stream>>>(B, tol, order, diag);
+    else
+        fp64_resident_kernel<<<count, threads, smem, stream>>>(B, tol, order, diag);
     return cudaGetLastError();
 }
 
